@@ -1,0 +1,155 @@
+/*
+ * gf.h -- C-ABI of libgf, the GB300 (sm_103a) lattice Green's function library.
+ *
+ * The library evaluates the data-parallel hot path of the fully charge
+ * self-consistent LDA+DMFT loop of Zhao et al., "Implementation of LDA+DMFT
+ * with pseudo-potential-plane-wave method" (arXiv:1111.2157):
+ *
+ *   G(k, i w_n)  = [(i w_n + mu) I - H_k - P_k^+ Sigma(i w_n) P_k]^{-1}   Sec. 3.2.2, Eq. dmftloop1
+ *   G_loc(i w_n) = sum_k w_k P_k G(k, i w_n) P_k^+                      Sec. 3.2.2, k-sum in Eq. dmftloop2
+ *   rho_k        = (1/beta) sum_n G(k, i w_n) e^{i w_n 0+}               Sec. 3.3, Eq. rho_LDA+DMFT
+ *   N(mu)        = sum_k w_k Tr rho_k = N_target                        Sec. 3.3, Eq. fix_mu
+ *   n_corr       = sum_k w_k Tr(P_k rho_k P_k^+)                        Sec. 3.4, Eq. nf_LDA+DMFT
+ *
+ * Conventions shared by every entry point:
+ *  - w_n = (2n+1) pi / beta, n = 0 .. n_iw-1 (positive fermionic frequencies only;
+ *    the negative ones follow from G(-i w_n) = G(i w_n)^+, which needs
+ *    Sigma(-i w_n) = Sigma(i w_n)^+).
+ *  - The Matsubara sum subtracts the 1/(i w) and 1/(i w)^2 moments of G,
+ *    T = I/(i w) + M2/(i w)^2 with M2 = H_k + P_k^+ Sigma_inf P_k - mu I, and adds
+ *    their exact sums back: rho_k = (1/beta) sum_{n<n_iw} [(G-T) + (G-T)^+] + I/2
+ *    - (beta/4) M2.  tail_order = 1 keeps only the 1/(i w) moment.
+ *  - The band index n already includes spin (Sec. 3.1): no factor 2 anywhere.
+ *  - Complex numbers are interleaved (re, im).  Arrays are row-major.
+ *  - Energies in eV, beta in 1/eV.
+ *  - k-points are grouped by system: k_system[] must be non-decreasing.
+ *  - Pointer arguments named *_ptr may point to host memory (pageable or
+ *    pinned) or to device memory of the context's device; the library tells
+ *    them apart through unified addressing.  Input arrays are copied into
+ *    library-owned device memory; the caller keeps ownership of its buffers.
+ *  - Every compute call is ordered on the context's stream and returns after
+ *    the stream has drained, so host outputs are valid on return.
+ *  - Calls on one context are not thread-safe.  No entry point throws; each
+ *    returns a gf_status and records a message for gf_last_error().
+ *  - There is no CPU fallback: gf_create fails with GF_ECUDA without a device.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gf_ctx gf_ctx;
+
+typedef enum {
+    GF_OK = 0,
+    GF_EINVAL = 1,     /* invalid argument (sizes, pointers, enum values)          */
+    GF_ENOMEM = 2,     /* device or host allocation failed                         */
+    GF_ECUDA = 3,      /* a CUDA runtime call failed (message in gf_last_error)    */
+    GF_ESINGULAR = 4,  /* a zero or non-finite pivot in some (k, i w_n) inverse    */
+    GF_ENOTCONV = 5,   /* the mu search did not reach tol within max_iter          */
+    GF_ETIMEOUT = 6,   /* reserved: a bounded device-side wait gave up             */
+    GF_ESTATE = 7      /* inputs missing (e.g. gf_local before gf_set_sigma)        */
+} gf_status;
+
+typedef enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1 } gf_precision;
+typedef enum { GF_C128 = 0, GF_C64 = 1 } gf_dtype;
+
+typedef struct {
+    int32_t n_systems;        /* >= 1: independent lattice problems in one context              */
+    int32_t n_k;              /* total k-points over all systems                                 */
+    const int32_t *nb;        /* host [n_k]: band-window size N_b(k) >= 1, or NULL: nb_uniform   */
+    int32_t nb_uniform;       /* used when nb == NULL                                            */
+    const int32_t *k_system;  /* host [n_k]: system of each k (non-decreasing), or NULL: all 0   */
+    const int32_t *m_system;  /* host [n_systems]: correlated orbitals m >= 1 of each system      */
+    int32_t n_iw;             /* positive Matsubara frequencies, >= 1                            */
+    const double *beta;       /* host [n_systems]: inverse temperature > 0                       */
+    const double *k_weight;   /* host [n_k]: w_k, or NULL: 1/N_k of the k's system               */
+    int32_t precision;        /* gf_precision                                                    */
+    int32_t input_dtype;      /* gf_dtype of the arrays given to gf_set_*                        */
+    int32_t tail_order;       /* 1 or 2 (2 recommended)                                          */
+    int32_t device;           /* CUDA device ordinal                                             */
+    void *stream;             /* cudaStream_t to order all work on, or NULL (legacy default)     */
+} gf_desc;
+
+/* Create a context: validates the descriptor, copies it, selects the device
+ * and allocates the device-side tables.  *out is NULL on failure.
+ * Errors: GF_EINVAL, GF_ENOMEM, GF_ECUDA. */
+gf_status gf_create(gf_ctx **out, const gf_desc *desc);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+gf_status gf_destroy(gf_ctx *ctx);
+
+/* H_k for all k (Sec. 3.1, Eq. H_LDA in the band window): packed per k, an
+ * N_b(k) x N_b(k) Hermitian block (is_diagonal = 0) or the N_b(k) diagonal
+ * entries E_nk (is_diagonal != 0, stored as complex with zero imaginary part).
+ * Hermiticity is the caller's contract and is not checked.
+ * Errors: GF_EINVAL (NULL), GF_ECUDA. */
+gf_status gf_set_hamiltonian(gf_ctx *ctx, const void *h_ptr, int32_t is_diagonal);
+
+/* P_k = S^k_{alpha n} = <alpha_k | phi_nk> (Sec. 3.1, Eq. S_norm): packed per k,
+ * an m(system) x N_b(k) block.  Orthonormal rows are not assumed.
+ * Errors: GF_EINVAL, GF_ECUDA. */
+gf_status gf_set_projectors(gf_ctx *ctx, const void *p_ptr);
+
+/* Sigma(i w_n) (Sec. 3.2.4): packed per system [n_iw][m][m], and Sigma(inf):
+ * packed per system [m][m] (Hermitian; the double-counting shift -V_DC is to be
+ * folded in by the caller, as H_ps of Eq. pseudo_H_k does).
+ * Errors: GF_EINVAL, GF_ECUDA. */
+gf_status gf_set_sigma(gf_ctx *ctx, const void *sigma_iw_ptr, const void *sigma_inf_ptr);
+
+/* G_loc(i w_n) = sum_k w_k P_k G P_k^+ (Eq. dmftloop2) at mu[s] (host [n_systems]).
+ * Output: packed per system [n_iw][m][m] complex128, host or device.
+ * Errors: GF_ESTATE (inputs missing), GF_ESINGULAR, GF_EINVAL, GF_ECUDA. */
+gf_status gf_local(gf_ctx *ctx, const double *mu, void *gloc_out_ptr);
+
+/* N(mu) = sum_k w_k Tr rho_k (Eq. fix_mu) and dN/dmu per system, to host
+ * arrays [n_systems] (dn_dmu_out may be NULL).
+ * Errors: GF_ESTATE, GF_ESINGULAR, GF_EINVAL, GF_ECUDA. */
+gf_status gf_occupation(gf_ctx *ctx, const double *mu, double *n_out, double *dn_dmu_out);
+
+/* Chemical potential of every system with |N(mu) - n_target[s]| <= tol
+ * (Eq. fix_mu), by safeguarded Newton steps on N(mu) with a bisection bracket.
+ * mu_inout [n_systems] holds the start values and receives the result;
+ * iters_out (may be NULL) receives the number of N(mu) evaluations.
+ * Errors: GF_ENOTCONV (mu_inout then holds the best iterate), GF_ESTATE,
+ * GF_ESINGULAR, GF_EINVAL, GF_ECUDA. */
+gf_status gf_find_mu(gf_ctx *ctx, const double *n_target, double tol, int32_t max_iter,
+                     double *mu_inout, int32_t *iters_out);
+
+/* rho_k (Eq. rho_LDA+DMFT) for every k, packed per k as N_b(k) x N_b(k)
+ * complex128 (host or device), and n_corr = sum_k w_k Tr(P_k rho_k P_k^+)
+ * (Eq. nf_LDA+DMFT) per system to host [n_systems] (may be NULL).
+ * rho_out_ptr may be NULL to get n_corr only.
+ * Errors: GF_ESTATE, GF_ESINGULAR, GF_EINVAL, GF_ECUDA. */
+gf_status gf_density_matrix(gf_ctx *ctx, const double *mu, void *rho_out_ptr, double *n_corr_out);
+
+/* Vector-Jacobian product (not in the paper; derived from Eq. dmftloop1 with
+ * dG = G P^+ dSigma P G and dG/dmu = -G^2).  For a real loss L with
+ * dL = Re<gloc_bar, dG_loc> + n_bar . dN, and the convention
+ * grad z = dL/dRe z + i dL/dIm z:
+ *   sigma_bar(w_n) = sum_k w_k [A_k^+ gloc_bar(w_n) A_k^+ + n_bar (2/beta) B_k^+],
+ *   mu_bar         = n_bar dN/dmu - sum_n sum_k w_k Re<gloc_bar(w_n), B_k>,
+ * with A_k = P_k G P_k^+ and B_k = P_k G G P_k^+.
+ * gloc_bar_ptr: packed per system [n_iw][m][m] complex128 or NULL (= 0);
+ * n_bar: host [n_systems] or NULL (= 0).  sigma_bar_out_ptr: packed like
+ * Sigma(i w_n), complex128, host or device.  mu_bar_out: host [n_systems].
+ * Errors: GF_ESTATE, GF_ESINGULAR, GF_EINVAL, GF_ECUDA. */
+gf_status gf_backward(gf_ctx *ctx, const double *mu, const void *gloc_bar_ptr, const double *n_bar,
+                      void *sigma_bar_out_ptr, double *mu_bar_out);
+
+/* Message of the last failed call on this context ("" if none).  Owned by the
+ * context, valid until the next call on it. */
+const char *gf_last_error(const gf_ctx *ctx);
+
+/* Counters of the last compute call: kernel launches and (k, i w_n) points. */
+gf_status gf_last_stats(const gf_ctx *ctx, int64_t *kernel_launches, int64_t *points);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF_H */

@@ -1,0 +1,733 @@
+// C-ABI of libgf (declared in include/gf.h): context, argument validation,
+// host<->device marshalling, work-item scheduling and the mu search.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "gf.h"
+#include "gf_internal.cuh"
+
+using gf::Item;
+using gf::KInfo;
+using gf::SInfo;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  return e;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Trigamma psi'(x) for x > 0: recurrence up to x >= 20, then the asymptotic series
+// psi'(x) ~ 1/x + 1/(2x^2) + sum_k B_2k / x^(2k+1).
+double trigamma(double x) {
+  double acc = 0.0;
+  while (x < 20.0) {
+    acc += 1.0 / (x * x);
+    x += 1.0;
+  }
+  const double ix = 1.0 / x, ix2 = ix * ix;
+  const double series =
+      ix + 0.5 * ix2 +
+      ix * ix2 * (1.0 / 6 - ix2 * (1.0 / 30 - ix2 * (1.0 / 42 - ix2 * (1.0 / 30 - ix2 * 5.0 / 66))));
+  return acc + series;
+}
+
+}  // namespace
+
+struct gf_ctx {
+  int n_sys = 0, n_k = 0, n_iw = 0, precision = 0, in_dtype = 0, tail_order = 2, device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<int> nb, ksys, msys;
+  std::vector<double> beta, wk;
+  std::vector<KInfo> kinfo;
+  std::vector<SInfo> sinfo;
+  std::vector<int64_t> offD;  // prefix sums of nb (diagonal H input)
+  int64_t totH = 0, totP = 0, totSig = 0, totSinf = 0, totNb = 0;
+  int nbmax = 0, mmax = 0;
+  int sm_count = 0, smem_optin = 0;
+  int chunk_w = 1, n_chunks = 1;
+  size_t gq_budget = 0;
+  std::vector<Item> items;              // sorted by (k batch, -nb, k, chunk)
+  std::vector<int> batch_k0, batch_item0;  // batch b: k in [batch_k0[b], batch_k0[b+1])
+  DevBuf H, P, Sig, Sinf, Einf, trHE, kinfo_d, sinfo_d, items_d, offD_d, mu, nbar, gbar, status,
+      queue, stage, occ_part, rho_part, rho_out, gq, kN, kdN, kNc, sysout, a_scratch, mubar_part,
+      mubar_sys, gacc;
+  bool have_H = false, have_P = false, have_S = false, einf_dirty = true;
+  bool have_gbar_for_call = false;
+  // pinned host staging: mu [S] | n_bar [S] | status | per-system outputs [2S] | mu_bar [S]
+  double* hpin = nullptr;
+  double* hp_mu() { return hpin; }
+  double* hp_nbar() { return hpin + n_sys; }
+  double* hp_status() { return hpin + 2 * n_sys; }
+  double* hp_sys() { return hpin + 2 * n_sys + 1; }
+  double* hp_mubar() { return hpin + 4 * n_sys + 1; }
+  std::string err;
+  int64_t last_launches = 0, last_points = 0;
+};
+
+namespace {
+
+gf_status fail(gf_ctx* c, gf_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define GF_CU(call)                                                                        \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA,               \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+// Copy n complex numbers of the input dtype from a host or device pointer into
+// a complex128 device array.
+gf_status load_complex(gf_ctx* c, const void* src, int64_t n, double2* dst) {
+  if (n <= 0) return GF_OK;
+  if (c->in_dtype == GF_C128) {
+    GF_CU(cudaMemcpyAsync(dst, src, (size_t)n * 16, cudaMemcpyDefault, c->stream));
+  } else {
+    GF_CU(ensure(c->stage, (size_t)n * 8));
+    GF_CU(cudaMemcpyAsync(c->stage.p, src, (size_t)n * 8, cudaMemcpyDefault, c->stream));
+    GF_CU(gf::launch_upcast(c->stage.as<float2>(), dst, n, c->stream));
+  }
+  return GF_OK;
+}
+
+gf_status sync_and_check(gf_ctx* c) {
+  GF_CU(cudaMemcpyAsync(c->hp_status(), c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GF_CU(cudaStreamSynchronize(c->stream));
+  int flags = 0;
+  std::memcpy(&flags, c->hp_status(), sizeof(int));
+  if (flags & gf::kFlagSingular)
+    return fail(c, GF_ESINGULAR, "zero or non-finite pivot in a (k, i w_n) inverse");
+  return GF_OK;
+}
+
+gf_status ensure_einf(gf_ctx* c) {
+  if (!c->einf_dirty) return GF_OK;
+  GF_CU(gf::launch_einf(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->H.as<double2>(),
+                        c->P.as<double2>(), c->Sinf.as<double2>(), c->n_k, c->Einf.as<double2>(),
+                        c->trHE.as<double>(), c->stream));
+  c->last_launches += 1;
+  c->einf_dirty = false;
+  return GF_OK;
+}
+
+gf_status check_ready(gf_ctx* c) {
+  if (!c->have_H || !c->have_P || !c->have_S)
+    return fail(c, GF_ESTATE, "gf_set_hamiltonian, gf_set_projectors and gf_set_sigma must all be "
+                              "called before a compute call");
+  return GF_OK;
+}
+
+gf_status upload_mu(gf_ctx* c, const double* mu) {
+  if (!mu) return fail(c, GF_EINVAL, "mu is NULL");
+  for (int s = 0; s < c->n_sys; ++s) {
+    if (!std::isfinite(mu[s])) return fail(c, GF_EINVAL, "mu is not finite");
+    c->hp_mu()[s] = mu[s];
+  }
+  GF_CU(cudaMemcpyAsync(c->mu.p, c->hp_mu(), sizeof(double) * c->n_sys, cudaMemcpyHostToDevice,
+                        c->stream));
+  return GF_OK;
+}
+
+// Run the point kernel over every (k, chunk) item with the given mode.  For
+// kGloc / kAdj the per-(k, n) m x m results are reduced over k into c->gacc,
+// k-batch by k-batch, in increasing k order.
+gf_status run_points(gf_ctx* c, int mode) {
+  gf_status st = check_ready(c);
+  if (st) return st;
+  st = ensure_einf(c);
+  if (st) return st;
+  GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
+
+  int a_in_smem = 1;
+  size_t smem = gf::point_fp64_smem(c->nbmax, c->mmax, mode, 1);
+  const size_t limit = (size_t)c->smem_optin - 1024;
+  if (smem > limit) {
+    a_in_smem = 0;
+    smem = gf::point_fp64_smem(c->nbmax, c->mmax, mode, 0);
+    if (smem > limit)
+      return fail(c, GF_EINVAL, "N_b or m too large for the shared-memory tiles of the FP64 kernel");
+  }
+  int bps = gf::point_fp64_blocks_per_sm(smem);
+  if (bps < 1) bps = 1;
+  const int grid = c->sm_count * bps;
+  gf::PointParams p{};
+  p.H = c->H.as<double2>();
+  p.P = c->P.as<double2>();
+  p.Sig = c->Sig.as<double2>();
+  p.kinfo = c->kinfo_d.as<KInfo>();
+  p.sinfo = c->sinfo_d.as<SInfo>();
+  p.n_chunks = c->n_chunks;
+  p.queue = c->queue.as<int>();
+  p.mu = c->mu.as<double>();
+  p.mode = mode;
+  p.nbmax = c->nbmax;
+  p.mmax = c->mmax;
+  p.a_in_smem = a_in_smem;
+  if (!a_in_smem) {
+    p.a_stride = (int64_t)c->nbmax * (c->nbmax | 1);
+    GF_CU(ensure(c->a_scratch, (size_t)grid * p.a_stride * sizeof(double2)));
+    p.a_scratch = c->a_scratch.as<double2>();
+  }
+  if (mode & gf::kOcc) {
+    GF_CU(ensure(c->occ_part, sizeof(double) * 2 * (size_t)c->n_k * c->n_chunks));
+    p.occ_part = c->occ_part.as<double>();
+  }
+  if (mode & gf::kRho) {
+    p.rho_chunk_stride = c->totH;
+    GF_CU(ensure(c->rho_part, sizeof(double2) * (size_t)c->totH * c->n_chunks));
+    p.rho_part = c->rho_part.as<double2>();
+  }
+  if (mode & gf::kAdj) {
+    GF_CU(ensure(c->mubar_part, sizeof(double) * (size_t)c->n_k * c->n_chunks));
+    p.mubar_part = c->mubar_part.as<double>();
+  }
+  p.n_iw = c->n_iw;
+  p.status = c->status.as<int>();
+  p.gbar = nullptr;
+  p.nbar = nullptr;
+  if (mode & gf::kAdj) {
+    p.gbar = c->have_gbar_for_call ? c->gbar.as<double2>() : nullptr;
+    p.nbar = c->nbar.as<double>();
+  }
+  const bool kred = (mode & (gf::kGloc | gf::kAdj)) != 0;
+  const int nb_batches = kred ? (int)c->batch_k0.size() - 1 : 1;
+  int64_t points = 0;
+  for (int b = 0; b < nb_batches; ++b) {
+    const int i0 = kred ? c->batch_item0[b] : 0;
+    const int i1 = kred ? c->batch_item0[b + 1] : (int)c->items.size();
+    const int kb0 = kred ? c->batch_k0[b] : 0;
+    const int kb1 = kred ? c->batch_k0[b + 1] : c->n_k;
+    if (kred) {
+      GF_CU(ensure(c->gq, sizeof(double2) * (size_t)(kb1 - kb0) * c->n_iw * c->mmax * c->mmax));
+      p.gq = c->gq.as<double2>();
+      p.kb0 = kb0;
+    }
+    p.items = c->items_d.as<Item>() + i0;
+    p.n_items = i1 - i0;
+    GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
+    GF_CU(gf::launch_point_fp64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
+    c->last_launches += 1;
+    if (kred) {
+      int max_total = 0;
+      for (const SInfo& s : c->sinfo) max_total = std::max(max_total, c->n_iw * s.m * s.m);
+      GF_CU(gf::launch_gq_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys, max_total,
+                                 c->gq.as<double2>(), kb0, kb1, c->n_iw, c->mmax, b == 0,
+                                 c->gacc.as<double2>(), c->stream));
+      c->last_launches += 1;
+    }
+    for (int i = i0; i < i1; ++i) points += c->items[i].n1 - c->items[i].n0;
+  }
+  c->last_points = points;
+  return GF_OK;
+}
+
+gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  st = run_points(c, gf::kOcc);
+  if (st) return st;
+  GF_CU(gf::launch_occ_finalize(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->trHE.as<double>(),
+                                c->mu.as<double>(), c->occ_part.as<double>(), c->n_chunks, c->n_k,
+                                c->kN.as<double>(), c->kdN.as<double>(), c->stream));
+  GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                              c->kN.as<double>(), c->kdN.as<double>(), c->sysout.as<double>(),
+                              c->stream));
+  c->last_launches += 2;
+  GF_CU(cudaMemcpyAsync(c->hp_sys(), c->sysout.p, sizeof(double) * 2 * c->n_sys,
+                        cudaMemcpyDeviceToHost, c->stream));
+  st = sync_and_check(c);
+  if (st) return st;
+  for (int s = 0; s < c->n_sys; ++s) {
+    if (n_out) n_out[s] = c->hp_sys()[2 * s];
+    if (dn_out) dn_out[s] = c->hp_sys()[2 * s + 1];
+  }
+  return GF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gf_status gf_create(gf_ctx** out, const gf_desc* d) {
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "out is NULL";
+    return GF_EINVAL;
+  }
+  *out = nullptr;
+  auto bad = [](const char* m) {
+    g_create_error = m;
+    return GF_EINVAL;
+  };
+  if (!d) return bad("desc is NULL");
+  if (d->n_systems < 1) return bad("n_systems must be >= 1");
+  if (d->n_k < 1) return bad("n_k must be >= 1");
+  if (d->n_iw < 1) return bad("n_iw must be >= 1");
+  if (!d->m_system) return bad("m_system is NULL");
+  if (!d->beta) return bad("beta is NULL");
+  if (!d->nb && d->nb_uniform < 1) return bad("nb is NULL and nb_uniform < 1");
+  if (d->precision != GF_PREC_FP64 && d->precision != GF_PREC_MIXED) return bad("bad precision");
+  if (d->input_dtype != GF_C128 && d->input_dtype != GF_C64) return bad("bad input_dtype");
+  if (d->tail_order != 1 && d->tail_order != 2) return bad("tail_order must be 1 or 2");
+  gf_ctx* c = new (std::nothrow) gf_ctx();
+  if (!c) {
+    g_create_error = "host allocation failed";
+    return GF_ENOMEM;
+  }
+  c->n_sys = d->n_systems;
+  c->n_k = d->n_k;
+  c->n_iw = d->n_iw;
+  c->precision = d->precision;
+  c->in_dtype = d->input_dtype;
+  c->tail_order = d->tail_order;
+  c->device = d->device;
+  c->stream = static_cast<cudaStream_t>(d->stream);
+  c->nb.resize(c->n_k);
+  c->ksys.resize(c->n_k);
+  for (int k = 0; k < c->n_k; ++k) {
+    c->nb[k] = d->nb ? d->nb[k] : d->nb_uniform;
+    c->ksys[k] = d->k_system ? d->k_system[k] : 0;
+    if (c->nb[k] < 1) { delete c; return bad("every N_b(k) must be >= 1"); }
+    if (c->ksys[k] < 0 || c->ksys[k] >= c->n_sys) { delete c; return bad("k_system out of range"); }
+    if (k > 0 && c->ksys[k] < c->ksys[k - 1]) { delete c; return bad("k_system must be non-decreasing"); }
+  }
+  c->msys.assign(d->m_system, d->m_system + c->n_sys);
+  c->beta.assign(d->beta, d->beta + c->n_sys);
+  for (int s = 0; s < c->n_sys; ++s) {
+    if (c->msys[s] < 1) { delete c; return bad("every m must be >= 1"); }
+    if (!(c->beta[s] > 0.0) || !std::isfinite(c->beta[s])) { delete c; return bad("beta must be > 0"); }
+  }
+  // systems, k ranges and weights
+  c->sinfo.resize(c->n_sys);
+  std::vector<int> count(c->n_sys, 0);
+  for (int k = 0; k < c->n_k; ++k) count[c->ksys[k]]++;
+  int64_t offSig = 0, offSinf = 0;
+  int k0 = 0;
+  for (int s = 0; s < c->n_sys; ++s) {
+    if (count[s] == 0) { delete c; return bad("a system has no k-points"); }
+    SInfo& si = c->sinfo[s];
+    si.m = c->msys[s];
+    si.k0 = k0;
+    si.k1 = k0 + count[s];
+    k0 = si.k1;
+    si.pad = 0;
+    si.beta = c->beta[s];
+    if (c->tail_order == 2) {
+      // (2/beta) sum_{n<N} 1/w_n^2 - beta/4 = -(2/beta)(beta/pi)^2 sum_{n>=N} (2n+1)^-2
+      //                                     = -(beta/(2 pi^2)) psi'(N + 1/2)
+      si.tailc = -si.beta / (2.0 * M_PI * M_PI) * trigamma(c->n_iw + 0.5);
+    } else {
+      si.tailc = 0.0;
+    }
+    si.offSig = offSig;
+    si.offSinf = offSinf;
+    offSig += (int64_t)c->n_iw * si.m * si.m;
+    offSinf += (int64_t)si.m * si.m;
+    c->mmax = std::max(c->mmax, si.m);
+  }
+  c->totSig = offSig;
+  c->totSinf = offSinf;
+  c->kinfo.resize(c->n_k);
+  c->wk.resize(c->n_k);
+  c->offD.resize(c->n_k);
+  int64_t offH = 0, offP = 0, offD = 0;
+  for (int k = 0; k < c->n_k; ++k) {
+    KInfo& ki = c->kinfo[k];
+    ki.nb = c->nb[k];
+    ki.sys = c->ksys[k];
+    ki.offH = offH;
+    ki.offP = offP;
+    const SInfo& si = c->sinfo[ki.sys];
+    ki.w = d->k_weight ? d->k_weight[k] : 1.0 / (si.k1 - si.k0);
+    if (!std::isfinite(ki.w)) { delete c; return bad("k_weight is not finite"); }
+    c->wk[k] = ki.w;
+    c->offD[k] = offD;
+    offH += (int64_t)ki.nb * ki.nb;
+    offP += (int64_t)si.m * ki.nb;
+    offD += ki.nb;
+    c->nbmax = std::max(c->nbmax, ki.nb);
+  }
+  c->totH = offH;
+  c->totP = offP;
+  c->totNb = offD;
+
+  // device
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    delete c;
+    g_create_error = "no CUDA device";
+    return GF_ECUDA;
+  }
+  if (c->device < 0 || c->device >= ndev) { delete c; return bad("device ordinal out of range"); }
+  DeviceGuard guard(c->device);
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  // k-batches for the k-reductions: gq holds (k1-k0) * n_iw * mmax^2 complex numbers
+  size_t budget = (size_t)8 << 30;
+  if (const char* env = std::getenv("GF_GQ_BUDGET_MB")) budget = (size_t)std::atoll(env) << 20;
+  c->gq_budget = budget;
+  const size_t per_k = sizeof(double2) * (size_t)c->n_iw * c->mmax * c->mmax;
+  const int kpb = (int)std::max<size_t>(1, std::min<size_t>(c->n_k, budget / per_k));
+  // chunk width: about 40 items per resident CTA
+  const size_t smem = gf::point_fp64_smem(c->nbmax, c->mmax, gf::kOcc, 1);
+  int bps = (smem <= (size_t)c->smem_optin - 1024) ? gf::point_fp64_blocks_per_sm(smem) : 1;
+  if (bps < 1) bps = 1;
+  const double resident = (double)c->sm_count * bps;
+  const double want = (double)c->n_k * c->n_iw / (40.0 * resident);
+  c->chunk_w = (int)std::min<double>(c->n_iw, std::max(4.0, std::ceil(want)));
+  c->n_chunks = (c->n_iw + c->chunk_w - 1) / c->chunk_w;
+  c->batch_k0.clear();
+  c->batch_item0.clear();
+  for (int kb = 0; kb < c->n_k; kb += kpb) {
+    const int ke = std::min(c->n_k, kb + kpb);
+    c->batch_k0.push_back(kb);
+    c->batch_item0.push_back((int)c->items.size());
+    std::vector<Item> its;
+    for (int k = kb; k < ke; ++k)
+      for (int ch = 0; ch < c->n_chunks; ++ch)
+        its.push_back(Item{k, ch * c->chunk_w, std::min(c->n_iw, (ch + 1) * c->chunk_w), ch});
+    // most expensive first (N_b^3), stable in (k, chunk)
+    std::stable_sort(its.begin(), its.end(),
+                     [&](const Item& a, const Item& b) { return c->nb[a.k] > c->nb[b.k]; });
+    c->items.insert(c->items.end(), its.begin(), its.end());
+  }
+  c->batch_k0.push_back(c->n_k);
+  c->batch_item0.push_back((int)c->items.size());
+
+  auto alloc_all = [&]() -> cudaError_t {
+    cudaError_t e;
+    if ((e = ensure(c->H, sizeof(double2) * c->totH))) return e;
+    if ((e = ensure(c->Einf, sizeof(double2) * c->totH))) return e;
+    if ((e = ensure(c->P, sizeof(double2) * c->totP))) return e;
+    if ((e = ensure(c->Sig, sizeof(double2) * c->totSig))) return e;
+    if ((e = ensure(c->gacc, sizeof(double2) * c->totSig))) return e;
+    if ((e = ensure(c->Sinf, sizeof(double2) * c->totSinf))) return e;
+    if ((e = ensure(c->trHE, sizeof(double) * c->n_k))) return e;
+    if ((e = ensure(c->kN, sizeof(double) * c->n_k))) return e;
+    if ((e = ensure(c->kdN, sizeof(double) * c->n_k))) return e;
+    if ((e = ensure(c->kNc, sizeof(double) * c->n_k))) return e;
+    if ((e = ensure(c->kinfo_d, sizeof(KInfo) * c->n_k))) return e;
+    if ((e = ensure(c->sinfo_d, sizeof(SInfo) * c->n_sys))) return e;
+    if ((e = ensure(c->items_d, sizeof(Item) * c->items.size()))) return e;
+    if ((e = ensure(c->offD_d, sizeof(int64_t) * c->n_k))) return e;
+    if ((e = ensure(c->mu, sizeof(double) * c->n_sys))) return e;
+    if ((e = ensure(c->nbar, sizeof(double) * c->n_sys))) return e;
+    if ((e = ensure(c->mubar_sys, sizeof(double) * c->n_sys))) return e;
+    if ((e = ensure(c->sysout, sizeof(double) * 2 * c->n_sys))) return e;
+    if ((e = ensure(c->status, sizeof(int)))) return e;
+    if ((e = ensure(c->queue, sizeof(int)))) return e;
+    if ((e = cudaMallocHost(&c->hpin, sizeof(double) * (8 + 5 * (size_t)c->n_sys)))) return e;
+    if ((e = cudaMemcpyAsync(c->kinfo_d.p, c->kinfo.data(), sizeof(KInfo) * c->n_k,
+                             cudaMemcpyHostToDevice, c->stream)))
+      return e;
+    if ((e = cudaMemcpyAsync(c->sinfo_d.p, c->sinfo.data(), sizeof(SInfo) * c->n_sys,
+                             cudaMemcpyHostToDevice, c->stream)))
+      return e;
+    if ((e = cudaMemcpyAsync(c->items_d.p, c->items.data(), sizeof(Item) * c->items.size(),
+                             cudaMemcpyHostToDevice, c->stream)))
+      return e;
+    if ((e = cudaMemcpyAsync(c->offD_d.p, c->offD.data(), sizeof(int64_t) * c->n_k,
+                             cudaMemcpyHostToDevice, c->stream)))
+      return e;
+    if ((e = cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream))) return e;
+    return cudaStreamSynchronize(c->stream);
+  };
+  cudaError_t e = alloc_all();
+  if (e != cudaSuccess) {
+    g_create_error = std::string("device setup failed: ") + cudaGetErrorString(e);
+    gf_destroy(c);
+    return e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA;
+  }
+  *out = c;
+  return GF_OK;
+}
+
+gf_status gf_destroy(gf_ctx* c) {
+  if (!c) return GF_OK;
+  DeviceGuard guard(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->H, &c->P, &c->Sig, &c->Sinf, &c->Einf, &c->trHE, &c->kinfo_d, &c->sinfo_d,
+                    &c->items_d, &c->offD_d, &c->mu, &c->nbar, &c->gbar, &c->status, &c->queue,
+                    &c->stage, &c->occ_part, &c->rho_part, &c->rho_out, &c->gq, &c->kN, &c->kdN,
+                    &c->kNc, &c->sysout, &c->a_scratch, &c->mubar_part, &c->mubar_sys, &c->gacc};
+  for (DevBuf* b : bufs) release(*b);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  delete c;
+  return GF_OK;
+}
+
+gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) {
+  if (!c) return GF_EINVAL;
+  if (!h) return fail(c, GF_EINVAL, "h_ptr is NULL");
+  DeviceGuard guard(c->device);
+  if (is_diagonal) {
+    GF_CU(ensure(c->stage, 0));
+    DevBuf diag;
+    gf_status st = GF_OK;
+    cudaError_t e = ensure(diag, sizeof(double2) * c->totNb);
+    if (e != cudaSuccess) return fail(c, GF_ENOMEM, "allocation of the diagonal staging failed");
+    st = load_complex(c, h, c->totNb, diag.as<double2>());
+    if (st == GF_OK) {
+      e = gf::launch_diag_to_dense(c->kinfo_d.as<KInfo>(), diag.as<double2>(), c->offD_d.as<int64_t>(),
+                                   c->n_k, c->H.as<double2>(), c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) st = fail(c, GF_ECUDA, std::string("diagonal H: ") + cudaGetErrorString(e));
+    }
+    release(diag);
+    if (st) return st;
+  } else {
+    gf_status st = load_complex(c, h, c->totH, c->H.as<double2>());
+    if (st) return st;
+    GF_CU(cudaStreamSynchronize(c->stream));
+  }
+  c->have_H = true;
+  c->einf_dirty = true;
+  return GF_OK;
+}
+
+gf_status gf_set_projectors(gf_ctx* c, const void* p) {
+  if (!c) return GF_EINVAL;
+  if (!p) return fail(c, GF_EINVAL, "p_ptr is NULL");
+  DeviceGuard guard(c->device);
+  gf_status st = load_complex(c, p, c->totP, c->P.as<double2>());
+  if (st) return st;
+  GF_CU(cudaStreamSynchronize(c->stream));
+  c->have_P = true;
+  c->einf_dirty = true;
+  return GF_OK;
+}
+
+gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) {
+  if (!c) return GF_EINVAL;
+  if (!sig || !sinf) return fail(c, GF_EINVAL, "sigma_iw_ptr or sigma_inf_ptr is NULL");
+  DeviceGuard guard(c->device);
+  gf_status st = load_complex(c, sig, c->totSig, c->Sig.as<double2>());
+  if (st) return st;
+  st = load_complex(c, sinf, c->totSinf, c->Sinf.as<double2>());
+  if (st) return st;
+  GF_CU(cudaStreamSynchronize(c->stream));
+  c->have_S = true;
+  c->einf_dirty = true;
+  return GF_OK;
+}
+
+gf_status gf_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+  if (!c) return GF_EINVAL;
+  if (!n_out) return fail(c, GF_EINVAL, "n_out is NULL");
+  DeviceGuard guard(c->device);
+  c->last_launches = 0;
+  return occupation_impl(c, mu, n_out, dn_out);
+}
+
+gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_iter,
+                     double* mu_inout, int32_t* iters_out) {
+  if (!c) return GF_EINVAL;
+  if (!n_target || !mu_inout) return fail(c, GF_EINVAL, "n_target or mu_inout is NULL");
+  if (!(tol > 0.0) || max_iter < 1) return fail(c, GF_EINVAL, "tol must be > 0 and max_iter >= 1");
+  DeviceGuard guard(c->device);
+  c->last_launches = 0;
+  const int S = c->n_sys;
+  const double inf = std::numeric_limits<double>::infinity();
+  std::vector<double> mu(mu_inout, mu_inout + S), lo(S, -inf), hi(S, inf), N(S), dN(S);
+  std::vector<double> best_mu(mu), best_f(S, inf);
+  std::vector<char> done(S, 0);
+  int it = 0;
+  int64_t launches = 0, points = 0;
+  for (; it < max_iter;) {
+    gf_status st = occupation_impl(c, mu.data(), N.data(), dN.data());
+    launches += c->last_launches;
+    points += c->last_points;
+    c->last_launches = 0;
+    ++it;
+    if (st) {
+      c->last_launches = launches;
+      return st;
+    }
+    bool all = true;
+    for (int s = 0; s < S; ++s) {
+      if (done[s]) continue;
+      const double f = N[s] - n_target[s];
+      if (std::fabs(f) < best_f[s]) { best_f[s] = std::fabs(f); best_mu[s] = mu[s]; }
+      if (std::fabs(f) <= tol) { done[s] = 1; continue; }
+      all = false;
+      if (f < 0) lo[s] = std::max(lo[s], mu[s]);
+      else hi[s] = std::min(hi[s], mu[s]);
+      // safeguarded Newton: N is increasing in mu, dN/dmu > 0
+      double step = (dN[s] > 1e-300) ? -f / dN[s] : (f < 0 ? 1.0 : -1.0);
+      const double cap = 4.0;  // eV: no wild jumps while the bracket is one-sided
+      if (!(std::isfinite(lo[s]) && std::isfinite(hi[s]))) step = std::max(-cap, std::min(cap, step));
+      double mn = mu[s] + step;
+      if (std::isfinite(lo[s]) && std::isfinite(hi[s])) {
+        if (!(mn > lo[s] && mn < hi[s])) mn = 0.5 * (lo[s] + hi[s]);
+        if (hi[s] - lo[s] <= 4e-16 * std::max(1.0, std::fabs(mu[s]))) { done[s] = 2; continue; }
+      }
+      mu[s] = mn;
+    }
+    if (all) break;
+  }
+  bool conv = true;
+  for (int s = 0; s < S; ++s) {
+    if (done[s] != 1) conv = false;
+    mu_inout[s] = done[s] == 1 ? mu[s] : best_mu[s];
+  }
+  if (iters_out) *iters_out = it;
+  c->last_launches = launches;
+  c->last_points = points;
+  if (!conv) return fail(c, GF_ENOTCONV, "mu search did not reach tol within max_iter");
+  return GF_OK;
+}
+
+gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) {
+  if (!c) return GF_EINVAL;
+  DeviceGuard guard(c->device);
+  c->last_launches = 0;
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  st = run_points(c, gf::kRho);
+  if (st) return st;
+  GF_CU(ensure(c->rho_out, sizeof(double2) * c->totH));
+  GF_CU(gf::launch_rho_finalize(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->H.as<double2>(),
+                                c->Einf.as<double2>(), c->P.as<double2>(), c->mu.as<double>(),
+                                c->rho_part.as<double2>(), c->totH, c->n_chunks, c->n_k,
+                                c->rho_out.as<double2>(), c->kN.as<double>(), c->kNc.as<double>(),
+                                c->stream));
+  GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                              c->kNc.as<double>(), c->kN.as<double>(), c->sysout.as<double>(),
+                              c->stream));
+  c->last_launches += 2;
+  if (rho_out)
+    GF_CU(cudaMemcpyAsync(rho_out, c->rho_out.p, sizeof(double2) * c->totH, cudaMemcpyDefault,
+                          c->stream));
+  GF_CU(cudaMemcpyAsync(c->hp_sys(), c->sysout.p, sizeof(double) * 2 * c->n_sys,
+                        cudaMemcpyDeviceToHost, c->stream));
+  st = sync_and_check(c);
+  if (st) return st;
+  if (n_corr_out)
+    for (int s = 0; s < c->n_sys; ++s) n_corr_out[s] = c->hp_sys()[2 * s];
+  return GF_OK;
+}
+
+gf_status gf_local(gf_ctx* c, const double* mu, void* gloc_out) {
+  if (!c) return GF_EINVAL;
+  if (!gloc_out) return fail(c, GF_EINVAL, "gloc_out_ptr is NULL");
+  DeviceGuard guard(c->device);
+  c->last_launches = 0;
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  st = run_points(c, gf::kGloc);
+  if (st) return st;
+  GF_CU(cudaMemcpyAsync(gloc_out, c->gacc.p, sizeof(double2) * c->totSig, cudaMemcpyDefault,
+                        c->stream));
+  return sync_and_check(c);
+}
+
+gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const double* nbar,
+                      void* sbar_out, double* mubar_out) {
+  if (!c) return GF_EINVAL;
+  if (!sbar_out || !mubar_out) return fail(c, GF_EINVAL, "sigma_bar_out_ptr or mu_bar_out is NULL");
+  DeviceGuard guard(c->device);
+  c->last_launches = 0;
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  bool any_nbar = false;
+  for (int s = 0; s < c->n_sys; ++s) {
+    const double v = nbar ? nbar[s] : 0.0;
+    if (!std::isfinite(v)) return fail(c, GF_EINVAL, "n_bar is not finite");
+    c->hp_nbar()[s] = v;
+    any_nbar = any_nbar || v != 0.0;
+  }
+  GF_CU(cudaMemcpyAsync(c->nbar.p, c->hp_nbar(), sizeof(double) * c->n_sys, cudaMemcpyHostToDevice,
+                        c->stream));
+  c->have_gbar_for_call = (gbar != nullptr);
+  if (gbar) {
+    GF_CU(ensure(c->gbar, sizeof(double2) * c->totSig));
+    GF_CU(cudaMemcpyAsync(c->gbar.p, gbar, sizeof(double2) * c->totSig, cudaMemcpyDefault, c->stream));
+  }
+  const int mode = gf::kAdj | (any_nbar ? gf::kOcc : 0);
+  st = run_points(c, mode);
+  if (st) return st;
+  GF_CU(gf::launch_mubar_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                                c->n_chunks, c->mubar_part.as<double>(), c->mubar_sys.as<double>(),
+                                c->stream));
+  c->last_launches += 1;
+  if (any_nbar) {
+    GF_CU(gf::launch_occ_finalize(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(),
+                                  c->trHE.as<double>(), c->mu.as<double>(), c->occ_part.as<double>(),
+                                  c->n_chunks, c->n_k, c->kN.as<double>(), c->kdN.as<double>(),
+                                  c->stream));
+    GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                                c->kN.as<double>(), c->kdN.as<double>(), c->sysout.as<double>(),
+                                c->stream));
+    c->last_launches += 2;
+    GF_CU(cudaMemcpyAsync(c->hp_sys(), c->sysout.p, sizeof(double) * 2 * c->n_sys,
+                          cudaMemcpyDeviceToHost, c->stream));
+  }
+  GF_CU(cudaMemcpyAsync(c->hp_mubar(), c->mubar_sys.p, sizeof(double) * c->n_sys,
+                        cudaMemcpyDeviceToHost, c->stream));
+  GF_CU(cudaMemcpyAsync(sbar_out, c->gacc.p, sizeof(double2) * c->totSig, cudaMemcpyDefault,
+                        c->stream));
+  st = sync_and_check(c);
+  if (st) return st;
+  for (int s = 0; s < c->n_sys; ++s) {
+    const double dn = any_nbar ? c->hp_sys()[2 * s + 1] : 0.0;
+    mubar_out[s] = c->hp_nbar()[s] * dn + c->hp_mubar()[s];
+  }
+  return GF_OK;
+}
+
+const char* gf_last_error(const gf_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+gf_status gf_last_stats(const gf_ctx* c, int64_t* launches, int64_t* points) {
+  if (!c) return GF_EINVAL;
+  if (launches) *launches = c->last_launches;
+  if (points) *points = c->last_points;
+  return GF_OK;
+}
+
+}  // extern "C"

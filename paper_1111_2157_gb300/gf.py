@@ -1,0 +1,261 @@
+"""Thin ctypes binding of libgf (include/gf.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+Arrays may be numpy arrays or torch tensors, on the host or on the context's
+device; outputs are torch tensors on the device unless an ``out`` is given.
+The library is loaded on first use; if it is missing the call fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libgf.so"
+_lib = None
+
+GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ESINGULAR, GF_ENOTCONV, GF_ETIMEOUT, GF_ESTATE = range(8)
+STATUS_NAMES = {0: "GF_OK", 1: "GF_EINVAL", 2: "GF_ENOMEM", 3: "GF_ECUDA", 4: "GF_ESINGULAR",
+                5: "GF_ENOTCONV", 6: "GF_ETIMEOUT", 7: "GF_ESTATE"}
+PRECISION = {"fp64": 0, "mixed": 1}
+DTYPE = {"c128": 0, "c64": 1}
+
+EXPORTS = ["gf_create", "gf_destroy", "gf_set_hamiltonian", "gf_set_projectors", "gf_set_sigma",
+           "gf_local", "gf_occupation", "gf_find_mu", "gf_density_matrix", "gf_backward",
+           "gf_last_error", "gf_last_stats"]
+
+
+class GFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GFDesc(ctypes.Structure):
+    _fields_ = [("n_systems", ctypes.c_int32), ("n_k", ctypes.c_int32),
+                ("nb", ctypes.POINTER(ctypes.c_int32)), ("nb_uniform", ctypes.c_int32),
+                ("k_system", ctypes.POINTER(ctypes.c_int32)),
+                ("m_system", ctypes.POINTER(ctypes.c_int32)), ("n_iw", ctypes.c_int32),
+                ("beta", ctypes.POINTER(ctypes.c_double)), ("k_weight", ctypes.POINTER(ctypes.c_double)),
+                ("precision", ctypes.c_int32), ("input_dtype", ctypes.c_int32),
+                ("tail_order", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+def load():
+    """Load libgf.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"{LIB_PATH.name} is not built: run `python -m paper_1111_2157_gb300.build` "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(str(LIB_PATH))
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    lib.gf_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(GFDesc)]
+    lib.gf_destroy.argtypes = [vp]
+    lib.gf_set_hamiltonian.argtypes = [vp, vp, ctypes.c_int32]
+    lib.gf_set_projectors.argtypes = [vp, vp]
+    lib.gf_set_sigma.argtypes = [vp, vp, vp]
+    lib.gf_local.argtypes = [vp, dp, vp]
+    lib.gf_occupation.argtypes = [vp, dp, dp, dp]
+    lib.gf_find_mu.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int32, dp, ip]
+    lib.gf_density_matrix.argtypes = [vp, dp, vp, dp]
+    lib.gf_backward.argtypes = [vp, dp, vp, dp, vp, dp]
+    lib.gf_last_error.argtypes = [vp]
+    lib.gf_last_error.restype = ctypes.c_char_p
+    lib.gf_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    for name in EXPORTS:
+        if name not in ("gf_last_error",):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _doubles(values, n):
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(values, dtype=np.float64), (n,)))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class _Arg:
+    """Pointer to array data (numpy or torch; host or device) kept alive for a call."""
+
+    def __init__(self, x, complex_dtype=None):
+        import torch
+        if isinstance(x, (list, tuple)):
+            x = np.concatenate([np.asarray(b).reshape(-1) for b in x])
+        if isinstance(x, torch.Tensor):
+            if complex_dtype is not None:
+                x = x.to(dtype=getattr(torch, complex_dtype))
+            self.obj = x.contiguous()
+            self.ptr = self.obj.data_ptr()
+        else:
+            arr = np.asarray(x)
+            if complex_dtype is not None:
+                arr = arr.astype(np.dtype(complex_dtype), copy=False)
+            self.obj = np.ascontiguousarray(arr)
+            self.ptr = self.obj.ctypes.data
+
+
+class GreensFunction:
+    """One libgf context: inputs live on the device, every call runs the CUDA path.
+
+    nb: int (uniform) or per-k sequence; m and beta: per system (scalars for one
+    system); k_system: per-k system index (non-decreasing) for several systems.
+    """
+
+    def __init__(self, nb, m, n_iw, beta, k_system=None, n_k=None, k_weight=None, precision="fp64",
+                 input_dtype="c128", tail_order=2, device=0, stream=None):
+        import torch
+        self.lib = load()
+        self.device = int(device)
+        self.input_dtype = input_dtype
+        m = np.atleast_1d(np.asarray(m, dtype=np.int32))
+        beta = np.atleast_1d(np.asarray(beta, dtype=np.float64))
+        n_sys = len(m)
+        if np.ndim(nb) == 0:
+            if n_k is None:
+                raise ValueError("n_k is required with a uniform nb")
+            nb_arr = None
+            self.nb = np.full(int(n_k), int(nb), np.int32)
+        else:
+            nb_arr = np.ascontiguousarray(nb, dtype=np.int32)
+            self.nb = nb_arr
+        n_k = len(self.nb)
+        ks = None if k_system is None else np.ascontiguousarray(k_system, dtype=np.int32)
+        self.k_system = np.zeros(n_k, np.int32) if ks is None else ks
+        self.m, self.beta, self.n_iw, self.n_sys, self.n_k = m, beta, int(n_iw), n_sys, n_k
+        kw = None if k_weight is None else np.ascontiguousarray(k_weight, dtype=np.float64)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream if torch.cuda.is_available() else 0
+        self._keep = [nb_arr, ks, m, beta, kw]
+        d = GFDesc()
+        d.n_systems, d.n_k = n_sys, n_k
+        d.nb = nb_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if nb_arr is not None else None
+        d.nb_uniform = int(self.nb[0])
+        d.k_system = ks.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if ks is not None else None
+        d.m_system = m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.n_iw = self.n_iw
+        d.beta = beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.k_weight = kw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if kw is not None else None
+        d.precision = PRECISION[precision]
+        d.input_dtype = DTYPE[input_dtype]
+        d.tail_order = int(tail_order)
+        d.device = self.device
+        d.stream = int(stream)
+        h = ctypes.c_void_p()
+        st = self.lib.gf_create(ctypes.byref(h), ctypes.byref(d))
+        if st != GF_OK:
+            raise GFError(st, self.lib.gf_last_error(None).decode())
+        self.h = h
+        msys = self.m[self.k_system]
+        self.tot_h = int(np.sum(self.nb.astype(np.int64) ** 2))
+        self.tot_p = int(np.sum(msys.astype(np.int64) * self.nb))
+        self.tot_sig = int(np.sum(self.n_iw * self.m.astype(np.int64) ** 2))
+        self.tot_sinf = int(np.sum(self.m.astype(np.int64) ** 2))
+
+    @classmethod
+    def for_systems(cls, systems, precision="fp64", input_dtype="c128", tail_order=2, device=0):
+        """Context for a list of ``synth.System`` (one or several, ragged or not)."""
+        nb = np.concatenate([s.nb for s in systems])
+        ks = np.concatenate([np.full(s.nk, i, np.int32) for i, s in enumerate(systems)])
+        n_iw = systems[0].n_iw
+        return cls(nb, [s.m for s in systems], n_iw, [s.beta for s in systems],
+                   k_system=ks if len(systems) > 1 else None, precision=precision,
+                   input_dtype=input_dtype, tail_order=tail_order, device=device)
+
+    def _check(self, st):
+        if st != GF_OK:
+            raise GFError(st, self.lib.gf_last_error(self.h).decode())
+
+    def _cdt(self):
+        return "complex128" if self.input_dtype == "c128" else "complex64"
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, n, out):
+        import torch
+        if out is None:
+            out = torch.empty(n, dtype=torch.complex128, device=f"cuda:{self.device}")
+        return out
+
+    # ---------------------------------------------------------------- inputs
+    def set_hamiltonian(self, H, diagonal=False):
+        a = _Arg(H, self._cdt())
+        self._check(self.lib.gf_set_hamiltonian(self.h, a.ptr, 1 if diagonal else 0))
+
+    def set_projectors(self, P):
+        a = _Arg(P, self._cdt())
+        self._check(self.lib.gf_set_projectors(self.h, a.ptr))
+
+    def set_sigma(self, sigma, sigma_inf):
+        a, b = _Arg(sigma, self._cdt()), _Arg(sigma_inf, self._cdt())
+        self._check(self.lib.gf_set_sigma(self.h, a.ptr, b.ptr))
+
+    # --------------------------------------------------------------- compute
+    def local(self, mu, out=None):
+        """G_loc packed per system [n_iw][m][m], complex128."""
+        _, mp = _doubles(mu, self.n_sys)
+        out = self._out(self.tot_sig, out)
+        o = _Arg(out)
+        self._check(self.lib.gf_local(self.h, mp, ctypes.c_void_p(o.ptr)))
+        return out
+
+    def occupation(self, mu):
+        """(N, dN/dmu) per system."""
+        keep, mp = _doubles(mu, self.n_sys)
+        n, d = np.zeros(self.n_sys), np.zeros(self.n_sys)
+        self._check(self.lib.gf_occupation(self.h, mp, n.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return n, d
+
+    def find_mu(self, n_target, mu0=0.0, tol=1e-10, max_iter=60):
+        """mu per system with |N - n_target| <= tol; returns (mu, evaluations)."""
+        _, tp = _doubles(n_target, self.n_sys)
+        mu = np.ascontiguousarray(np.broadcast_to(np.asarray(mu0, np.float64), (self.n_sys,))).copy()
+        it = ctypes.c_int32()
+        self._check(self.lib.gf_find_mu(self.h, tp, float(tol), int(max_iter),
+                                        mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.byref(it)))
+        return mu, it.value
+
+    def density_matrix(self, mu, out=None, want_rho=True):
+        """(rho packed per k [N_b][N_b] complex128 or None, n_corr per system)."""
+        _, mp = _doubles(mu, self.n_sys)
+        nc = np.zeros(self.n_sys)
+        o = _Arg(self._out(self.tot_h, out)) if want_rho else None
+        self._check(self.lib.gf_density_matrix(self.h, mp, ctypes.c_void_p(o.ptr if o else 0),
+                                               nc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return (o.obj if o else None), nc
+
+    def backward(self, mu, gloc_bar=None, n_bar=None, out=None):
+        """(Sigma_bar packed like Sigma, complex128; mu_bar per system)."""
+        _, mp = _doubles(mu, self.n_sys)
+        gb = _Arg(gloc_bar, "complex128") if gloc_bar is not None else None
+        nb_keep = None
+        nbp = None
+        if n_bar is not None:
+            nb_keep, nbp = _doubles(n_bar, self.n_sys)
+        out = self._out(self.tot_sig, out)
+        o = _Arg(out)
+        mub = np.zeros(self.n_sys)
+        self._check(self.lib.gf_backward(self.h, mp, ctypes.c_void_p(gb.ptr if gb else 0), nbp,
+                                         ctypes.c_void_p(o.ptr),
+                                         mub.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out, mub
+
+    def stats(self):
+        """(kernel launches, (k, i w_n) points) of the last compute call."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.gf_last_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value

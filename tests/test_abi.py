@@ -1,0 +1,83 @@
+"""The C-ABI library loads and exports every entry point include/gf.h declares (no GPU needed)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_1111_2157_gb300 import build as gfbuild
+from paper_1111_2157_gb300 import gf
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def declared_symbols():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = h.read_text()
+        names |= set(re.findall(r"^\s*(?:gf_status|const char \*)\s*(gf_\w+)\s*\(", text, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gfbuild.build()
+    return gf.load()
+
+
+def test_header_declares_the_boundary():
+    want = {"gf_create", "gf_destroy", "gf_set_hamiltonian", "gf_set_projectors", "gf_set_sigma",
+            "gf_local", "gf_occupation", "gf_find_mu", "gf_density_matrix", "gf_backward",
+            "gf_last_error"}
+    assert want <= declared_symbols()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in sorted(declared_symbols()):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_python_binding_names_match_header():
+    assert set(gf.EXPORTS) == declared_symbols()
+
+
+def _desc(**kw):
+    m = (ctypes.c_int32 * 1)(5)
+    beta = (ctypes.c_double * 1)(40.0)
+    d = gf.GFDesc()
+    d.n_systems, d.n_k, d.nb, d.nb_uniform = 1, 4, None, 8
+    d.k_system, d.m_system, d.n_iw, d.beta, d.k_weight = None, m, 16, beta, None
+    d.precision, d.input_dtype, d.tail_order, d.device, d.stream = 0, 0, 2, 0, None
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d, (m, beta)
+
+
+@pytest.mark.parametrize("field,value", [("n_systems", 0), ("n_k", 0), ("n_iw", 0),
+                                         ("nb_uniform", 0), ("tail_order", 3), ("precision", 7),
+                                         ("input_dtype", 5)])
+def test_create_rejects_invalid_descriptor(lib, field, value):
+    d, keep = _desc(**{field: value})
+    h = ctypes.c_void_p()
+    st = lib.gf_create(ctypes.byref(h), ctypes.byref(d))
+    assert st == gf.GF_EINVAL
+    assert not h.value
+    assert lib.gf_last_error(None).decode()
+
+
+def test_create_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.gf_create(ctypes.byref(h), None) == gf.GF_EINVAL
+    assert lib.gf_create(None, None) == gf.GF_EINVAL
+    assert lib.gf_destroy(None) == gf.GF_OK
+
+
+def test_no_cpu_fallback_without_device(lib):
+    """Without a usable GPU the library refuses to create a context (no CPU path exists)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    d, keep = _desc()
+    h = ctypes.c_void_p()
+    assert lib.gf_create(ctypes.byref(h), ctypes.byref(d)) == gf.GF_ECUDA
+    assert not h.value
