@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the lattice Green's function step on one GB300.
+
+Workload: the Ce-like f-system (N_k = 1000 k-points, band window N_b = 40,
+m = 14 correlated orbitals, 1024 positive Matsubara frequencies at beta = 100,
+U = 6 eV), seeded synthetic inputs, FP64 path.
+
+One step is one pass of the whole hot path over the workload, as a DMFT
+iteration needs it:
+  1. mu search: Newton from mu = 0 on N(mu) (each evaluation embeds and inverts
+     every G(k, i w_n) and sums the Matsubara series),
+  2. one fused pass at mu*: G_loc, rho_k, N, dN/dmu, n_corr,
+  3. the adjoint at mu*: Sigma_bar and mu_bar for a seeded G_loc_bar and N_bar = 1.
+value = (k, i w_n) points evaluated per second (every pass counts its points).
+
+``--impl reference`` times the FP64 CPU oracle (the plain definition, one LU
+inverse per point) on the host cores instead, on a bounded sample of the same
+workload, and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "(k,iω_n) G points/s & % FP64/TF32 peak; mixed vs plain FP64 GPU at 1e-7 N(μ)"
+UNIT = "points/s"
+WORKLOAD = "ce_like: N_k=1000, N_b=40, m=14, N_w=1024, beta=100 1/eV, U=6 eV, dense H, two-pole Sigma"
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+PROFILES = ROOT / "profiles"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target duration of the bounded CPU-oracle sample")
+    ap.add_argument("--nk", type=int, default=None,
+                    help="smaller k-set of the same workload (profiling captures only)")
+    ap.add_argument("--n-iw", type=int, default=None,
+                    help="fewer Matsubara frequencies (profiling captures only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.TemporaryFile(mode="w+")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power), "reasons": sorted(reasons)}
+
+
+def ncu_traffic():
+    """dram bytes per launch of the point kernel from the committed ncu summary (or None)."""
+    f = PROFILES / "point_fp64_ce_like.md"
+    if not f.exists():
+        return None
+    for line in f.read_text().splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_calibrate(system, mu):
+    """Seconds per k-point of the FP64 oracle's Matsubara-sum pass (all frequencies)."""
+    import oracle
+    o = oracle.get()
+    o.set_threads(cpu_cores())
+    s = system
+    kc = min(s.nk, o.get_threads())
+    w = np.full(s.nk, 1.0 / s.nk)
+    t0 = time.perf_counter()
+    o.density(s.H[:kc], s.P[:kc], s.sigma, s.sigma_inf, s.beta, mu, weights=w[:kc], want_rho=False)
+    return max(time.perf_counter() - t0, 1e-6) / kc
+
+
+def oracle_sample(system, mu, seconds):
+    """Time the FP64 oracle's Matsubara-sum pass on the first K k-points (K sized to ~seconds)."""
+    import oracle
+    o = oracle.get()
+    s = system
+    per_k = oracle_calibrate(s, mu)
+    thr = o.get_threads()
+    k = int(min(s.nk, max(thr, int(seconds / per_k) // thr * thr)))
+    w = np.full(s.nk, 1.0 / s.nk)
+    t0 = time.perf_counter()
+    o.density(s.H[:k], s.P[:k], s.sigma, s.sigma_inf, s.beta, mu, weights=w[:k], want_rho=False)
+    dt = time.perf_counter() - t0
+    pts = k * s.n_iw
+    return {"value": pts / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{k} of {s.nk} k-points x all {s.n_iw} frequencies, one Matsubara-sum "
+                      f"pass (LU inverse per point, N and dN/dmu) at fixed mu, {dt:.1f} s"}, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1111_2157_gb300 import synth
+    s = synth.ce_like().systems[0]
+    import oracle
+    o = oracle.get()
+    o.set_threads(cpu_cores())
+    per_step = max(2.0, min(10.0, 100.0 / max(1, args.steps + args.warmup)))
+    per_k = oracle_calibrate(s, 0.0)
+    thr = o.get_threads()
+    k = int(min(s.nk, max(thr, int(per_step / per_k) // thr * thr)))
+    w = np.full(s.nk, 1.0 / s.nk)
+    for _ in range(args.warmup):
+        o.density(s.H[:k], s.P[:k], s.sigma, s.sigma_inf, s.beta, 0.0, weights=w[:k], want_rho=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.density(s.H[:k], s.P[:k], s.sigma, s.sigma_inf, s.beta, 0.0, weights=w[:k], want_rho=False)
+    dt = time.perf_counter() - t0
+    value = args.steps * k * s.n_iw / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": f"oracle Matsubara-sum pass over {k} k-points x "
+                                                     f"{s.n_iw} frequencies at mu=0 (bounded sample)",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.get_threads(), "kind": "oracle",
+                             "sample": f"{k} of {s.nk} k-points x all {s.n_iw} frequencies per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    from paper_1111_2157_gb300 import build as gfbuild
+    if not gfbuild.LIB.exists():
+        gfbuild.build()
+    from paper_1111_2157_gb300 import gf, synth
+
+    kw = {}
+    if args.nk:
+        kw["nk"] = args.nk
+    if args.n_iw:
+        kw["n_iw"] = args.n_iw
+    s = synth.ce_like(**kw).systems[0]
+    nk, nb, m, n_iw = s.nk, 40, s.m, s.n_iw
+    dev = torch.device(f"cuda:{local}")
+    g = gf.GreensFunction(nb, m, n_iw, s.beta, n_k=nk, device=local)
+    H_d = torch.from_numpy(s.H).to(dev)
+    P_d = torch.from_numpy(s.P).to(dev)
+    S_d = torch.from_numpy(s.sigma).to(dev)
+    Si_d = torch.from_numpy(s.sigma_inf).to(dev)
+    rng = np.random.default_rng(2157)
+    gbar_h = (rng.standard_normal(s.sigma.shape) + 1j * rng.standard_normal(s.sigma.shape)) * 1e-3
+    gbar_d = torch.from_numpy(gbar_h).to(dev)
+    g.set_hamiltonian(H_d)
+    g.set_projectors(P_d)
+    g.set_sigma(S_d, Si_d)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    gloc_d = torch.empty(g.tot_sig, dtype=torch.complex128, device=dev)
+    rho_d = torch.empty(g.tot_h, dtype=torch.complex128, device=dev)
+    sbar_d = torch.empty(g.tot_sig, dtype=torch.complex128, device=dev)
+    totals = {"launches": 0, "points": 0, "kernel_ms": 0.0, "flops": 0.0}
+    passes = {name: {"kernel_ms": 0.0, "flops": 0.0, "launches": 0}
+              for name in ("find_mu", "evaluate", "backward")}
+
+    def acc(name):
+        st = g.stats()
+        for k in totals:
+            totals[k] += st[k]
+        passes[name]["kernel_ms"] += st["kernel_ms"]
+        passes[name]["flops"] += st["flops"]
+        passes[name]["launches"] += 1
+
+    info = {}
+
+    def step():
+        mu, it = g.find_mu([s.n_target], 0.0, tol=1e-10, max_iter=60)
+        acc("find_mu")
+        out = g.evaluate(mu, gloc_out=gloc_d, rho_out=rho_d)
+        acc("evaluate")
+        g.backward(mu, gloc_bar=gbar_d, n_bar=[1.0], out=sbar_d)
+        acc("backward")
+        info["mu"], info["iters"], info["N"] = float(mu[0]), it, float(out["N"][0])
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    for k in totals:
+        totals[k] = 0 if k in ("launches", "points") else 0.0
+    for v in passes.values():
+        v.update(kernel_ms=0.0, flops=0.0, launches=0)
+
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        step()
+        if i + 1 < args.steps:
+            flush.zero_()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+        torch.distributed.barrier()
+    points_all = totals["points"] * ws
+    value = points_all / elapsed
+    achieved = totals["flops"] / (totals["kernel_ms"] / 1e3) / 1e12
+
+    e2e = None
+    if not args.no_e2e:
+        # Same step through the public API with HOST buffers: inputs copied in and
+        # outputs copied out inside the timed region, every step.
+        H_h = torch.from_numpy(s.H).pin_memory()
+        P_h = torch.from_numpy(s.P).pin_memory()
+        S_h = torch.from_numpy(s.sigma).pin_memory()
+        Si_h = torch.from_numpy(s.sigma_inf).pin_memory()
+        gb_h = torch.from_numpy(gbar_h).pin_memory()
+        gloc_h = torch.empty(g.tot_sig, dtype=torch.complex128).pin_memory()
+        rho_h = torch.empty(g.tot_h, dtype=torch.complex128).pin_memory()
+        sbar_h = torch.empty(g.tot_sig, dtype=torch.complex128).pin_memory()
+        e2e_steps = max(1, min(args.steps, 2))
+        pts = 0
+
+        def step_host():
+            g.set_hamiltonian(H_h)
+            g.set_projectors(P_h)
+            g.set_sigma(S_h, Si_h)
+            mu, _ = g.find_mu([s.n_target], 0.0, tol=1e-10, max_iter=60)
+            p = g.stats()["points"]
+            g.evaluate(mu, gloc_out=gloc_h, rho_out=rho_h)
+            p += g.stats()["points"]
+            g.backward(mu, gloc_bar=gb_h, n_bar=[1.0], out=sbar_h)
+            p += g.stats()["points"]
+            return p
+
+        step_host()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pts += step_host()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([te], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = sum(x.numel() * x.element_size() for x in (H_h, P_h, S_h, Si_h, gb_h))
+        d2h = sum(x.numel() * x.element_size() for x in (gloc_h, rho_h, sbar_h))
+        e2e = {"value": pts * ws / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu, _ = oracle_sample(s, info["mu"], args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "step": "find_mu (Newton from mu=0, tol 1e-10) + fused G_loc/rho_k/N/dN/n_corr "
+                               "pass + adjoint (Sigma_bar, mu_bar)",
+                       "precision": "fp64", "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "points_per_step": totals["points"] // args.steps,
+                       "mu_evaluations_per_step": info["iters"], "mu_star": info["mu"],
+                       "N_at_mu_star": info["N"]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": ncu_traffic(), "kernel": "k_point_fp64",
+                         "peak_source": "FP64 DFMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz",
+                         "kernel_share_of_step": totals["kernel_ms"] / 1e3 / elapsed,
+                         "by_pass_tflops": {k: v["flops"] / max(v["kernel_ms"], 1e-9) / 1e9
+                                            for k, v in passes.items()},
+                         "by_pass_ms_per_step": {k: v["kernel_ms"] / args.steps
+                                                 for k, v in passes.items()}},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": totals["launches"], "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

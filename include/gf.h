@@ -127,6 +127,14 @@ gf_status gf_find_mu(gf_ctx *ctx, const double *n_target, double tol, int32_t ma
  * Errors: GF_ESTATE, GF_ESINGULAR, GF_EINVAL, GF_ECUDA. */
 gf_status gf_density_matrix(gf_ctx *ctx, const double *mu, void *rho_out_ptr, double *n_corr_out);
 
+/* One fused pass over every (k, i w_n) point at mu[s]: any subset of G_loc
+ * (as gf_local), rho_k (as gf_density_matrix), N and dN/dmu (as gf_occupation)
+ * and n_corr; NULL outputs are not computed.  Each G(k, i w_n) is formed and
+ * inverted once for all requested outputs.
+ * Errors: GF_ESTATE, GF_ESINGULAR, GF_EINVAL (all outputs NULL), GF_ECUDA. */
+gf_status gf_evaluate(gf_ctx *ctx, const double *mu, void *gloc_out_ptr, void *rho_out_ptr,
+                      double *n_out, double *dn_dmu_out, double *n_corr_out);
+
 /* Vector-Jacobian product (not in the paper; derived from Eq. dmftloop1 with
  * dG = G P^+ dSigma P G and dG/dmu = -G^2).  For a real loss L with
  * dL = Re<gloc_bar, dG_loc> + n_bar . dN, and the convention
@@ -145,8 +153,14 @@ gf_status gf_backward(gf_ctx *ctx, const double *mu, const void *gloc_bar_ptr, c
  * context, valid until the next call on it. */
 const char *gf_last_error(const gf_ctx *ctx);
 
-/* Counters of the last compute call: kernel launches and (k, i w_n) points. */
-gf_status gf_last_stats(const gf_ctx *ctx, int64_t *kernel_launches, int64_t *points);
+/* Counters of the last compute call (any pointer may be NULL): kernel launches
+ * of this library, (k, i w_n) points evaluated, the summed duration of the
+ * point-kernel launches in milliseconds (CUDA events recorded on the context's
+ * stream around each launch), and their algorithmic floating-point operations
+ * (8 per complex multiply-add: N_b^3 for the inverse, m^2 N_b + m N_b^2 for the
+ * embedding, plus the epilogue's projections and traces). */
+gf_status gf_last_stats(const gf_ctx *ctx, int64_t *kernel_launches, int64_t *points,
+                        double *point_kernel_ms, double *point_flops);
 
 #ifdef __cplusplus
 }

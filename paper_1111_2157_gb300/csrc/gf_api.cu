@@ -89,18 +89,23 @@ struct gf_ctx {
   std::vector<int> batch_k0, batch_item0;  // batch b: k in [batch_k0[b], batch_k0[b+1])
   DevBuf H, P, Sig, Sinf, Einf, trHE, kinfo_d, sinfo_d, items_d, offD_d, mu, nbar, gbar, status,
       queue, stage, occ_part, rho_part, rho_out, gq, kN, kdN, kNc, sysout, a_scratch, mubar_part,
-      mubar_sys, gacc;
+      mubar_sys, gacc, sysout2;
   bool have_H = false, have_P = false, have_S = false, einf_dirty = true;
   bool have_gbar_for_call = false;
-  // pinned host staging: mu [S] | n_bar [S] | status | per-system outputs [2S] | mu_bar [S]
+  // pinned host staging: mu [S] | n_bar [S] | status | outputs [2S] | mu_bar [S] | outputs [2S]
   double* hpin = nullptr;
   double* hp_mu() { return hpin; }
   double* hp_nbar() { return hpin + n_sys; }
   double* hp_status() { return hpin + 2 * n_sys; }
   double* hp_sys() { return hpin + 2 * n_sys + 1; }
   double* hp_mubar() { return hpin + 4 * n_sys + 1; }
+  double* hp_sys2() { return hpin + 5 * n_sys + 1; }
   std::string err;
   int64_t last_launches = 0, last_points = 0;
+  double last_kernel_ms = 0.0, last_flops = 0.0;
+  // CUDA event pairs around the point-kernel launches of the current call
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
 };
 
 namespace {
@@ -135,6 +140,12 @@ gf_status load_complex(gf_ctx* c, const void* src, int64_t n, double2* dst) {
 gf_status sync_and_check(gf_ctx* c) {
   GF_CU(cudaMemcpyAsync(c->hp_status(), c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   GF_CU(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    GF_CU(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+    c->last_kernel_ms += ms;
+  }
+  c->ev_used = 0;
   int flags = 0;
   std::memcpy(&flags, c->hp_status(), sizeof(int));
   if (flags & gf::kFlagSingular)
@@ -168,6 +179,19 @@ gf_status upload_mu(gf_ctx* c, const double* mu) {
   GF_CU(cudaMemcpyAsync(c->mu.p, c->hp_mu(), sizeof(double) * c->n_sys, cudaMemcpyHostToDevice,
                         c->stream));
   return GF_OK;
+}
+
+// Algorithmic floating-point operations of one (k, i w_n) point (8 per complex
+// multiply-add, 2 per complex add or real product pair).
+double point_flops(int N, int M, int mode) {
+  const double n = N, m = M;
+  double cmac = n * n * n + m * m * n + m * n * n;  // inverse + embedding
+  double f = 0.0;
+  if (mode & gf::kOcc) f += 2.0 * n * n + 2.0 * n;  // Re Tr G^2, Re Tr G
+  if (mode & gf::kRho) f += 2.0 * n * n;            // S += G
+  if (mode & (gf::kGloc | gf::kAdj)) cmac += m * n * n + m * m * n;  // Y = G P^+, P Y
+  if (mode & gf::kAdj) cmac += m * n * n + m * m * n + 2.0 * m * m * m;  // Z = P G, Z Y, A^+ Gbar A^+
+  return 8.0 * cmac + f;
 }
 
 // Run the point kernel over every (k, chunk) item with the given mode.  For
@@ -247,7 +271,15 @@ gf_status run_points(gf_ctx* c, int mode) {
     p.items = c->items_d.as<Item>() + i0;
     p.n_items = i1 - i0;
     GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
+    while ((int)c->ev.size() < c->ev_used + 2) {
+      cudaEvent_t e;
+      GF_CU(cudaEventCreate(&e));
+      c->ev.push_back(e);
+    }
+    GF_CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
     GF_CU(gf::launch_point_fp64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
+    GF_CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+    c->ev_used += 2;
     c->last_launches += 1;
     if (kred) {
       int max_total = 0;
@@ -257,10 +289,22 @@ gf_status run_points(gf_ctx* c, int mode) {
                                  c->gacc.as<double2>(), c->stream));
       c->last_launches += 1;
     }
-    for (int i = i0; i < i1; ++i) points += c->items[i].n1 - c->items[i].n0;
+    for (int i = i0; i < i1; ++i) {
+      const Item& it = c->items[i];
+      points += it.n1 - it.n0;
+      c->last_flops += (it.n1 - it.n0) * point_flops(c->nb[it.k], c->msys[c->ksys[it.k]], mode);
+    }
   }
-  c->last_points = points;
+  c->last_points += points;
   return GF_OK;
+}
+
+void reset_stats(gf_ctx* c) {
+  c->last_launches = 0;
+  c->last_points = 0;
+  c->last_kernel_ms = 0.0;
+  c->last_flops = 0.0;
+  c->ev_used = 0;
 }
 
 gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
@@ -456,10 +500,11 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
     if ((e = ensure(c->mu, sizeof(double) * c->n_sys))) return e;
     if ((e = ensure(c->nbar, sizeof(double) * c->n_sys))) return e;
     if ((e = ensure(c->mubar_sys, sizeof(double) * c->n_sys))) return e;
+    if ((e = ensure(c->sysout2, sizeof(double) * 2 * c->n_sys))) return e;
     if ((e = ensure(c->sysout, sizeof(double) * 2 * c->n_sys))) return e;
     if ((e = ensure(c->status, sizeof(int)))) return e;
     if ((e = ensure(c->queue, sizeof(int)))) return e;
-    if ((e = cudaMallocHost(&c->hpin, sizeof(double) * (8 + 5 * (size_t)c->n_sys)))) return e;
+    if ((e = cudaMallocHost(&c->hpin, sizeof(double) * (8 + 7 * (size_t)c->n_sys)))) return e;
     if ((e = cudaMemcpyAsync(c->kinfo_d.p, c->kinfo.data(), sizeof(KInfo) * c->n_k,
                              cudaMemcpyHostToDevice, c->stream)))
       return e;
@@ -492,8 +537,10 @@ gf_status gf_destroy(gf_ctx* c) {
   DevBuf* bufs[] = {&c->H, &c->P, &c->Sig, &c->Sinf, &c->Einf, &c->trHE, &c->kinfo_d, &c->sinfo_d,
                     &c->items_d, &c->offD_d, &c->mu, &c->nbar, &c->gbar, &c->status, &c->queue,
                     &c->stage, &c->occ_part, &c->rho_part, &c->rho_out, &c->gq, &c->kN, &c->kdN,
-                    &c->kNc, &c->sysout, &c->a_scratch, &c->mubar_part, &c->mubar_sys, &c->gacc};
+                    &c->kNc, &c->sysout, &c->a_scratch, &c->mubar_part, &c->mubar_sys, &c->gacc,
+                    &c->sysout2};
   for (DevBuf* b : bufs) release(*b);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->hpin) cudaFreeHost(c->hpin);
   delete c;
   return GF_OK;
@@ -558,7 +605,7 @@ gf_status gf_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_o
   if (!c) return GF_EINVAL;
   if (!n_out) return fail(c, GF_EINVAL, "n_out is NULL");
   DeviceGuard guard(c->device);
-  c->last_launches = 0;
+  reset_stats(c);
   return occupation_impl(c, mu, n_out, dn_out);
 }
 
@@ -568,24 +615,17 @@ gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_
   if (!n_target || !mu_inout) return fail(c, GF_EINVAL, "n_target or mu_inout is NULL");
   if (!(tol > 0.0) || max_iter < 1) return fail(c, GF_EINVAL, "tol must be > 0 and max_iter >= 1");
   DeviceGuard guard(c->device);
-  c->last_launches = 0;
+  reset_stats(c);
   const int S = c->n_sys;
   const double inf = std::numeric_limits<double>::infinity();
   std::vector<double> mu(mu_inout, mu_inout + S), lo(S, -inf), hi(S, inf), N(S), dN(S);
   std::vector<double> best_mu(mu), best_f(S, inf);
   std::vector<char> done(S, 0);
   int it = 0;
-  int64_t launches = 0, points = 0;
   for (; it < max_iter;) {
-    gf_status st = occupation_impl(c, mu.data(), N.data(), dN.data());
-    launches += c->last_launches;
-    points += c->last_points;
-    c->last_launches = 0;
+    gf_status st = occupation_impl(c, mu.data(), N.data(), dN.data());  // stats accumulate
     ++it;
-    if (st) {
-      c->last_launches = launches;
-      return st;
-    }
+    if (st) return st;
     bool all = true;
     for (int s = 0; s < S; ++s) {
       if (done[s]) continue;
@@ -614,8 +654,6 @@ gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_
     mu_inout[s] = done[s] == 1 ? mu[s] : best_mu[s];
   }
   if (iters_out) *iters_out = it;
-  c->last_launches = launches;
-  c->last_points = points;
   if (!conv) return fail(c, GF_ENOTCONV, "mu search did not reach tol within max_iter");
   return GF_OK;
 }
@@ -623,7 +661,7 @@ gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_
 gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) {
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
-  c->last_launches = 0;
+  reset_stats(c);
   gf_status st = upload_mu(c, mu);
   if (st) return st;
   st = run_points(c, gf::kRho);
@@ -654,7 +692,7 @@ gf_status gf_local(gf_ctx* c, const double* mu, void* gloc_out) {
   if (!c) return GF_EINVAL;
   if (!gloc_out) return fail(c, GF_EINVAL, "gloc_out_ptr is NULL");
   DeviceGuard guard(c->device);
-  c->last_launches = 0;
+  reset_stats(c);
   gf_status st = upload_mu(c, mu);
   if (st) return st;
   st = run_points(c, gf::kGloc);
@@ -664,12 +702,67 @@ gf_status gf_local(gf_ctx* c, const double* mu, void* gloc_out) {
   return sync_and_check(c);
 }
 
+gf_status gf_evaluate(gf_ctx* c, const double* mu, void* gloc_out, void* rho_out, double* n_out,
+                      double* dn_out, double* n_corr_out) {
+  if (!c) return GF_EINVAL;
+  const int mode = (gloc_out ? gf::kGloc : 0) | ((rho_out || n_corr_out) ? gf::kRho : 0) |
+                   ((n_out || dn_out) ? gf::kOcc : 0);
+  if (!mode) return fail(c, GF_EINVAL, "every output of gf_evaluate is NULL");
+  DeviceGuard guard(c->device);
+  reset_stats(c);
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  st = run_points(c, mode);
+  if (st) return st;
+  if (mode & gf::kOcc) {
+    GF_CU(gf::launch_occ_finalize(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(),
+                                  c->trHE.as<double>(), c->mu.as<double>(), c->occ_part.as<double>(),
+                                  c->n_chunks, c->n_k, c->kN.as<double>(), c->kdN.as<double>(),
+                                  c->stream));
+    GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                                c->kN.as<double>(), c->kdN.as<double>(), c->sysout.as<double>(),
+                                c->stream));
+    c->last_launches += 2;
+    GF_CU(cudaMemcpyAsync(c->hp_sys(), c->sysout.p, sizeof(double) * 2 * c->n_sys,
+                          cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (mode & gf::kRho) {
+    GF_CU(ensure(c->rho_out, sizeof(double2) * c->totH));
+    GF_CU(gf::launch_rho_finalize(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->H.as<double2>(),
+                                  c->Einf.as<double2>(), c->P.as<double2>(), c->mu.as<double>(),
+                                  c->rho_part.as<double2>(), c->totH, c->n_chunks, c->n_k,
+                                  c->rho_out.as<double2>(), c->kN.as<double>(), c->kNc.as<double>(),
+                                  c->stream));
+    GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                                c->kNc.as<double>(), c->kN.as<double>(), c->sysout2.as<double>(),
+                                c->stream));
+    c->last_launches += 2;
+    GF_CU(cudaMemcpyAsync(c->hp_sys2(), c->sysout2.p, sizeof(double) * 2 * c->n_sys,
+                          cudaMemcpyDeviceToHost, c->stream));
+    if (rho_out)
+      GF_CU(cudaMemcpyAsync(rho_out, c->rho_out.p, sizeof(double2) * c->totH, cudaMemcpyDefault,
+                            c->stream));
+  }
+  if (gloc_out)
+    GF_CU(cudaMemcpyAsync(gloc_out, c->gacc.p, sizeof(double2) * c->totSig, cudaMemcpyDefault,
+                          c->stream));
+  st = sync_and_check(c);
+  if (st) return st;
+  for (int s = 0; s < c->n_sys; ++s) {
+    if (n_out) n_out[s] = c->hp_sys()[2 * s];
+    if (dn_out) dn_out[s] = c->hp_sys()[2 * s + 1];
+  }
+  if (n_corr_out)
+    for (int s = 0; s < c->n_sys; ++s) n_corr_out[s] = c->hp_sys2()[2 * s];
+  return GF_OK;
+}
+
 gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const double* nbar,
                       void* sbar_out, double* mubar_out) {
   if (!c) return GF_EINVAL;
   if (!sbar_out || !mubar_out) return fail(c, GF_EINVAL, "sigma_bar_out_ptr or mu_bar_out is NULL");
   DeviceGuard guard(c->device);
-  c->last_launches = 0;
+  reset_stats(c);
   gf_status st = upload_mu(c, mu);
   if (st) return st;
   bool any_nbar = false;
@@ -723,10 +816,13 @@ const char* gf_last_error(const gf_ctx* c) {
   return c->err.c_str();
 }
 
-gf_status gf_last_stats(const gf_ctx* c, int64_t* launches, int64_t* points) {
+gf_status gf_last_stats(const gf_ctx* c, int64_t* launches, int64_t* points, double* kernel_ms,
+                        double* flops) {
   if (!c) return GF_EINVAL;
   if (launches) *launches = c->last_launches;
   if (points) *points = c->last_points;
+  if (kernel_ms) *kernel_ms = c->last_kernel_ms;
+  if (flops) *flops = c->last_flops;
   return GF_OK;
 }
 

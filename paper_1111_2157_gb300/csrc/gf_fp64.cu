@@ -147,27 +147,23 @@ __device__ void gauss_jordan_fp64(double2* A, int N, int ld, double2* col, doubl
     }
     for (int i = tid; i < N; i += kThreads) col[i] = (i == pr) ? A[j * ld + j] : A[i * ld + j];
     __syncthreads();
-    // Eliminate column j from every other row; column j receives the inverse's entries.
+    // Eliminate column j from every other row; column j receives the inverse's
+    // entries.  One branch-free update a' = a - l u for every element: row j takes
+    // l = 0, a = urow (so a' = urow), column j takes a = 0 (so a' = -l r, since
+    // urow[j] = r).  The selects keep divergent FP64 paths out of the warps.
     const int total = N * N;
     int i = tid / N, c = tid - (tid / N) * N;
     const int di = kThreads / N, dc = kThreads - (kThreads / N) * N;
+    const double2 zero = make_double2(0.0, 0.0);
     for (int e = tid; e < total; e += kThreads) {
       double2* a = &A[i * ld + c];
-      if (i == j) {
-        *a = urow[c];
-      } else {
-        const double2 l = col[i];
-        if (c == j) {
-          const double2 q = cmul(l, r);
-          *a = make_double2(-q.x, -q.y);
-        } else {
-          const double2 u = urow[c];
-          double2 v = *a;
-          v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
-          v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
-          *a = v;
-        }
-      }
+      const double2 u = urow[c];
+      const double2 l = (i == j) ? zero : col[i];
+      const double2 a0 = *a;
+      double2 v = (i == j) ? u : ((c == j) ? zero : a0);
+      v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
+      v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
+      *a = v;
       i += di; c += dc;
       if (c >= N) { c -= N; ++i; }
     }
@@ -237,14 +233,16 @@ __global__ void __launch_bounds__(kThreads) k_point_fp64(const PointParams p) {
         sT[e] = acc;
       }
       __syncthreads();
-      // A = (i w_n + mu) I - H_k - P_k^+ T
+      // A = (i w_n + mu) I - H_k - P_k^+ T, accumulated as d - H - sum_a conj(P_ai) T_aj
       for (int e = tid; e < N * N; e += kThreads) {
         const int i = e / N, j = e - i * N;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int a = 0; a < M; ++a) cmac_ca(acc, sP[a * N + i], sT[a * N + j]);
         const double2 h = Hk[e];
-        double2 v = make_double2(-h.x - acc.x, -h.y - acc.y);
-        if (i == j) { v.x += mu; v.y += wn; }
+        double2 v = make_double2((i == j ? mu : 0.0) - h.x, (i == j ? wn : 0.0) - h.y);
+        for (int a = 0; a < M; ++a) {
+          const double2 p = sP[a * N + i], t = sT[a * N + j];
+          v.x = fma(-p.x, t.x, fma(-p.y, t.y, v.x));
+          v.y = fma(-p.x, t.y, fma(p.y, t.x, v.y));
+        }
         A[i * ld + j] = v;
       }
       __syncthreads();

@@ -24,7 +24,7 @@ DTYPE = {"c128": 0, "c64": 1}
 
 EXPORTS = ["gf_create", "gf_destroy", "gf_set_hamiltonian", "gf_set_projectors", "gf_set_sigma",
            "gf_local", "gf_occupation", "gf_find_mu", "gf_density_matrix", "gf_backward",
-           "gf_last_error", "gf_last_stats"]
+           "gf_evaluate", "gf_last_error", "gf_last_stats"]
 
 
 class GFError(RuntimeError):
@@ -63,9 +63,11 @@ def load():
     lib.gf_find_mu.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int32, dp, ip]
     lib.gf_density_matrix.argtypes = [vp, dp, vp, dp]
     lib.gf_backward.argtypes = [vp, dp, vp, dp, vp, dp]
+    lib.gf_evaluate.argtypes = [vp, dp, vp, vp, dp, dp, dp]
     lib.gf_last_error.argtypes = [vp]
     lib.gf_last_error.restype = ctypes.c_char_p
-    lib.gf_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.gf_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                  dp, dp]
     for name in EXPORTS:
         if name not in ("gf_last_error",):
             getattr(lib, name).restype = ctypes.c_int
@@ -238,6 +240,22 @@ class GreensFunction:
                                                nc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return (o.obj if o else None), nc
 
+    def evaluate(self, mu, gloc=True, rho=True, occupation=True, n_corr=True, gloc_out=None,
+                 rho_out=None):
+        """One fused pass: dict(gloc, rho, N, dN_dmu, n_corr) for the requested outputs."""
+        _, mp = _doubles(mu, self.n_sys)
+        go = _Arg(self._out(self.tot_sig, gloc_out)) if gloc else None
+        ro = _Arg(self._out(self.tot_h, rho_out)) if rho else None
+        n, d, nc = np.zeros(self.n_sys), np.zeros(self.n_sys), np.zeros(self.n_sys)
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+        self._check(self.lib.gf_evaluate(
+            self.h, mp, ctypes.c_void_p(go.ptr if go else 0), ctypes.c_void_p(ro.ptr if ro else 0),
+            dptr(n) if occupation else None, dptr(d) if occupation else None,
+            dptr(nc) if n_corr else None))
+        return {"gloc": go.obj if go else None, "rho": ro.obj if ro else None,
+                "N": n if occupation else None, "dN_dmu": d if occupation else None,
+                "n_corr": nc if n_corr else None}
+
     def backward(self, mu, gloc_bar=None, n_bar=None, out=None):
         """(Sigma_bar packed like Sigma, complex128; mu_bar per system)."""
         _, mp = _doubles(mu, self.n_sys)
@@ -255,7 +273,9 @@ class GreensFunction:
         return out, mub
 
     def stats(self):
-        """(kernel launches, (k, i w_n) points) of the last compute call."""
+        """dict(launches, points, kernel_ms, flops) of the last compute call."""
         a, b = ctypes.c_int64(), ctypes.c_int64()
-        self._check(self.lib.gf_last_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
-        return a.value, b.value
+        ms, fl = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.gf_last_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms),
+                                           ctypes.byref(fl)))
+        return {"launches": a.value, "points": b.value, "kernel_ms": ms.value, "flops": fl.value}

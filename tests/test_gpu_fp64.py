@@ -172,3 +172,21 @@ def test_ce_like_full_size_sampled():
     assert rel(rho[ks], r["rho"]) < TOL
     # N = sum_k w_k Tr rho_k holds for the GPU's own outputs
     assert abs(n[0] - np.trace(rho, axis1=1, axis2=2).real.sum() / s.nk) < 1e-10 * n[0]
+
+
+def test_evaluate_fused_pass():
+    s = synth.ce_like(nk=4, n_iw=40).systems[0]
+    mu = 0.1
+    g = make_gf([s])
+    out = g.evaluate([mu])
+    r, glo = oracle_all(s, mu)
+    assert rel(out["gloc"].cpu().numpy(), glo.reshape(-1)) < TOL
+    assert rel(out["rho"].cpu().numpy(), r["rho"].reshape(-1)) < TOL
+    assert abs(out["N"][0] - r["N"]) < TOL * r["N"]
+    assert abs(out["dN_dmu"][0] - r["dN_dmu"]) < TOL * r["dN_dmu"]
+    assert abs(out["n_corr"][0] - r["n_corr"]) < TOL * r["n_corr"]
+    only_n = g.evaluate([mu], gloc=False, rho=False, n_corr=False)
+    assert only_n["gloc"] is None and only_n["rho"] is None
+    assert abs(only_n["N"][0] - r["N"]) < TOL * r["N"]
+    st = g.stats()
+    assert st["points"] == s.nk * s.n_iw and st["kernel_ms"] > 0 and st["flops"] > 0
