@@ -53,7 +53,7 @@ def hamiltonian_dense(rng, nk, nb, lo, hi, s):
     H = U + np.conj(np.swapaxes(U, 1, 2))
     idx = np.arange(nb)
     H[:, idx, idx] = d
-    return H
+    return np.ascontiguousarray(H)
 
 
 def projectors(rng, nk, nb, m):
