@@ -149,6 +149,35 @@ gf_status gf_evaluate(gf_ctx *ctx, const double *mu, void *gloc_out_ptr, void *r
 gf_status gf_backward(gf_ctx *ctx, const double *mu, const void *gloc_bar_ptr, const double *n_bar,
                       void *sigma_bar_out_ptr, double *mu_bar_out);
 
+/* N(mu) and dN/dmu of one system with a uniform band window, without any
+ * device allocation.  The paper has no counterpart: this is a library
+ * service for callers that cannot call cudaMalloc, such as code running
+ * inside another framework's memory pool or allocator hooks, plugins that may
+ * not grow the device footprint after start-up, or hot paths where allocation
+ * is forbidden.  It computes what gf_occupation computes for a context made
+ * of these sizes, with the same point kernel.
+ *
+ * Inputs are device pointers of the current device, complex128: h_dev
+ * [n_k][nb][nb], p_dev [n_k][m][nb], sigma_dev [n_iw][m][m], sigma_inf_dev
+ * [m][m]; k-weights are 1/n_k.  stream: cudaStream_t or NULL.  Results go to
+ * the host: *n_out and, if not NULL, *dn_dmu_out; the call returns after the
+ * stream has drained.
+ *
+ * Scratch: a file-scope device array of 4 MiB that every GPU loading the
+ * library holds until the process exits.  The problem must fit in it:
+ * about 32 bytes per (k, frequency chunk) item plus 56 bytes per k-point
+ * (n_k = 1000 with 1024 frequencies needs about 0.5 MiB); larger problems,
+ * and windows whose matrix does not fit in shared memory, return GF_EINVAL.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one array and overwrites it, so calls whose work overlaps on
+ * the GPU (other streams, other host threads) race: serialise them.
+ * Errors (message in gf_last_error(NULL)): GF_EINVAL, GF_ESINGULAR, GF_ECUDA. */
+gf_status gf_occupation_static(const void *h_dev, const void *p_dev, const void *sigma_dev,
+                               const void *sigma_inf_dev, int32_t n_k, int32_t nb, int32_t m,
+                               int32_t n_iw, double beta, double mu, int32_t tail_order,
+                               void *stream, double *n_out, double *dn_dmu_out);
+
 /* Message of the last failed call on this context ("" if none).  Owned by the
  * context, valid until the next call on it. */
 const char *gf_last_error(const gf_ctx *ctx);

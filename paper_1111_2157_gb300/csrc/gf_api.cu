@@ -72,6 +72,19 @@ double trigamma(double x) {
 
 }  // namespace
 
+namespace gf {
+
+// (2/beta) sum_{n<N} 1/w_n^2 - beta/4 = -(2/beta)(beta/pi)^2 sum_{n>=N} (2n+1)^-2
+//                                     = -(beta/(2 pi^2)) psi'(N + 1/2)
+double tail_coefficient(double beta, int n_iw, int tail_order) {
+  if (tail_order != 2) return 0.0;
+  return -beta / (2.0 * M_PI * M_PI) * trigamma(n_iw + 0.5);
+}
+
+void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
+}  // namespace gf
+
 struct gf_ctx {
   int n_sys = 0, n_k = 0, n_iw = 0, precision = 0, in_dtype = 0, tail_order = 2, device = 0;
   cudaStream_t stream = nullptr;
@@ -398,13 +411,7 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
     k0 = si.k1;
     si.pad = 0;
     si.beta = c->beta[s];
-    if (c->tail_order == 2) {
-      // (2/beta) sum_{n<N} 1/w_n^2 - beta/4 = -(2/beta)(beta/pi)^2 sum_{n>=N} (2n+1)^-2
-      //                                     = -(beta/(2 pi^2)) psi'(N + 1/2)
-      si.tailc = -si.beta / (2.0 * M_PI * M_PI) * trigamma(c->n_iw + 0.5);
-    } else {
-      si.tailc = 0.0;
-    }
+    si.tailc = gf::tail_coefficient(si.beta, c->n_iw, c->tail_order);
     si.offSig = offSig;
     si.offSinf = offSinf;
     offSig += (int64_t)c->n_iw * si.m * si.m;

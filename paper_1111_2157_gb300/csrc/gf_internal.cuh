@@ -96,4 +96,11 @@ cudaError_t launch_diag_to_dense(const KInfo* kinfo, const double2* diag, const 
 cudaError_t launch_mubar_reduce(const KInfo* kinfo, const SInfo* sinfo, int n_sys, int n_chunks,
                                 const double* mubar_part, double* out, cudaStream_t s);
 
+// Coefficient of M2 in rho_k: (2/beta) sum_{n<n_iw} 1/w_n^2 - beta/4 for tail_order 2
+// (= -(beta / (2 pi^2)) psi'(n_iw + 1/2)), 0 for tail_order 1.
+double tail_coefficient(double beta, int n_iw, int tail_order);
+
+// Message returned by gf_last_error(NULL) (calls that have no context).
+void set_global_error(const char* msg);
+
 }  // namespace gf

@@ -24,7 +24,7 @@ DTYPE = {"c128": 0, "c64": 1}
 
 EXPORTS = ["gf_create", "gf_destroy", "gf_set_hamiltonian", "gf_set_projectors", "gf_set_sigma",
            "gf_local", "gf_occupation", "gf_find_mu", "gf_density_matrix", "gf_backward",
-           "gf_evaluate", "gf_last_error", "gf_last_stats"]
+           "gf_evaluate", "gf_occupation_static", "gf_last_error", "gf_last_stats"]
 
 
 class GFError(RuntimeError):
@@ -64,6 +64,9 @@ def load():
     lib.gf_density_matrix.argtypes = [vp, dp, vp, dp]
     lib.gf_backward.argtypes = [vp, dp, vp, dp, vp, dp]
     lib.gf_evaluate.argtypes = [vp, dp, vp, vp, dp, dp, dp]
+    lib.gf_occupation_static.argtypes = [vp, vp, vp, vp, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int32, vp, dp, dp]
     lib.gf_last_error.argtypes = [vp]
     lib.gf_last_error.restype = ctypes.c_char_p
     lib.gf_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
