@@ -57,6 +57,8 @@ def parse():
                     help="smaller k-set of the same workload (profiling captures only)")
     ap.add_argument("--n-iw", type=int, default=None,
                     help="fewer Matsubara frequencies (profiling captures only)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="compile and run the pipe-throughput microbenchmark (peaks.cu) and exit")
     return ap.parse_args()
 
 
@@ -204,8 +206,20 @@ def run_reference(args):
     return 0
 
 
+def run_peaks():
+    """Build paper_1111_2157_gb300/peaks.cu with nvcc and run it (prints one line per pipe)."""
+    from paper_1111_2157_gb300 import build as gfbuild
+    src = ROOT / "paper_1111_2157_gb300" / "peaks.cu"
+    exe = gfbuild.BUILD / "peaks"
+    gfbuild.BUILD.mkdir(exist_ok=True)
+    subprocess.run([gfbuild.nvcc(), *gfbuild.ARCH, "-O3", "-o", str(exe), str(src)], check=True)
+    return subprocess.run([str(exe)]).returncode
+
+
 def main():
     args = parse()
+    if args.peaks:
+        return run_peaks()
     if args.impl == "reference":
         return run_reference(args)
     ws, rank, local = dist_env()
