@@ -51,12 +51,15 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the bounded CPU-oracle sample")
     ap.add_argument("--nk", type=int, default=None,
                     help="smaller k-set of the same workload (profiling captures only)")
     ap.add_argument("--n-iw", type=int, default=None,
                     help="fewer Matsubara frequencies (profiling captures only)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="arithmetic of the point kernel (mixed: FP32 pairs on the FP32 pipes)")
     ap.add_argument("--peaks", action="store_true",
                     help="compile and run the pipe-throughput microbenchmark (peaks.cu) and exit")
     return ap.parse_args()
@@ -194,7 +197,8 @@ def run_reference(args):
     value = args.steps * k * s.n_iw / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32x2",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "step": f"oracle Matsubara-sum pass over {k} k-points x "
                                                      f"{s.n_iw} frequencies at mu=0 (bounded sample)",
@@ -241,7 +245,6 @@ def main():
     s = synth.ce_like(**kw).systems[0]
     nk, nb, m, n_iw = s.nk, 40, s.m, s.n_iw
     dev = torch.device(f"cuda:{local}")
-    g = gf.GreensFunction(nb, m, n_iw, s.beta, n_k=nk, device=local)
     H_d = torch.from_numpy(s.H).to(dev)
     P_d = torch.from_numpy(s.P).to(dev)
     S_d = torch.from_numpy(s.sigma).to(dev)
@@ -249,67 +252,97 @@ def main():
     rng = np.random.default_rng(2157)
     gbar_h = (rng.standard_normal(s.sigma.shape) + 1j * rng.standard_normal(s.sigma.shape)) * 1e-3
     gbar_d = torch.from_numpy(gbar_h).to(dev)
-    g.set_hamiltonian(H_d)
-    g.set_projectors(P_d)
-    g.set_sigma(S_d, Si_d)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    gloc_d = torch.empty(g.tot_sig, dtype=torch.complex128, device=dev)
-    rho_d = torch.empty(g.tot_h, dtype=torch.complex128, device=dev)
-    sbar_d = torch.empty(g.tot_sig, dtype=torch.complex128, device=dev)
-    totals = {"launches": 0, "points": 0, "kernel_ms": 0.0, "flops": 0.0}
-    passes = {name: {"kernel_ms": 0.0, "flops": 0.0, "launches": 0}
-              for name in ("find_mu", "evaluate", "backward")}
 
-    def acc(name):
-        st = g.stats()
-        for k in totals:
-            totals[k] += st[k]
-        passes[name]["kernel_ms"] += st["kernel_ms"]
-        passes[name]["flops"] += st["flops"]
-        passes[name]["launches"] += 1
+    def run_leg(precision, steps, warmup, sample_clocks):
+        g = gf.GreensFunction(nb, m, n_iw, s.beta, n_k=nk, device=local, precision=precision)
+        g.set_hamiltonian(H_d)
+        g.set_projectors(P_d)
+        g.set_sigma(S_d, Si_d)
+        gloc_d = torch.empty(g.tot_sig, dtype=torch.complex128, device=dev)
+        rho_d = torch.empty(g.tot_h, dtype=torch.complex128, device=dev)
+        sbar_d = torch.empty(g.tot_sig, dtype=torch.complex128, device=dev)
+        totals = {"launches": 0, "points": 0, "kernel_ms": 0.0, "flops": 0.0}
+        passes = {name: {"kernel_ms": 0.0, "flops": 0.0, "launches": 0}
+                  for name in ("find_mu", "evaluate", "backward")}
+        info = {}
 
-    info = {}
+        def acc(name):
+            st = g.stats()
+            for k in totals:
+                totals[k] += st[k]
+            passes[name]["kernel_ms"] += st["kernel_ms"]
+            passes[name]["flops"] += st["flops"]
+            passes[name]["launches"] += 1
 
-    def step():
-        mu, it = g.find_mu([s.n_target], 0.0, tol=1e-10, max_iter=60)
-        acc("find_mu")
-        out = g.evaluate(mu, gloc_out=gloc_d, rho_out=rho_d)
-        acc("evaluate")
-        g.backward(mu, gloc_bar=gbar_d, n_bar=[1.0], out=sbar_d)
-        acc("backward")
-        info["mu"], info["iters"], info["N"] = float(mu[0]), it, float(out["N"][0])
+        def step():
+            mu, it = g.find_mu([s.n_target], 0.0, tol=1e-10, max_iter=60)
+            acc("find_mu")
+            out = g.evaluate(mu, gloc_out=gloc_d, rho_out=rho_d)
+            acc("evaluate")
+            g.backward(mu, gloc_bar=gbar_d, n_bar=[1.0], out=sbar_d)
+            acc("backward")
+            info["mu"], info["iters"], info["N"] = float(mu[0]), it, float(out["N"][0])
 
-    for _ in range(args.warmup):
-        step()
-        flush.zero_()
-    for k in totals:
-        totals[k] = 0 if k in ("launches", "points") else 0.0
-    for v in passes.values():
-        v.update(kernel_ms=0.0, flops=0.0, launches=0)
-
-    clocks = ClockSampler(local)
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for i in range(args.steps):
-        step()
-        if i + 1 < args.steps:
+        for _ in range(warmup):
+            step()
             flush.zero_()
-    e1.record()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-        torch.distributed.barrier()
+        for k in totals:
+            totals[k] = 0 if k in ("launches", "points") else 0.0
+        for v in passes.values():
+            v.update(kernel_ms=0.0, flops=0.0, launches=0)
+        clocks = ClockSampler(local) if sample_clocks else None
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(steps):
+            step()
+            if i + 1 < steps:
+                flush.zero_()
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        elapsed = e0.elapsed_time(e1) / 1e3
+        if ws > 1:
+            t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            elapsed = float(t.item())
+            torch.distributed.barrier()
+        return {"g": g, "elapsed": elapsed, "totals": totals, "passes": passes, "info": info,
+                "clocks": clk, "gloc": gloc_d}
+
+    fp = run_leg(args.precision, args.steps, args.warmup, True)
+    g, elapsed, totals, passes, info, clk = (fp["g"], fp["elapsed"], fp["totals"], fp["passes"],
+                                             fp["info"], fp["clocks"])
     points_all = totals["points"] * ws
     value = points_all / elapsed
     achieved = totals["flops"] / (totals["kernel_ms"] / 1e3) / 1e12
+
+    mixed = None
+    if args.precision == "fp64" and not args.no_mixed:
+        mx = run_leg("mixed", args.steps, args.warmup, False)
+        gm = mx["g"]
+        # errors of the mixed path against the FP64 GPU path at the FP64 mu*
+        n_mx, _ = gm.occupation([info["mu"]])
+        gl_mx = gm.local([info["mu"]])
+        gl_fp = g.local([info["mu"]])
+        err_n = abs(n_mx[0] - info["N"]) / abs(info["N"])
+        err_g = float((gl_mx - gl_fp).abs().max() / gl_fp.abs().max())
+        mt = mx["totals"]
+        mixed = {"value": mt["points"] * ws / mx["elapsed"], "unit": UNIT,
+                 "ms_per_step": mx["elapsed"] / args.steps * 1e3,
+                 "speedup_vs_fp64_gpu": (mt["points"] / mx["elapsed"]) / (totals["points"] / elapsed),
+                 "N_rel_err_vs_fp64_gpu": err_n, "G_loc_rel_err_vs_fp64_gpu": err_g,
+                 "mu_star": mx["info"]["mu"],
+                 "fp64_equivalent_tflops": mt["flops"] / (mt["kernel_ms"] / 1e3) / 1e12,
+                 "arithmetic": "FP32 pairs (hi + lo, error-free transformations) on the FP32 pipes; "
+                               "FP64 reductions, Matsubara tail and mu search",
+                 "kernel_choice": gm.tuning_log(), "gpu_launches": mt["launches"]}
+        gm.close()
 
     e2e = None
     if not args.no_e2e:
@@ -364,12 +397,13 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32x2",
             "data": "synthetic",
             "config": {"workload": WORKLOAD,
                        "step": "find_mu (Newton from mu=0, tol 1e-10) + fused G_loc/rho_k/N/dN/n_corr "
                                "pass + adjoint (Sigma_bar, mu_bar)",
-                       "precision": "fp64", "l2": "flushed between steps (256 MiB write)",
+                       "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "points_per_step": totals["points"] // args.steps,
                        "mu_evaluations_per_step": info["iters"], "mu_star": info["mu"],
@@ -384,6 +418,7 @@ def main():
                          "by_pass_ms_per_step": {k: v["kernel_ms"] / args.steps
                                                  for k, v in passes.items()}},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": totals["launches"], "clocks": clk,
+            "mixed": mixed,
         }
         print(json.dumps(line), flush=True)
     g.close()

@@ -182,6 +182,11 @@ gf_status gf_occupation_static(const void *h_dev, const void *p_dev, const void 
  * context, valid until the next call on it. */
 const char *gf_last_error(const gf_ctx *ctx);
 
+/* How the library configured its kernels for this context (e.g. which
+ * mixed-precision kernel the autotuner kept and the timings it compared), as a
+ * context-owned string ("" before the first compute call). */
+const char *gf_tuning_log(const gf_ctx *ctx);
+
 /* Counters of the last compute call (any pointer may be NULL): kernel launches
  * of this library, (k, i w_n) points evaluated, the summed duration of the
  * point-kernel launches in milliseconds (CUDA events recorded on the context's

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -103,6 +104,7 @@ struct gf_ctx {
   DevBuf H, P, Sig, Sinf, Einf, trHE, kinfo_d, sinfo_d, items_d, offD_d, mu, nbar, gbar, status,
       queue, stage, occ_part, rho_part, rho_out, gq, kN, kdN, kNc, sysout, a_scratch, mubar_part,
       mubar_sys, gacc, sysout2;
+  DevBuf Hd, Pd, Sd, Gbd;  // FP32-pair copies for the mixed path
   bool have_H = false, have_P = false, have_S = false, einf_dirty = true;
   bool have_gbar_for_call = false;
   // pinned host staging: mu [S] | n_bar [S] | status | outputs [2S] | mu_bar [S] | outputs [2S]
@@ -114,6 +116,8 @@ struct gf_ctx {
   double* hp_mubar() { return hpin + 4 * n_sys + 1; }
   double* hp_sys2() { return hpin + 5 * n_sys + 1; }
   std::string err;
+  std::map<int, bool> tuned;  // mixed path: register kernel chosen, per mode
+  std::string tune_log;
   int64_t last_launches = 0, last_points = 0;
   double last_kernel_ms = 0.0, last_flops = 0.0;
   // CUDA event pairs around the point-kernel launches of the current call
@@ -194,6 +198,65 @@ gf_status upload_mu(gf_ctx* c, const double* mu) {
   return GF_OK;
 }
 
+// Autotuner of the mixed path: on the first call of a mode, run the first items
+// of the work list with each candidate kernel (the shared-memory one and the
+// register-resident one), time them with CUDA events, and keep the faster for
+// this context.  The sample runs write only scratch that the real run
+// overwrites.  GF_AUTOTUNE=0 skips the timing and takes the register kernel.
+gf_status autotune_df64(gf_ctx* c, int mode, gf::PointParams p, int grid, size_t smem, int rshape,
+                        int rgrid, int rthreads, size_t rsmem, bool* use_r) {
+  auto it = c->tuned.find(mode);
+  if (it != c->tuned.end()) {
+    *use_r = it->second;
+    return GF_OK;
+  }
+  const char* env = std::getenv("GF_AUTOTUNE");
+  if (env && std::atoi(env) == 0) {
+    c->tuned[mode] = true;
+    *use_r = true;
+    return GF_OK;
+  }
+  if (mode & (gf::kGloc | gf::kAdj)) {
+    GF_CU(ensure(c->gq, sizeof(double2) * (size_t)(c->batch_k0[1] - c->batch_k0[0]) * c->n_iw *
+                            c->mmax * c->mmax));
+    p.gq = c->gq.as<double2>();
+    p.kb0 = c->batch_k0[0];
+  }
+  const int n_sample = std::min(c->batch_item0[1] - c->batch_item0[0], 2 * std::max(grid, rgrid));
+  p.items = c->items_d.as<Item>();
+  p.n_items = n_sample;
+  cudaEvent_t e0, e1;
+  GF_CU(cudaEventCreate(&e0));
+  GF_CU(cudaEventCreate(&e1));
+  float ms[2] = {0.f, 0.f};
+  for (int cand = 0; cand < 2; ++cand) {
+    for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the module
+      GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
+      GF_CU(cudaEventRecord(e0, c->stream));
+      if (cand == 0)
+        GF_CU(gf::launch_point_df64(p, std::min(grid, n_sample), smem, c->stream));
+      else
+        GF_CU(gf::launch_point_df64r(rshape, p, std::min(rgrid, n_sample), rthreads, rsmem, c->stream));
+      GF_CU(cudaEventRecord(e1, c->stream));
+      GF_CU(cudaEventSynchronize(e1));
+      GF_CU(cudaEventElapsedTime(&ms[cand], e0, e1));
+      c->last_launches += 1;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *use_r = ms[1] < ms[0];
+  c->tuned[mode] = *use_r;
+  char buf[200];
+  std::snprintf(buf, sizeof(buf),
+                "mixed mode %d: %s (sample of %d items: shared-memory %.3f ms, register %dx%d tiles "
+                "x %d threads %.3f ms)",
+                mode, *use_r ? "register-resident kernel" : "shared-memory kernel", n_sample, ms[0],
+                gf::df64r_tile(rshape, 0), gf::df64r_tile(rshape, 1), rthreads, ms[1]);
+  c->tune_log = buf;
+  return GF_OK;
+}
+
 // Algorithmic floating-point operations of one (k, i w_n) point (8 per complex
 // multiply-add, 2 per complex add or real product pair).
 double point_flops(int N, int M, int mode) {
@@ -226,13 +289,34 @@ gf_status run_points(gf_ctx* c, int mode) {
     if (smem > limit)
       return fail(c, GF_EINVAL, "N_b or m too large for the shared-memory tiles of the FP64 kernel");
   }
-  int bps = gf::point_fp64_blocks_per_sm(smem);
-  if (bps < 1) bps = 1;
+  const bool df64 = (c->precision == GF_PREC_MIXED);
+  int nmat = 1;
+  int bps = 1;
+  int rshape = -1, rthreads = 0;
+  size_t rsmem = 0;
+  if (df64) {
+    // candidates: the shared-memory FP32-pair kernel and, for windows up to 96
+    // bands, the register-resident one; the autotuner picks between them
+    const int shape = gf::df64r_shape(c->nbmax);
+    if (shape >= 0) {
+      rsmem = gf::point_df64r_smem(c->nbmax, c->mmax, mode);
+      rthreads = gf::df64r_threads(shape, c->nbmax);
+      if (rsmem <= limit) rshape = shape;
+    }
+    bps = std::max(1, gf::point_df64_blocks_per_sm(smem));
+  } else {
+    bps = std::max(1, gf::point_fp64_blocks_per_sm(smem));
+  }
   const int grid = c->sm_count * bps;
   gf::PointParams p{};
   p.H = c->H.as<double2>();
   p.P = c->P.as<double2>();
   p.Sig = c->Sig.as<double2>();
+  if (df64) {
+    p.Hd = c->Hd.as<float4>();
+    p.Pd = c->Pd.as<float4>();
+    p.Sd = c->Sd.as<float4>();
+  }
   p.kinfo = c->kinfo_d.as<KInfo>();
   p.sinfo = c->sinfo_d.as<SInfo>();
   p.n_chunks = c->n_chunks;
@@ -242,9 +326,10 @@ gf_status run_points(gf_ctx* c, int mode) {
   p.nbmax = c->nbmax;
   p.mmax = c->mmax;
   p.a_in_smem = a_in_smem;
+  p.nmat = nmat;
   if (!a_in_smem) {
     p.a_stride = (int64_t)c->nbmax * (c->nbmax | 1);
-    GF_CU(ensure(c->a_scratch, (size_t)grid * p.a_stride * sizeof(double2)));
+    GF_CU(ensure(c->a_scratch, (size_t)grid * nmat * p.a_stride * sizeof(double2)));
     p.a_scratch = c->a_scratch.as<double2>();
   }
   if (mode & gf::kOcc) {
@@ -266,10 +351,19 @@ gf_status run_points(gf_ctx* c, int mode) {
   p.nbar = nullptr;
   if (mode & gf::kAdj) {
     p.gbar = c->have_gbar_for_call ? c->gbar.as<double2>() : nullptr;
+    p.Gbd = (df64 && c->have_gbar_for_call) ? c->Gbd.as<float4>() : nullptr;
     p.nbar = c->nbar.as<double>();
   }
   const bool kred = (mode & (gf::kGloc | gf::kAdj)) != 0;
   const int nb_batches = kred ? (int)c->batch_k0.size() - 1 : 1;
+  // mixed path: register-resident or shared-memory kernel, chosen once per mode
+  bool use_r = false;
+  int rgrid = 0;
+  if (rshape >= 0) {
+    rgrid = c->sm_count * std::max(1, gf::point_df64r_blocks_per_sm(rshape, rthreads, rsmem));
+    st = autotune_df64(c, mode, p, grid, smem, rshape, rgrid, rthreads, rsmem, &use_r);
+    if (st) return st;
+  }
   int64_t points = 0;
   for (int b = 0; b < nb_batches; ++b) {
     const int i0 = kred ? c->batch_item0[b] : 0;
@@ -290,7 +384,13 @@ gf_status run_points(gf_ctx* c, int mode) {
       c->ev.push_back(e);
     }
     GF_CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
-    GF_CU(gf::launch_point_fp64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
+    if (use_r)
+      GF_CU(gf::launch_point_df64r(rshape, p, std::min(rgrid, std::max(1, i1 - i0)), rthreads, rsmem,
+                                   c->stream));
+    else if (df64)
+      GF_CU(gf::launch_point_df64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
+    else
+      GF_CU(gf::launch_point_fp64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
     GF_CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
     c->ev_used += 2;
     c->last_launches += 1;
@@ -464,7 +564,10 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   const int kpb = (int)std::max<size_t>(1, std::min<size_t>(c->n_k, budget / per_k));
   // chunk width: about 40 items per resident CTA
   const size_t smem = gf::point_fp64_smem(c->nbmax, c->mmax, gf::kOcc, 1);
-  int bps = (smem <= (size_t)c->smem_optin - 1024) ? gf::point_fp64_blocks_per_sm(smem) : 1;
+  int bps = 1;
+  if (smem <= (size_t)c->smem_optin - 1024)
+    bps = (c->precision == GF_PREC_MIXED) ? gf::point_df64_blocks_per_sm(smem)
+                                          : gf::point_fp64_blocks_per_sm(smem);
   if (bps < 1) bps = 1;
   const double resident = (double)c->sm_count * bps;
   const double want = (double)c->n_k * c->n_iw / (40.0 * resident);
@@ -496,6 +599,11 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
     if ((e = ensure(c->Sig, sizeof(double2) * c->totSig))) return e;
     if ((e = ensure(c->gacc, sizeof(double2) * c->totSig))) return e;
     if ((e = ensure(c->Sinf, sizeof(double2) * c->totSinf))) return e;
+    if (c->precision == GF_PREC_MIXED) {
+      if ((e = ensure(c->Hd, sizeof(float4) * c->totH))) return e;
+      if ((e = ensure(c->Pd, sizeof(float4) * c->totP))) return e;
+      if ((e = ensure(c->Sd, sizeof(float4) * c->totSig))) return e;
+    }
     if ((e = ensure(c->trHE, sizeof(double) * c->n_k))) return e;
     if ((e = ensure(c->kN, sizeof(double) * c->n_k))) return e;
     if ((e = ensure(c->kdN, sizeof(double) * c->n_k))) return e;
@@ -545,7 +653,7 @@ gf_status gf_destroy(gf_ctx* c) {
                     &c->items_d, &c->offD_d, &c->mu, &c->nbar, &c->gbar, &c->status, &c->queue,
                     &c->stage, &c->occ_part, &c->rho_part, &c->rho_out, &c->gq, &c->kN, &c->kdN,
                     &c->kNc, &c->sysout, &c->a_scratch, &c->mubar_part, &c->mubar_sys, &c->gacc,
-                    &c->sysout2};
+                    &c->sysout2, &c->Hd, &c->Pd, &c->Sd, &c->Gbd};
   for (DevBuf* b : bufs) release(*b);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -577,6 +685,10 @@ gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) {
     if (st) return st;
     GF_CU(cudaStreamSynchronize(c->stream));
   }
+  if (c->precision == GF_PREC_MIXED) {
+    GF_CU(gf::launch_split_df64(c->H.as<double2>(), c->Hd.as<float4>(), c->totH, c->stream));
+    GF_CU(cudaStreamSynchronize(c->stream));
+  }
   c->have_H = true;
   c->einf_dirty = true;
   return GF_OK;
@@ -588,6 +700,8 @@ gf_status gf_set_projectors(gf_ctx* c, const void* p) {
   DeviceGuard guard(c->device);
   gf_status st = load_complex(c, p, c->totP, c->P.as<double2>());
   if (st) return st;
+  if (c->precision == GF_PREC_MIXED)
+    GF_CU(gf::launch_split_df64(c->P.as<double2>(), c->Pd.as<float4>(), c->totP, c->stream));
   GF_CU(cudaStreamSynchronize(c->stream));
   c->have_P = true;
   c->einf_dirty = true;
@@ -602,6 +716,8 @@ gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) {
   if (st) return st;
   st = load_complex(c, sinf, c->totSinf, c->Sinf.as<double2>());
   if (st) return st;
+  if (c->precision == GF_PREC_MIXED)
+    GF_CU(gf::launch_split_df64(c->Sig.as<double2>(), c->Sd.as<float4>(), c->totSig, c->stream));
   GF_CU(cudaStreamSynchronize(c->stream));
   c->have_S = true;
   c->einf_dirty = true;
@@ -785,6 +901,10 @@ gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const doubl
   if (gbar) {
     GF_CU(ensure(c->gbar, sizeof(double2) * c->totSig));
     GF_CU(cudaMemcpyAsync(c->gbar.p, gbar, sizeof(double2) * c->totSig, cudaMemcpyDefault, c->stream));
+    if (c->precision == GF_PREC_MIXED) {
+      GF_CU(ensure(c->Gbd, sizeof(float4) * c->totSig));
+      GF_CU(gf::launch_split_df64(c->gbar.as<double2>(), c->Gbd.as<float4>(), c->totSig, c->stream));
+    }
   }
   const int mode = gf::kAdj | (any_nbar ? gf::kOcc : 0);
   st = run_points(c, mode);
@@ -816,6 +936,11 @@ gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const doubl
     mubar_out[s] = c->hp_nbar()[s] * dn + c->hp_mubar()[s];
   }
   return GF_OK;
+}
+
+const char* gf_tuning_log(const gf_ctx* c) {
+  if (!c) return "";
+  return c->tune_log.c_str();
 }
 
 const char* gf_last_error(const gf_ctx* c) {

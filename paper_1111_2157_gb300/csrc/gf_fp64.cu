@@ -23,32 +23,6 @@ namespace gf {
 
 namespace {
 
-struct Layout {
-  int offA, offP, offT, offZ, offS, offQa, offQb, offCol, offU;
-  int n2;        // double2 elements before the int arrays
-  size_t bytes;
-};
-
-__host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
-
-__host__ __device__ inline Layout make_layout(int nbmax, int mmax, int mode, int a_in_smem) {
-  Layout L;
-  const int ld = nbmax | 1;
-  int o = 0;
-  L.offA = o; o += a_in_smem ? nbmax * ld : 0;
-  L.offP = o; o += mmax * nbmax;
-  L.offT = o; o += imax(mmax * nbmax, mmax * mmax);
-  L.offZ = o; o += (mode & kAdj) ? mmax * nbmax : 0;
-  L.offS = o; o += mmax * mmax;
-  L.offQa = o; o += (mode & kAdj) ? mmax * mmax : 0;
-  L.offQb = o; o += (mode & kAdj) ? mmax * mmax : 0;
-  L.offCol = o; o += nbmax;
-  L.offU = o; o += nbmax;
-  L.n2 = o;
-  L.bytes = (size_t)o * sizeof(double2) + 2 * (size_t)nbmax * sizeof(int);
-  return L;
-}
-
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }

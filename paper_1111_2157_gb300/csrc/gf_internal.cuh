@@ -53,10 +53,16 @@ struct PointParams {
   int* queue;           // work counter, zero before launch
   const double* mu;     // [n_sys]
   int mode;
+  int nmat;             // df64 kernel: frequencies processed together per CTA (1..4)
   int nbmax, mmax;
   int a_in_smem;        // 1: the N_b x N_b matrix lives in shared memory
   double2* a_scratch;   // else: per-CTA slices of a_stride elements in global memory
   int64_t a_stride;
+  // FP32-pair copies of H, P, Sigma and Gbar for the df64 kernel: {re.hi, re.lo, im.hi, im.lo}
+  const float4* Hd;
+  const float4* Pd;
+  const float4* Sd;
+  const float4* Gbd;
   // outputs
   double* occ_part;     // [n_k][n_chunks][2]
   double2* rho_part;    // [n_chunks][sum_k N_b^2]
@@ -71,11 +77,59 @@ struct PointParams {
   int* status;
 };
 
+// Shared-memory layout of the point kernels, in 16-byte complex elements (a
+// complex double or a complex FP32 pair): the N_b x N_b matrix (odd leading
+// dimension), P_k, T = Sigma P_k / Y = G P^+ / Gbar A^+, Z = P G (adjoint),
+// Sigma(i w_n) / Gbar, A_k and B_k (adjoint), the pivot column and row, then the
+// pivot and column-permutation index arrays.
+struct Layout {
+  int offA, offP, offT, offZ, offS, offQa, offQb, offCol, offU;
+  int n2;        // 16-byte elements before the int arrays
+  size_t bytes;
+};
+
+__host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
+
+__host__ __device__ inline Layout make_layout(int nbmax, int mmax, int mode, int a_in_smem) {
+  Layout L;
+  const int ld = nbmax | 1;
+  int o = 0;
+  L.offA = o; o += a_in_smem ? nbmax * ld : 0;
+  L.offP = o; o += mmax * nbmax;
+  L.offT = o; o += imax(mmax * nbmax, mmax * mmax);
+  L.offZ = o; o += (mode & kAdj) ? mmax * nbmax : 0;
+  L.offS = o; o += mmax * mmax;
+  L.offQa = o; o += (mode & kAdj) ? mmax * mmax : 0;
+  L.offQb = o; o += (mode & kAdj) ? mmax * mmax : 0;
+  L.offCol = o; o += nbmax;
+  L.offU = o; o += nbmax;
+  L.n2 = o;
+  L.bytes = (size_t)o * 16 + 2 * (size_t)nbmax * sizeof(int);
+  return L;
+}
+
 // Shared-memory footprint (bytes) of k_point_fp64 for the given sizes and mode.
 size_t point_fp64_smem(int nbmax, int mmax, int mode, int a_in_smem);
 
 cudaError_t launch_point_fp64(const PointParams& p, int grid, size_t smem, cudaStream_t s);
 int point_fp64_blocks_per_sm(size_t smem);
+cudaError_t launch_point_df64(const PointParams& p, int grid, size_t smem, cudaStream_t s);
+int point_df64_blocks_per_sm(size_t smem);
+// Register-resident FP32-pair kernel (windows up to 96 bands): tile shape for a
+// maximum window (-1 if none), its thread count, shared memory and occupancy.
+int df64r_shape(int nbmax);
+int df64r_num_shapes();
+int df64r_tile(int shape, int which);  // RA (which = 0) or RB (which = 1) of a shape
+bool df64r_shape_fits(int shape, int nbmax);
+int df64r_threads(int shape, int nbmax);
+size_t point_df64r_smem(int nbmax, int mmax, int mode);
+int point_df64r_blocks_per_sm(int shape, int threads, size_t smem);
+cudaError_t launch_point_df64r(int shape, const PointParams& p, int grid, int threads, size_t smem,
+                               cudaStream_t s);
+// Shared memory of k_point_df64 with nmat matrices (frequencies) per CTA step.
+size_t point_df64_smem(int nbmax, int mmax, int mode, int a_in_smem, int nmat);
+// out[i] = FP32 pair (hi, lo) of in[i], hi = RN(x), lo = RN(x - hi), for n complex numbers
+cudaError_t launch_split_df64(const double2* in, float4* out, int64_t n, cudaStream_t s);
 cudaError_t launch_occ_finalize(const KInfo* kinfo, const SInfo* sinfo, const double* trHE,
                                 const double* mu, const double* occ_part, int n_chunks, int n_k,
                                 double* kN, double* kdN, cudaStream_t s);

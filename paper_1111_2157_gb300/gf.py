@@ -24,7 +24,8 @@ DTYPE = {"c128": 0, "c64": 1}
 
 EXPORTS = ["gf_create", "gf_destroy", "gf_set_hamiltonian", "gf_set_projectors", "gf_set_sigma",
            "gf_local", "gf_occupation", "gf_find_mu", "gf_density_matrix", "gf_backward",
-           "gf_evaluate", "gf_occupation_static", "gf_last_error", "gf_last_stats"]
+           "gf_evaluate", "gf_occupation_static", "gf_last_error", "gf_last_stats",
+           "gf_tuning_log"]
 
 
 class GFError(RuntimeError):
@@ -69,10 +70,12 @@ def load():
                                          ctypes.c_double, ctypes.c_int32, vp, dp, dp]
     lib.gf_last_error.argtypes = [vp]
     lib.gf_last_error.restype = ctypes.c_char_p
+    lib.gf_tuning_log.argtypes = [vp]
+    lib.gf_tuning_log.restype = ctypes.c_char_p
     lib.gf_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   dp, dp]
     for name in EXPORTS:
-        if name not in ("gf_last_error",):
+        if name not in ("gf_last_error", "gf_tuning_log"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -274,6 +277,10 @@ class GreensFunction:
                                          ctypes.c_void_p(o.ptr),
                                          mub.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out, mub
+
+    def tuning_log(self):
+        """Kernel configuration chosen for this context (autotuner report)."""
+        return self.lib.gf_tuning_log(self.h).decode()
 
     def stats(self):
         """dict(launches, points, kernel_ms, flops) of the last compute call."""

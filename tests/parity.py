@@ -40,3 +40,28 @@ def oracle_all(s, mu, tail_order=2, gloc=True):
     r = o.density(s.H, s.P, s.sigma, s.sigma_inf, s.beta, mu, weights=s.weights, tail_order=tail_order)
     gl = o.local(s.H, s.P, s.sigma, s.beta, mu, weights=s.weights) if gloc else None
     return r, gl
+
+
+def check_system_set(systems, mus, tol, precision="fp64", tail_order=2, input_dtype="c128",
+                     report=None):
+    """Every output of the CUDA path (G_loc, N, dN/dmu, n_corr, rho) against the oracle."""
+    g = make_gf(systems, precision=precision, tail_order=tail_order, input_dtype=input_dtype)
+    gl = g.local(mus).cpu().numpy()
+    n, dn = g.occupation(mus)
+    rho, nc = g.density_matrix(mus)
+    rho = rho.cpu().numpy()
+    g.close()
+    gls = split_sys(gl, systems, lambda s: s.n_iw * s.m * s.m)
+    rhos = split_sys(rho, systems, lambda s: int(np.sum(s.nb.astype(np.int64) ** 2)))
+    for i, s in enumerate(systems):
+        r, glo = oracle_all(s, mus[i], tail_order=tail_order)
+        errs = {"G_loc": rel(gls[i], glo.reshape(-1)),
+                "N": abs(n[i] - r["N"]) / max(1.0, abs(r["N"])),
+                "dN_dmu": abs(dn[i] - r["dN_dmu"]) / abs(r["dN_dmu"]),
+                "n_corr": abs(nc[i] - r["n_corr"]) / max(1.0, abs(r["n_corr"])),
+                "rho": rel(rhos[i], pack(r["rho"]))}
+        if report is not None:
+            report.append(errs)
+        for name, err in errs.items():
+            t = tol[name] if isinstance(tol, dict) else tol
+            assert err < t, f"{name} system {i}: {err:.3e} >= {t:.1e}"
