@@ -140,37 +140,74 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return r;
 }
 
-// In-place Gauss-Jordan inversion in FP32-pair arithmetic; the same pivoting
-// and bookkeeping as the FP64 kernel (pivot key from the head words).
+// Pivot search of column j over rows j..N-1 by one warp; lane 0 stores the
+// pivot row and the pair reciprocal of the pivot.
+__device__ __forceinline__ void pivot_warp(const float4* A, int N, int ld, int j, int lane, int* s_p,
+                                           float4* s_r, int* piv, int* status) {
+  unsigned best = 0u;
+  int bi = 0x7fffffff;
+  for (int i = j + lane; i < N; i += 32) {
+    const unsigned key = pivot_key_f(A[i * ld + j]);
+    if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
+  }
+  for (int off = 16; off; off >>= 1) {
+    const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) {
+    const cf pv = ld4(A[bi * ld + j]);
+    if (best == 0u || best >= 0x7f800000u) atomicOr(status, kFlagSingular);
+    *s_p = bi;
+    *s_r = st4(crcp_df(pv));
+    piv[j] = bi;
+  }
+}
+
+// a' = a - l u for one entry of the elimination of column j (row j takes urow,
+// column j takes -l r since urow[j] = r).
+// (h, l) <- h + l assuming |h| >= |l| (Dekker); after an update the low word
+// holds only rounding errors of the high word.
+__device__ __forceinline__ void renorm_fast(float& h, float& l) {
+  const float s = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(s, h));
+  h = s;
+}
+
+__device__ __forceinline__ void elim_entry(float4* A, int ld, const float4* col, const float4* urow,
+                                           int i, int c, int j) {
+  float4* a = &A[i * ld + c];
+  const float4 u4 = urow[c];
+  if (i == j) {
+    *a = u4;
+  } else {
+    const cf l = cneg(ld4(col[i]));
+    const float4 a0 = *a;
+    cf v = (c == j) ? czero() : ld4(a0);
+    cacc(v, l, ld4(u4));
+    renorm_fast(v.rh, v.rl);
+    renorm_fast(v.ih, v.il);
+    *a = st4(v);
+  }
+}
+
+// In-place Gauss-Jordan inversion in FP32-pair arithmetic with one pivot of
+// lookahead; the same pivoting and bookkeeping as the FP64 kernel (pivot key
+// from the head words).  Step j: (b) scaled pivot row to urow, old row j to row
+// p, column j to col; (c) warp 0 eliminates column j+1 first, then searches it
+// for the next pivot and forms its reciprocal, while warps 1..7 eliminate every
+// other column.  Two barriers per pivot; the pivot search is off the critical path.
 __device__ void gauss_jordan_df64(float4* A, int N, int ld, float4* col, float4* urow, int* piv,
                                   int* idx, int* status) {
-  __shared__ int s_p;
-  __shared__ float4 s_r;
+  __shared__ int s_p[2];
+  __shared__ float4 s_r[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) pivot_warp(A, N, ld, 0, lane, &s_p[0], &s_r[0], piv, status);
+  __syncthreads();
   for (int j = 0; j < N; ++j) {
-    if (warp == 0) {
-      unsigned best = 0u;
-      int bi = 0x7fffffff;
-      for (int i = j + lane; i < N; i += 32) {
-        const unsigned key = pivot_key_f(A[i * ld + j]);
-        if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
-      }
-      for (int off = 16; off; off >>= 1) {
-        const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) {
-        const cf pv = ld4(A[bi * ld + j]);
-        if (best == 0u || best >= 0x7f800000u) atomicOr(status, kFlagSingular);
-        s_p = bi;
-        s_r = st4(crcp_df(pv));
-        piv[j] = bi;
-      }
-    }
-    __syncthreads();
-    const int pr = s_p;
-    const cf r = ld4(s_r);
+    const int bf = j & 1;
+    const int pr = s_p[bf];
+    const cf r = ld4(s_r[bf]);
     for (int c = tid; c < N; c += kThreads) {
       const cf vp = ld4(A[pr * ld + c]);
       if (c == j) {
@@ -185,24 +222,24 @@ __device__ void gauss_jordan_df64(float4* A, int N, int ld, float4* col, float4*
     }
     for (int i = tid; i < N; i += kThreads) col[i] = (i == pr) ? A[j * ld + j] : A[i * ld + j];
     __syncthreads();
-    const int total = N * N;
-    int i = tid / N, c = tid - (tid / N) * N;
-    const int di = kThreads / N, dc = kThreads - (kThreads / N) * N;
-    for (int e = tid; e < total; e += kThreads) {
-      float4* a = &A[i * ld + c];
-      const float4 u4 = urow[c];
-      if (i == j) {
-        *a = u4;
-      } else {
-        const cf l = cneg(ld4(col[i]));
-        const float4 a0 = *a;
-        cf v = (c == j) ? czero() : ld4(a0);
-        cacc(v, l, ld4(u4));
-        cnorm(v);
-        *a = st4(v);
+    const int jn = j + 1;
+    if (jn < N && warp == 0) {
+      for (int i = lane; i < N; i += 32) elim_entry(A, ld, col, urow, i, jn, j);
+      __syncwarp();
+      pivot_warp(A, N, ld, jn, lane, &s_p[bf ^ 1], &s_r[bf ^ 1], piv, status);
+    } else {
+      // every (i, c) with c != jn, over warps 1..7 (all warps on the last step)
+      const int w0 = (jn < N) ? 32 : 0;
+      const int nt = kThreads - w0, me = tid - w0;
+      const int ncol = (jn < N) ? N - 1 : N;
+      const int total = N * ncol;
+      int i = me / ncol, cc = me - (me / ncol) * ncol;
+      const int di = nt / ncol, dc = nt - (nt / ncol) * ncol;
+      for (int e = me; e < total; e += nt) {
+        elim_entry(A, ld, col, urow, i, cc + (cc >= jn ? 1 : 0), j);
+        i += di; cc += dc;
+        if (cc >= ncol) { cc -= ncol; ++i; }
       }
-      i += di; c += dc;
-      if (c >= N) { c -= N; ++i; }
     }
     __syncthreads();
   }
