@@ -133,9 +133,10 @@ __device__ __forceinline__ double block_sum_any(double v, double* red) {
 }
 
 // Shared memory (16-byte elements): P_k | T (Sigma P, then Y) | Sigma / Gbar |
-// G copy (N x ld) | col x2 | urow x2 | rowj x2 | Z | A_k | B_k, then piv, idx.
+// G copy (N x ld) | col x2 | urow x2 | rowj x2 | next column x2 | Z | A_k | B_k,
+// then piv, idx.
 struct LayoutR {
-  int offP, offT, offS, offG, offCol, offU, offRj, offZ, offQa, offQb, n16;
+  int offP, offT, offS, offG, offCol, offU, offRj, offCx, offZ, offQa, offQb, n16;
   size_t bytes;
 };
 __host__ __device__ inline LayoutR make_layout_r(int nbmax, int mmax, int mode) {
@@ -149,6 +150,7 @@ __host__ __device__ inline LayoutR make_layout_r(int nbmax, int mmax, int mode) 
   L.offCol = o; o += 2 * nbmax;
   L.offU = o; o += 2 * nbmax;
   L.offRj = o; o += 2 * nbmax;
+  L.offCx = o; o += 2 * nbmax;
   L.offZ = o; o += (mode & kAdj) ? mmax * nbmax : 0;
   L.offQa = o; o += (mode & kAdj) ? mmax * mmax : 0;
   L.offQb = o; o += (mode & kAdj) ? mmax * mmax : 0;
@@ -189,8 +191,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_df64r(const PointParams p)
     const int N = ki.nb, M = si.m, ld = N | 1;
     // thread grid of this k-point's window
     const int TR = (N + RA - 1) / RA, TC = (N + RB - 1) / RB;
-    const bool owner = tid < TR * TC;
-    const int tr = owner ? tid / TC : 0, tc = owner ? tid - (tid / TC) * TC : 0;
+    const int ot = tid - 32;  // warp 0 owns no tile: it runs the pivot lookahead
+    const bool owner = ot >= 0 && ot < TR * TC;
+    const int tr = owner ? ot / TC : 0, tc = owner ? ot - (ot / TC) * TC : 0;
     const float4* Hk = p.Hd + ki.offH;
     const float4* Pg = p.Pd + ki.offP;
     const double mu = p.mu[ki.sys];
@@ -260,109 +263,133 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_df64r(const PointParams p)
             for (int b = 0; b < RB; ++b) cnorm(A[a][b]);
         }
       }
-      // Gauss-Jordan with partial pivoting on the register tiles.  Step j:
-      //  (A) the owners of column j publish it to col and zero it in registers;
-      //  (P) warp 0 searches col for the pivot row p, forms r = 1/pivot, and turns
-      //      col into the multipliers: l[j] = 0, l[p] = old A[j][j], l[i] = A[i][j];
-      //  (R) the owners of row p publish urow = r A[p][.] (urow[j] = r), the
-      //      owners of row j publish the old row j (rowj);
-      //  (U) rows j and p are replaced by urow and rowj in the owners' registers,
-      //      then every owned entry takes the same update a -= l[i] urow[c].
-      // col, urow and rowj are double-buffered by the parity of j, so (A) of the
-      // next step needs no barrier after (U).  Three barriers per pivot and no
-      // divergent arithmetic.
+      // Gauss-Jordan with partial pivoting on the register tiles, one pivot of
+      // lookahead.  Before step j the multipliers l = col (l[j] = 0,
+      // l[p] = A[j][j], l[i] = A[i][j]), the pivot row p and r = 1/pivot are known.
+      //  (R) owners of row p publish urow = r A[p][.] (urow[j] = r), owners of
+      //      row j publish the old row j (rowj), owners of column j+1 publish
+      //      their column j+1 (cnx);
+      //  (U) owners zero column j, replace row j by urow and row p by rowj, and
+      //      update every owned entry a -= l[i] urow[c]; meanwhile warp 0 applies
+      //      the same operations to cnx, searches the new column j+1 for the
+      //      next pivot, forms its reciprocal and the next multipliers.
+      // Two barriers per pivot; the search and the reciprocal overlap the update.
+      if (owner && tc == 0) {
+#pragma unroll
+        for (int a = 0; a < RA; ++a) {
+          const int i = tr + TR * a;
+          if (i < N) sm[L.offCx + p.nbmax + i] = st4(A[a][0]);
+        }
+      }
+      __syncthreads();
+      if (warp == 0) {
+        // pivot of column 0 from the published column (no transformation yet)
+        const float4* cx = sm + L.offCx + p.nbmax;
+        float4* col = sm + L.offCol;
+        unsigned best = 0u;
+        int bi = 0x7fffffff;
+        for (int i = lane; i < N; i += 32) {
+          const unsigned key = pivot_key_f(cx[i]);
+          if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
+        }
+        for (int off = 16; off; off >>= 1) {
+          const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        for (int i = lane; i < N; i += 32) col[i] = (i == 0) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                            : ((i == bi) ? cx[0] : cx[i]);
+        if (lane == 0) {
+          if (best == 0u || best >= 0x7f800000u) atomicOr(p.status, kFlagSingular);
+          s_p[0] = bi;
+          s_pq[0] = bi / TR;
+          s_pm[0] = bi - (bi / TR) * TR;
+          s_r[0] = st4(crcp_df(ld4(cx[bi])));
+          sPiv[0] = bi;
+        }
+      }
+      __syncthreads();
       int jqr = 0, jmr = 0, jqc = 0, jmc = 0;  // j / TR, j % TR, j / TC, j % TC
+      int nqc = (TC > 1) ? 0 : 1, nmc = (TC > 1) ? 1 : 0;  // (j+1) / TC, (j+1) % TC
       for (int j = 0; j < N; ++j) {
         const int bf = j & 1;
         float4* col = sm + L.offCol + bf * p.nbmax;
         float4* urow = sm + L.offU + bf * p.nbmax;
         float4* rowj = sm + L.offRj + bf * p.nbmax;
-        if (owner && tc == jmc) {
-          const int bj = jqc;
-#pragma unroll
-          for (int a = 0; a < RA; ++a)
-#pragma unroll
-            for (int b = 0; b < RB; ++b)
-              if (b == bj) {
-                const int i = tr + TR * a;
-                if (i < N) col[i] = st4(A[a][b]);
-                A[a][b] = czero();
-              }
-        }
-        __syncthreads();
-        if (warp == 0) {
-          unsigned best = 0u;
-          int bi = 0x7fffffff;
-          for (int i = j + lane; i < N; i += 32) {
-            const unsigned key = pivot_key_f(col[i]);
-            if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
-          }
-          for (int off = 16; off; off >>= 1) {
-            const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-          }
-          if (lane == 0) {
-            const float4 pv4 = col[bi];
-            const float4 ajj = col[j];
-            if (best == 0u || best >= 0x7f800000u) atomicOr(p.status, kFlagSingular);
-            s_p[bf] = bi;
-            s_pq[bf] = bi / TR;
-            s_pm[bf] = bi - (bi / TR) * TR;
-            s_r[bf] = st4(crcp_df(ld4(pv4)));
-            sPiv[j] = bi;
-            col[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (bi != j) col[bi] = ajj;
-          }
-        }
-        __syncthreads();
+        float4* cx = sm + L.offCx + bf * p.nbmax;
         const int pr = s_p[bf], prq = s_pq[bf], prm = s_pm[bf];
         const cf r = ld4(s_r[bf]);
-        if (owner && tr == prm) {
-          const int ap = prq;
+        const int jn = j + 1;
+        if (owner) {
+          if (tr == prm) {
 #pragma unroll
-          for (int a = 0; a < RA; ++a)
-            if (a == ap)
+            for (int a = 0; a < RA; ++a)
+              if (a == prq)
 #pragma unroll
-              for (int b = 0; b < RB; ++b) {
-                const int c = tc + TC * b;
-                if (c < N) {
-                  cf u = r;
-                  if (c != j) {
-                    u = czero();
-                    cacc(u, A[a][b], r);
-                    cnorm(u);
+                for (int b = 0; b < RB; ++b) {
+                  const int c = tc + TC * b;
+                  if (c < N) {
+                    cf u = r;
+                    if (c != j) {
+                      u = czero();
+                      cacc(u, A[a][b], r);
+                      cnorm(u);
+                    }
+                    urow[c] = st4(u);
                   }
-                  urow[c] = st4(u);
                 }
-              }
-        }
-        if (owner && tr == jmr) {
-          const int aj = jqr;
+          }
+          if (tr == jmr) {
 #pragma unroll
-          for (int a = 0; a < RA; ++a)
-            if (a == aj)
+            for (int a = 0; a < RA; ++a)
+              if (a == jqr)
 #pragma unroll
-              for (int b = 0; b < RB; ++b) {
-                const int c = tc + TC * b;
-                if (c < N) rowj[c] = st4(A[a][b]);
-              }
+                for (int b = 0; b < RB; ++b) {
+                  const int c = tc + TC * b;
+                  if (c < N) rowj[c] = st4(A[a][b]);
+                }
+          }
+          if (jn < N && tc == nmc) {
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+              for (int b = 0; b < RB; ++b)
+                if (b == nqc) {
+                  const int i = tr + TR * a;
+                  if (i < N) cx[i] = st4(A[a][b]);
+                }
+          }
         }
         __syncthreads();
         if (owner) {
-          if (tr == jmr || (pr != j && tr == prm)) {
-            const int aj = jqr, ap = prq;
-            const bool own_j = (tr == jmr), own_p = (pr != j && tr == prm);
+          const bool own_j = (tr == jmr), own_p = (pr != j && tr == prm);
+          if (own_j || own_p) {
 #pragma unroll
             for (int a = 0; a < RA; ++a)
 #pragma unroll
               for (int b = 0; b < RB; ++b) {
                 const int c = tc + TC * b;
                 if (c < N) {
-                  if (own_j && a == aj) A[a][b] = ld4(urow[c]);
-                  if (own_p && a == ap) A[a][b] = ld4(rowj[c]);
+                  if (own_p && a == prq && c != j) A[a][b] = ld4(rowj[c]);
                 }
               }
+          }
+          if (tc == jmc) {
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+              for (int b = 0; b < RB; ++b)
+                if (b == jqc) A[a][b] = czero();
+          }
+          if (own_j) {
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+              if (a == jqr)
+#pragma unroll
+                for (int b = 0; b < RB; ++b) {
+                  const int c = tc + TC * b;
+                  if (c < N) A[a][b] = ld4(urow[c]);
+                }
           }
           cf lv[RA];
 #pragma unroll
@@ -377,9 +404,45 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_df64r(const PointParams p)
 #pragma unroll
             for (int a = 0; a < RA; ++a) csub_prod(A[a][b], lv[a], u);
           }
+        } else if (warp == 0 && jn < N) {
+          // lookahead: column j+1 after step j, exactly as its owners compute it
+          float4* ncol = sm + L.offCol + (bf ^ 1) * p.nbmax;
+          const cf u = ld4(urow[jn]);
+          unsigned best = 0u;
+          int bi = 0x7fffffff;
+          for (int i = lane; i < N; i += 32) {
+            cf v;
+            if (i == j) v = ld4(urow[jn]);
+            else if (i == pr) v = ld4(rowj[jn]);
+            else v = ld4(cx[i]);
+            csub_prod(v, ld4(col[i]), u);
+            cx[i] = st4(v);
+            if (i >= jn) {
+              const unsigned key = pivot_key_f(cx[i]);
+              if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
+            }
+          }
+          for (int off = 16; off; off >>= 1) {
+            const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          }
+          __syncwarp();
+          for (int i = lane; i < N; i += 32)
+            ncol[i] = (i == jn) ? make_float4(0.f, 0.f, 0.f, 0.f) : ((i == bi) ? cx[jn] : cx[i]);
+          if (lane == 0) {
+            if (best == 0u || best >= 0x7f800000u) atomicOr(p.status, kFlagSingular);
+            s_p[bf ^ 1] = bi;
+            s_pq[bf ^ 1] = bi / TR;
+            s_pm[bf ^ 1] = bi - (bi / TR) * TR;
+            s_r[bf ^ 1] = st4(crcp_df(ld4(cx[bi])));
+            sPiv[jn] = bi;
+          }
         }
+        __syncthreads();
         if (++jmr == TR) { jmr = 0; ++jqr; }
         if (++jmc == TC) { jmc = 0; ++jqc; }
+        if (++nmc == TC) { nmc = 0; ++nqc; }
       }
       // inverse (columns permuted by idx) to shared memory for the epilogues
       if (owner) {
@@ -540,7 +603,7 @@ struct Shape {
   int ra, rb, maxt, nmax;
 };
 constexpr Shape kShapes[] = {
-    {1, 1, 512, 8}, {2, 2, 512, 16}, {2, 5, 512, 40}, {4, 4, 512, 64}, {3, 6, 512, 96},
+    {1, 1, 512, 8}, {2, 2, 512, 16}, {2, 5, 512, 40}, {4, 4, 512, 64}, {3, 7, 512, 96},
 };
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 
@@ -589,7 +652,7 @@ bool df64r_shape_fits(int shape, int nbmax) {
 int df64r_threads(int shape, int nbmax) {
   const Shape sh = kShapes[shape];
   const int t = ((nbmax + sh.ra - 1) / sh.ra) * ((nbmax + sh.rb - 1) / sh.rb);
-  return ((t + 31) / 32) * 32;
+  return 32 + ((t + 31) / 32) * 32;  // owners plus the pivot warp
 }
 
 size_t point_df64r_smem(int nbmax, int mmax, int mode) {
@@ -602,7 +665,7 @@ int point_df64r_blocks_per_sm(int shape, int threads, size_t smem) {
     case 1: return bps_r<2, 2, 512, 1>(threads, smem);
     case 2: return bps_r<2, 5, 512, 1>(threads, smem);
     case 3: return bps_r<4, 4, 512, 1>(threads, smem);
-    case 4: return bps_r<3, 6, 512, 1>(threads, smem);
+    case 4: return bps_r<3, 7, 512, 1>(threads, smem);
   }
   return 0;
 }
@@ -614,7 +677,7 @@ cudaError_t launch_point_df64r(int shape, const PointParams& p, int grid, int th
     case 1: return launch_r<2, 2, 512, 1>(p, grid, threads, smem, s);
     case 2: return launch_r<2, 5, 512, 1>(p, grid, threads, smem, s);
     case 3: return launch_r<4, 4, 512, 1>(p, grid, threads, smem, s);
-    case 4: return launch_r<3, 6, 512, 1>(p, grid, threads, smem, s);
+    case 4: return launch_r<3, 7, 512, 1>(p, grid, threads, smem, s);
   }
   return cudaErrorInvalidValue;
 }
