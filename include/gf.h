@@ -73,7 +73,15 @@ typedef struct {
     int32_t tail_order;       /* 1 or 2 (2 recommended)                                          */
     int32_t device;           /* CUDA device ordinal                                             */
     void *stream;             /* cudaStream_t to order all work on, or NULL (legacy default)     */
+    int32_t flags;            /* GF_FLAG_* bits                                                  */
 } gf_desc;
+
+/* gf_desc.flags: replay the N(mu) evaluation (gf_occupation, each step of
+ * gf_find_mu) as a CUDA graph.  The first evaluation runs normally (it sizes the
+ * scratch and runs the autotuner), the second is captured on a library-owned
+ * stream, later ones replay the graph with mu read from pinned memory at launch.
+ * The library orders the replay after the context's stream and waits for it. */
+#define GF_FLAG_GRAPH 1
 
 /* Create a context: validates the descriptor, copies it, selects the device
  * and allocates the device-side tables.  *out is NULL on failure.

@@ -117,6 +117,15 @@ struct gf_ctx {
   double* hp_sys2() { return hpin + 5 * n_sys + 1; }
   std::string err;
   std::map<int, bool> tuned;  // mixed path: register kernel chosen, per mode
+  // CUDA-graph replay of the N(mu) evaluation (GF_FLAG_GRAPH)
+  bool use_graph = false;
+  int occ_calls = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_user = nullptr;
+  cudaGraphExec_t occ_exec = nullptr;
+  bool capturing = false;
+  int64_t occ_launches = 0, occ_points = 0;
+  double occ_flops = 0.0;
   std::string tune_log;
   int64_t last_launches = 0, last_points = 0;
   double last_kernel_ms = 0.0, last_flops = 0.0;
@@ -383,7 +392,8 @@ gf_status run_points(gf_ctx* c, int mode) {
       GF_CU(cudaEventCreate(&e));
       c->ev.push_back(e);
     }
-    GF_CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
+    // (events recorded inside a CUDA graph cannot be timed: a replay is timed as a whole)
+    if (!c->capturing) GF_CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
     if (use_r)
       GF_CU(gf::launch_point_df64r(rshape, p, std::min(rgrid, std::max(1, i1 - i0)), rthreads, rsmem,
                                    c->stream));
@@ -391,8 +401,10 @@ gf_status run_points(gf_ctx* c, int mode) {
       GF_CU(gf::launch_point_df64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
     else
       GF_CU(gf::launch_point_fp64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
-    GF_CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
-    c->ev_used += 2;
+    if (!c->capturing) {
+      GF_CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+      c->ev_used += 2;
+    }
     c->last_launches += 1;
     if (kred) {
       int max_total = 0;
@@ -420,10 +432,13 @@ void reset_stats(gf_ctx* c) {
   c->ev_used = 0;
 }
 
-gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
-  gf_status st = upload_mu(c, mu);
-  if (st) return st;
-  st = run_points(c, gf::kOcc);
+// Enqueue one N(mu) evaluation (mu already in c->hp_mu): upload, point kernel,
+// finalize, read-back of (N, dN/dmu) and the status word.  No synchronisation,
+// so the sequence can be captured into a CUDA graph.
+gf_status enqueue_occupation(gf_ctx* c) {
+  GF_CU(cudaMemcpyAsync(c->mu.p, c->hp_mu(), sizeof(double) * c->n_sys, cudaMemcpyHostToDevice,
+                        c->stream));
+  gf_status st = run_points(c, gf::kOcc);
   if (st) return st;
   GF_CU(gf::launch_occ_finalize(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->trHE.as<double>(),
                                 c->mu.as<double>(), c->occ_part.as<double>(), c->n_chunks, c->n_k,
@@ -434,13 +449,102 @@ gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn
   c->last_launches += 2;
   GF_CU(cudaMemcpyAsync(c->hp_sys(), c->sysout.p, sizeof(double) * 2 * c->n_sys,
                         cudaMemcpyDeviceToHost, c->stream));
-  st = sync_and_check(c);
-  if (st) return st;
-  for (int s = 0; s < c->n_sys; ++s) {
-    if (n_out) n_out[s] = c->hp_sys()[2 * s];
-    if (dn_out) dn_out[s] = c->hp_sys()[2 * s + 1];
+  GF_CU(cudaMemcpyAsync(c->hp_status(), c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  return GF_OK;
+}
+
+// After the stream (or the graph's stream) drained: kernel times, status, results.
+gf_status finish_occupation(gf_ctx* c, cudaStream_t s, double* n_out, double* dn_out) {
+  GF_CU(cudaStreamSynchronize(s));
+  for (int i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    GF_CU(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+    c->last_kernel_ms += ms;
+  }
+  c->ev_used = 0;
+  int flags = 0;
+  std::memcpy(&flags, c->hp_status(), sizeof(int));
+  if (flags & gf::kFlagSingular)
+    return fail(c, GF_ESINGULAR, "zero or non-finite pivot in a (k, i w_n) inverse");
+  for (int s2 = 0; s2 < c->n_sys; ++s2) {
+    if (n_out) n_out[s2] = c->hp_sys()[2 * s2];
+    if (dn_out) dn_out[s2] = c->hp_sys()[2 * s2 + 1];
   }
   return GF_OK;
+}
+
+gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+  if (!mu) return fail(c, GF_EINVAL, "mu is NULL");
+  for (int s2 = 0; s2 < c->n_sys; ++s2)
+    if (!std::isfinite(mu[s2])) return fail(c, GF_EINVAL, "mu is not finite");
+  gf_status st = check_ready(c);
+  if (st) return st;
+  if (!c->use_graph || c->occ_calls == 0) {
+    // ordinary enqueue (also the warm-up of graph mode: scratch, autotuner)
+    ++c->occ_calls;
+    GF_CU(cudaStreamSynchronize(c->stream));  // hp_mu is about to be rewritten
+    for (int s2 = 0; s2 < c->n_sys; ++s2) c->hp_mu()[s2] = mu[s2];
+    st = enqueue_occupation(c);
+    if (st) return st;
+    return finish_occupation(c, c->stream, n_out, dn_out);
+  }
+  // graph mode: E_inf outside the graph (inputs may have changed), then replay
+  GF_CU(cudaStreamSynchronize(c->stream));
+  st = ensure_einf(c);
+  if (st) return st;
+  for (int s2 = 0; s2 < c->n_sys; ++s2) c->hp_mu()[s2] = mu[s2];
+  if (!c->occ_exec) {
+    GF_CU(cudaStreamSynchronize(c->stream));
+    const cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    const int64_t l0 = c->last_launches, p0 = c->last_points;
+    const double f0 = c->last_flops;
+    c->ev_used = 0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      c->capturing = true;
+      st = enqueue_occupation(c);
+      c->capturing = false;
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+      if (st == GF_OK && e2 != cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    if (st) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(c, GF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->occ_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->occ_exec = nullptr;
+      return fail(c, GF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    c->occ_launches = c->last_launches - l0;
+    c->occ_points = c->last_points - p0;
+    c->occ_flops = c->last_flops - f0;
+    c->last_launches = l0;
+    c->last_points = p0;
+    c->last_flops = f0;
+  }
+  GF_CU(cudaEventRecord(c->ev_user, c->stream));
+  GF_CU(cudaStreamWaitEvent(c->cap_stream, c->ev_user, 0));
+  if (c->ev.size() < 2) {
+    cudaEvent_t e0, e1;
+    GF_CU(cudaEventCreate(&e0));
+    GF_CU(cudaEventCreate(&e1));
+    c->ev.push_back(e0);
+    c->ev.push_back(e1);
+  }
+  GF_CU(cudaEventRecord(c->ev[0], c->cap_stream));
+  GF_CU(cudaGraphLaunch(c->occ_exec, c->cap_stream));
+  GF_CU(cudaEventRecord(c->ev[1], c->cap_stream));
+  c->ev_used = 2;
+  c->last_launches += c->occ_launches;
+  c->last_points += c->occ_points;
+  c->last_flops += c->occ_flops;
+  return finish_occupation(c, c->cap_stream, n_out, dn_out);
 }
 
 }  // namespace
@@ -481,6 +585,7 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   c->tail_order = d->tail_order;
   c->device = d->device;
   c->stream = static_cast<cudaStream_t>(d->stream);
+  c->use_graph = (d->flags & GF_FLAG_GRAPH) != 0;
   c->nb.resize(c->n_k);
   c->ksys.resize(c->n_k);
   for (int k = 0; k < c->n_k; ++k) {
@@ -633,6 +738,10 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
                              cudaMemcpyHostToDevice, c->stream)))
       return e;
     if ((e = cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream))) return e;
+    if (c->use_graph) {
+      if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking))) return e;
+      if ((e = cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming))) return e;
+    }
     return cudaStreamSynchronize(c->stream);
   };
   cudaError_t e = alloc_all();
@@ -656,6 +765,9 @@ gf_status gf_destroy(gf_ctx* c) {
                     &c->sysout2, &c->Hd, &c->Pd, &c->Sd, &c->Gbd};
   for (DevBuf* b : bufs) release(*b);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->occ_exec) cudaGraphExecDestroy(c->occ_exec);
+  if (c->ev_user) cudaEventDestroy(c->ev_user);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->hpin) cudaFreeHost(c->hpin);
   delete c;
   return GF_OK;

@@ -41,7 +41,9 @@ class GFDesc(ctypes.Structure):
                 ("m_system", ctypes.POINTER(ctypes.c_int32)), ("n_iw", ctypes.c_int32),
                 ("beta", ctypes.POINTER(ctypes.c_double)), ("k_weight", ctypes.POINTER(ctypes.c_double)),
                 ("precision", ctypes.c_int32), ("input_dtype", ctypes.c_int32),
-                ("tail_order", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("tail_order", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("flags", ctypes.c_int32)]
+GF_FLAG_GRAPH = 1
 
 
 def load():
@@ -114,7 +116,7 @@ class GreensFunction:
     """
 
     def __init__(self, nb, m, n_iw, beta, k_system=None, n_k=None, k_weight=None, precision="fp64",
-                 input_dtype="c128", tail_order=2, device=0, stream=None):
+                 input_dtype="c128", tail_order=2, device=0, stream=None, graph=False):
         import torch
         self.lib = load()
         self.device = int(device)
@@ -152,6 +154,7 @@ class GreensFunction:
         d.tail_order = int(tail_order)
         d.device = self.device
         d.stream = int(stream)
+        d.flags = GF_FLAG_GRAPH if graph else 0
         h = ctypes.c_void_p()
         st = self.lib.gf_create(ctypes.byref(h), ctypes.byref(d))
         if st != GF_OK:
@@ -164,14 +167,15 @@ class GreensFunction:
         self.tot_sinf = int(np.sum(self.m.astype(np.int64) ** 2))
 
     @classmethod
-    def for_systems(cls, systems, precision="fp64", input_dtype="c128", tail_order=2, device=0):
+    def for_systems(cls, systems, precision="fp64", input_dtype="c128", tail_order=2, device=0,
+                    graph=False):
         """Context for a list of ``synth.System`` (one or several, ragged or not)."""
         nb = np.concatenate([s.nb for s in systems])
         ks = np.concatenate([np.full(s.nk, i, np.int32) for i, s in enumerate(systems)])
         n_iw = systems[0].n_iw
         return cls(nb, [s.m for s in systems], n_iw, [s.beta for s in systems],
                    k_system=ks if len(systems) > 1 else None, precision=precision,
-                   input_dtype=input_dtype, tail_order=tail_order, device=device)
+                   input_dtype=input_dtype, tail_order=tail_order, device=device, graph=graph)
 
     def _check(self, st):
         if st != GF_OK:

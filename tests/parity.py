@@ -16,10 +16,10 @@ def pack(blocks):
     return np.concatenate([np.asarray(b).reshape(-1) for b in blocks])
 
 
-def make_gf(systems, precision="fp64", tail_order=2, input_dtype="c128"):
+def make_gf(systems, precision="fp64", tail_order=2, input_dtype="c128", graph=False):
     from paper_1111_2157_gb300.gf import GreensFunction
     g = GreensFunction.for_systems(systems, precision=precision, tail_order=tail_order,
-                                   input_dtype=input_dtype)
+                                   input_dtype=input_dtype, graph=graph)
     g.set_hamiltonian(pack([pack(s.H) for s in systems]))
     g.set_projectors(pack([pack(s.P) for s in systems]))
     g.set_sigma(pack([s.sigma for s in systems]), pack([s.sigma_inf for s in systems]))

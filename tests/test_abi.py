@@ -47,7 +47,7 @@ def _desc(**kw):
     d = gf.GFDesc()
     d.n_systems, d.n_k, d.nb, d.nb_uniform = 1, 4, None, 8
     d.k_system, d.m_system, d.n_iw, d.beta, d.k_weight = None, m, 16, beta, None
-    d.precision, d.input_dtype, d.tail_order, d.device, d.stream = 0, 0, 2, 0, None
+    d.precision, d.input_dtype, d.tail_order, d.device, d.stream, d.flags = 0, 0, 2, 0, None, 0
     for k, v in kw.items():
         setattr(d, k, v)
     return d, (m, beta)
