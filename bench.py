@@ -54,12 +54,16 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the bounded CPU-oracle sample")
+    ap.add_argument("--nk-scale", type=float, default=0.25,
+                    help="batched workload: fraction of each system's k-points")
     ap.add_argument("--nk", type=int, default=None,
                     help="smaller k-set of the same workload (profiling captures only)")
     ap.add_argument("--n-iw", type=int, default=None,
                     help="fewer Matsubara frequencies (profiling captures only)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="arithmetic of the point kernel (mixed: FP32 pairs on the FP32 pipes)")
+    ap.add_argument("--workload", choices=["ce_like", "nio_like", "batched", "adjoint"],
+                    default="ce_like", help="non-default workloads print one measurement line each")
     ap.add_argument("--peaks", action="store_true",
                     help="compile and run the pipe-throughput microbenchmark (peaks.cu) and exit")
     return ap.parse_args()
@@ -220,10 +224,166 @@ def run_peaks():
     return subprocess.run([str(exe)]).returncode
 
 
+def _sync_time(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def _pack(blocks):
+    return np.concatenate([np.asarray(b).reshape(-1) for b in blocks])
+
+
+def _context(gf, systems, precision, graph=False):
+    g = gf.GreensFunction.for_systems(systems, precision=precision, graph=graph)
+    g.set_hamiltonian(_pack([_pack(s.H) for s in systems]))
+    g.set_projectors(_pack([_pack(s.P) for s in systems]))
+    g.set_sigma(_pack([s.sigma for s in systems]), _pack([s.sigma_inf for s in systems]))
+    return g
+
+
+def run_workload(args):
+    """Measurements on the NiO-like, batched and adjoint workloads (one JSON line each)."""
+    import torch
+    from paper_1111_2157_gb300 import build as gfbuild
+    if not gfbuild.LIB.exists():
+        gfbuild.build()
+    from paper_1111_2157_gb300 import gf, synth
+    import oracle
+    o = oracle.get()
+    o.set_threads(cpu_cores())
+    out = {"workload": args.workload}
+    if args.workload == "nio_like":
+        s = synth.nio_like().systems[0]
+        out["config"] = "N_k=4096, N_b=96, m=20 (2 atoms x 5 d x 2 spin, AFM Sigma), N_w=2048, beta=40, U=8"
+        gm = _context(gf, [s], "mixed", graph=True)
+        (mu, it), t_mu = _sync_time(lambda: gm.find_mu([s.n_target], 0.0, tol=1e-10))
+        n_pass = gm.stats()
+        ev, t_ev = _sync_time(lambda: gm.evaluate(mu, rho=False, n_corr=False))
+        out["mixed"] = {"mu_star": float(mu[0]), "mu_evaluations": it, "find_mu_s": t_mu,
+                        "points_per_s": n_pass["points"] / t_mu, "evaluate_s": t_ev,
+                        "kernel_choice": gm.tuning_log()}
+        g64 = _context(gf, [s], "fp64")
+        (ev64), t64 = _sync_time(lambda: g64.evaluate(mu, rho=False, n_corr=False))
+        out["fp64"] = {"evaluate_s": t64, "points_per_s": s.nk * s.n_iw / t64}
+        out["mixed_speedup_per_pass"] = t64 / t_ev
+        out["N_rel_err_mixed_vs_fp64_gpu"] = abs(ev["N"][0] - ev64["N"][0]) / ev64["N"][0]
+        gl_m, gl_d = ev["gloc"], ev64["gloc"]
+        out["G_loc_rel_err_mixed_vs_fp64_gpu"] = float((gl_m - gl_d).abs().max() / gl_d.abs().max())
+        idx = [0, 1, 1000, 2047]
+        glo = o.local(s.H, s.P, s.sigma, s.beta, float(mu[0]), n_idx=idx)
+        glm = gl_m.cpu().numpy().reshape(s.n_iw, 20, 20)[idx]
+        gld = gl_d.cpu().numpy().reshape(s.n_iw, 20, 20)[idx]
+        out["G_loc_rel_err_vs_oracle_sampled"] = {
+            "mixed": float(np.max(np.abs(glm - glo)) / np.max(np.abs(glo))),
+            "fp64": float(np.max(np.abs(gld - glo)) / np.max(np.abs(glo))),
+            "frequencies": idx}
+        gm.close()
+        g64.close()
+    elif args.workload == "batched":
+        systems = synth.batched(nk_scale=args.nk_scale)
+        systems = systems.systems
+        out["config"] = (f"8 systems, N_k per system {[s.nk for s in systems]}, N_b(k) uniform in [48, 128], "
+                         f"m {[s.m for s in systems]}, N_w=1024, beta=40 (k-sets scaled by {args.nk_scale})")
+        mus = [0.0] * len(systems)
+        res = {}
+        for prec in ("fp64", "mixed"):
+            g = _context(gf, systems, prec)
+            g.occupation(mus)
+            _, t_one = _sync_time(lambda: g.occupation(mus))
+            pts = g.stats()["points"]
+            launches = g.stats()["launches"]
+            g.close()
+            t_per = 0.0
+            n_launch = 0
+            for sy in systems:
+                gi = _context(gf, [sy], prec)
+                gi.occupation([0.0])
+                _, t = _sync_time(lambda: gi.occupation([0.0]))
+                t_per += t
+                n_launch += gi.stats()["launches"]
+                gi.close()
+            gg = _context(gf, systems, prec, graph=True)
+            targets = [sy.n_target for sy in systems]
+            (mu_g, it_g), t_g = _sync_time(lambda: gg.find_mu(targets, 0.0, tol=1e-10))
+            pts_g = gg.stats()["points"]
+            log = gg.tuning_log()
+            gg.close()
+            res[prec] = {"one_launch_s": t_one, "one_launch_points_per_s": pts / t_one,
+                         "one_launch_kernel_launches": launches,
+                         "per_system_s": t_per, "per_system_kernel_launches": n_launch,
+                         "speedup_one_launch_vs_per_system": t_per / t_one,
+                         "graph_find_mu_s": t_g, "graph_find_mu_evaluations": it_g,
+                         "graph_points_per_s": pts_g / t_g, "kernel_choice": log}
+        out.update(res)
+        out["mixed_speedup_one_launch"] = res["fp64"]["one_launch_s"] / res["mixed"]["one_launch_s"]
+    elif args.workload == "adjoint":
+        from paper_1111_2157_gb300.autograd import lattice_green, newton_mu
+        s = synth.adjoint_case().systems[0]
+        out["config"] = "N_k=2048, N_b=64, m=14, N_w=1024, beta=100 (Ce-like generators)"
+        rng = np.random.default_rng(5)
+        gbar = torch.from_numpy(rng.standard_normal(s.sigma.shape) + 1j * rng.standard_normal(s.sigma.shape)).cuda()
+        for prec in ("fp64", "mixed"):
+            g = _context(gf, [s], prec)
+            sigma = torch.tensor(s.sigma, dtype=torch.complex128, device="cuda", requires_grad=True)
+            mu = torch.tensor([0.2], dtype=torch.float64, requires_grad=True)
+            (gl, n), t_f = _sync_time(lambda: lattice_green(g, sigma, mu, s.sigma_inf))
+            loss = (torch.conj(gbar) * gl).real.sum() + 0.7 * n.sum()
+            _, t_b = _sync_time(lambda: loss.backward())
+            (mu_n, it), t_n = _sync_time(lambda: newton_mu(g, sigma.detach(), s.sigma_inf, s.n_target, 0.0))
+            out[prec] = {"forward_s": t_f, "backward_s": t_b, "newton_mu": mu_n, "newton_evaluations": it,
+                         "newton_s": t_n, "grad_sample": [complex(sigma.grad[0, 0, 0].item()).real,
+                                                          float(mu.grad.item())]}
+            if prec == "fp64":
+                h = 1e-6
+                sig0 = sigma.detach()
+                fd = []
+                for (w, a, b) in [(0, 0, 0), (511, 3, 9)]:
+                    val = 0j
+                    for unit in (1.0, 1j):
+                        sp, sm = sig0.clone(), sig0.clone()
+                        sp[w, a, b] += h * unit
+                        sm[w, a, b] -= h * unit
+                        lp = lattice_green(g, sp, mu.detach(), s.sigma_inf)
+                        lm = lattice_green(g, sm, mu.detach(), s.sigma_inf)
+                        fp_ = float(((torch.conj(gbar) * lp[0]).real.sum() + 0.7 * lp[1].sum()).item())
+                        fm_ = float(((torch.conj(gbar) * lm[0]).real.sum() + 0.7 * lm[1].sum()).item())
+                        val += unit * (fp_ - fm_) / (2 * h)
+                    got = complex(sigma.grad[w, a, b].item())
+                    fd.append({"entry": [w, a, b], "adjoint": [got.real, got.imag], "fd": [val.real, val.imag],
+                               "rel_err": abs(got - val) / abs(val)})
+                out["fp64"]["finite_differences"] = fd
+                grad64 = sigma.grad.detach().clone()
+                mug64 = float(mu.grad.item())
+            else:
+                out["mixed"]["grad_rel_err_vs_fp64_gpu"] = float((sigma.grad - grad64).abs().max() / grad64.abs().max())
+                out["mixed"]["mu_grad_rel_err_vs_fp64_gpu"] = abs(mu.grad.item() - mug64) / abs(mug64)
+            g.close()
+        # oracle gradient on a k-subset (same weights as the full problem's first 16 k-points)
+        ks = list(range(16))
+        w = np.full(16, 1.0 / 16)
+        sb_o, mb_o = o.backward(s.H[ks], s.P[ks], s.sigma, s.sigma_inf, s.beta, 0.2,
+                                gloc_bar=gbar.cpu().numpy(), n_bar=0.7, weights=w)
+        sub = synth.System(s.H[ks], s.P[ks], s.pole, s.sigma, s.beta, s.n_target)
+        gsub = _context(gf, [sub], "fp64")
+        sb_g, mb_g = gsub.backward([0.2], gloc_bar=gbar.reshape(-1), n_bar=[0.7])
+        out["oracle_gradient_16k"] = {"sigma_bar_rel_err": float(np.max(np.abs(sb_g.cpu().numpy() - sb_o.reshape(-1)))
+                                                                 / np.max(np.abs(sb_o))),
+                                      "mu_bar_rel_err": abs(mb_g[0] - mb_o) / abs(mb_o)}
+        gsub.close()
+    print(json.dumps(out, default=float), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.peaks:
         return run_peaks()
+    if args.workload != "ce_like" and args.impl == "ours":
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     ws, rank, local = dist_env()
