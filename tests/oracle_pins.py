@@ -164,6 +164,36 @@ def pin_two_band_inverse(o):
     return worst, 1e-13
 
 
+def pin_woodbury_eigenbasis(o):
+    """G from the eigenbasis of H_k and an m x m solve (Woodbury), an independent route.
+
+    With H = U diag(eps) U^+, Pt = P U and D = diag(i w + mu - eps):
+    U^+ A U = D - Pt^+ Sigma Pt, so G = U [D^-1 + D^-1 Pt^+ (I - Sigma g0)^-1 Sigma Pt D^-1] U^+
+    with g0 = Pt D^-1 Pt^+ (m x m), and P G P^+ = (g0^-1 - Sigma)^-1.
+    """
+    rng = np.random.default_rng(17)
+    s = synth.random_system(23, 3, 9, 4, 32, 10.0)
+    worst = 0.0
+    for k in range(s.nk):
+        eps, U = np.linalg.eigh(s.H[k])
+        Pt = s.P[k] @ U
+        for n in (0, 3, 31):
+            mu = rng.uniform(-1.0, 1.0)
+            wn = (2 * n + 1) * np.pi / s.beta
+            Sig = s.sigma[n]
+            dinv = 1.0 / (1j * wn + mu - eps)
+            g0 = (Pt * dinv) @ np.conj(Pt.T)
+            core = np.linalg.solve(np.eye(s.m) - Sig @ g0, Sig)
+            Gp = np.diag(dinv) + (dinv[:, None] * np.conj(Pt.T)) @ core @ (Pt * dinv)
+            ref = U @ Gp @ np.conj(U.T)
+            got = o.green(s.H[k], s.P[k], Sig, wn, mu)
+            worst = max(worst, np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+            ploc = np.linalg.inv(np.linalg.inv(g0) - Sig)
+            got_loc = s.P[k] @ got @ np.conj(s.P[k].T)
+            worst = max(worst, np.max(np.abs(got_loc - ploc)) / np.max(np.abs(ploc)))
+    return worst, 1e-12
+
+
 def pin_high_frequency_moment(o):
     """w^2 (G - I/(i w)) -> -M2 = -(H + P^+ Sigma(inf) P - mu), with an O(1/w) remainder.
 
@@ -256,5 +286,6 @@ def pin_backward_fd(o):
 
 
 ALL_PINS = [pin_sigma0_gloc, pin_sigma0_density, pin_pseudo_hamiltonian, pin_two_band_inverse,
+            pin_woodbury_eigenbasis,
             pin_high_frequency_moment, pin_symmetry_and_causality, pin_density_bounds,
             pin_dn_dmu_fd, pin_backward_fd]
