@@ -39,6 +39,10 @@ UNIT = "points/s"
 WORKLOAD = "ce_like: N_k=1000, N_b=40, m=14, N_w=1024, beta=100 1/eV, U=6 eV, dense H, two-pole Sigma"
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Peak of the FP32-pair arithmetic of the mixed path, in FP64-equivalent flop/s: the FP32 pipes
+# issue 152 SMs x 128 lanes x 2.07 GHz operations, and one FP32-pair complex multiply-add takes
+# at least 48 of them (4 error-free products with head sums, 12 operations each); 8 flop per CMAC.
+MIXED_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 48 * 8 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 PROFILES = ROOT / "profiles"
 
@@ -62,7 +66,8 @@ def parse():
                     help="fewer Matsubara frequencies (profiling captures only)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="arithmetic of the point kernel (mixed: FP32 pairs on the FP32 pipes)")
-    ap.add_argument("--workload", choices=["ce_like", "nio_like", "batched", "adjoint"],
+    ap.add_argument("--workload", choices=["ce_like", "nio_like", "batched", "adjoint", "lowrank",
+                                           "pole"],
                     default="ce_like", help="non-default workloads print one measurement line each")
     ap.add_argument("--peaks", action="store_true",
                     help="compile and run the pipe-throughput microbenchmark (peaks.cu) and exit")
@@ -237,12 +242,20 @@ def _pack(blocks):
     return np.concatenate([np.asarray(b).reshape(-1) for b in blocks])
 
 
-def _context(gf, systems, precision, graph=False):
-    g = gf.GreensFunction.for_systems(systems, precision=precision, graph=graph)
+def _context(gf, systems, precision, graph=False, lowrank=False):
+    g = gf.GreensFunction.for_systems(systems, precision=precision, graph=graph, lowrank=lowrank)
     g.set_hamiltonian(_pack([_pack(s.H) for s in systems]))
     g.set_projectors(_pack([_pack(s.P) for s in systems]))
     g.set_sigma(_pack([s.sigma for s in systems]), _pack([s.sigma_inf for s in systems]))
     return g
+
+
+def _lr_pole_cases(args, synth):
+    """Ce-like and a NiO-like k-subset; with --nk / --n-iw only a small Ce-like case (profiling)."""
+    if args.nk or args.n_iw:
+        return [("ce_like_small", synth.ce_like(nk=args.nk or 1000, n_iw=args.n_iw or 1024).systems[0])]
+    return [("ce_like", synth.ce_like().systems[0]),
+            ("nio_like_1024k", synth.nio_like(nk=1024).systems[0])]
 
 
 def run_workload(args):
@@ -374,6 +387,74 @@ def run_workload(args):
                                                                  / np.max(np.abs(sb_o))),
                                       "mu_bar_rel_err": abs(mb_g[0] - mb_o) / abs(mb_o)}
         gsub.close()
+    elif args.workload == "lowrank":
+        # eigenbasis (Woodbury) algorithm against the direct inverse, FP64, at fixed mu
+        out["config"] = "Ce-like full size; NiO-like with N_k = 1024 of its 4096 k-points"
+        for name, s in _lr_pole_cases(args, synth):
+            mu = 0.3
+            gd = _context(gf, [s], "fp64")
+            gl = _context(gf, [s], "fp64", lowrank=True)
+            gd.occupation(mu)
+            (nd, dd), td = _sync_time(lambda: gd.occupation(mu))
+            sd = gd.stats()
+            _, t_setup = _sync_time(lambda: gl.occupation(mu))  # includes the eigen-decomposition
+            (nl, dl), tl = _sync_time(lambda: gl.occupation(mu))
+            sl = gl.stats()
+            ed, t_ed = _sync_time(lambda: gd.evaluate(mu, rho=True, n_corr=True))
+            el, t_el = _sync_time(lambda: gl.evaluate(mu, rho=True, n_corr=True))
+            (mu_l, it_l), t_mu = _sync_time(lambda: gl.find_mu(s.n_target, 0.0, tol=1e-10))
+            pts = s.nk * s.n_iw
+            out[name] = {
+                "points": pts,
+                "direct_occupation_s": td, "lowrank_occupation_s": tl,
+                "lowrank_first_call_s_with_eigendecomposition": t_setup,
+                "speedup_occupation": td / tl,
+                "lowrank_points_per_s": pts / tl, "direct_points_per_s": pts / td,
+                "lowrank_kernel_tflops": sl["flops"] / sl["kernel_ms"] / 1e9,
+                "lowrank_frac_of_fp64_peak": sl["flops"] / sl["kernel_ms"] / 1e9 / FP64_PEAK_TFLOPS,
+                "direct_kernel_tflops": sd["flops"] / sd["kernel_ms"] / 1e9,
+                "N_rel_diff": abs(nl[0] - nd[0]) / nd[0], "dN_rel_diff": abs(dl[0] - dd[0]) / dd[0],
+                "evaluate_direct_s": t_ed, "evaluate_lowrank_s": t_el,
+                "G_loc_rel_diff": float((el["gloc"] - ed["gloc"]).abs().max() / ed["gloc"].abs().max()),
+                "rho_rel_diff": float((el["rho"] - ed["rho"]).abs().max() / ed["rho"].abs().max()),
+                "find_mu_s": t_mu, "find_mu_evaluations": it_l}
+            gd.close()
+            gl.close()
+    elif args.workload == "pole":
+        # pseudo-Hamiltonian (pole) path against the Matsubara path, Ce-like and NiO-like
+        from oracle import pole as pole_oracle
+        out["config"] = "Ce-like full size; NiO-like with N_k = 1024 of its 4096 k-points"
+        for name, s in _lr_pole_cases(args, synth):
+            g = _context(gf, [s], "fp64")
+            g.set_sigma_poles([len(s.pole.p)], s.pole.p, s.pole.V.reshape(-1), s.pole.sigma_inf.reshape(-1))
+            mu = 0.3
+            g.pole_occupation(mu)
+            (n_p, d_p), t_occ = _sync_time(lambda: g.pole_occupation(mu))
+            (mu_p, it_p), t_mu = _sync_time(lambda: g.pole_find_mu(s.n_target, 0.0, tol=1e-10))
+            (_, nc_p), t_rho = _sync_time(lambda: g.pole_density_matrix(mu))
+            glp, t_gl = _sync_time(lambda: g.pole_local(mu))
+            eps = np.linspace(-10, 10, 2001)
+            _, t_dos = _sync_time(lambda: g.pole_spectral(mu, eps, 0.05))
+            g.occupation(mu)
+            (n_m, d_m), t_mats = _sync_time(lambda: g.occupation(mu))
+            glm = g.local(mu)
+            ks = list(range(8))
+            sub = pole_oracle.density(s.H[ks], s.P[ks], s.sigma_inf, s.pole.p, s.pole.V, s.beta, mu,
+                                      weights=np.full(8, 1.0 / 8))
+            gs = _context(gf, [synth.System(s.H[ks], s.P[ks], s.pole, s.sigma, s.beta, s.n_target)], "fp64")
+            gs.set_sigma_poles([len(s.pole.p)], s.pole.p, s.pole.V.reshape(-1), s.pole.sigma_inf.reshape(-1))
+            n_sub, _ = gs.pole_occupation(mu)
+            gs.close()
+            out[name] = {
+                "n_poles": len(s.pole.p), "matrix": s.H.shape[1] + len(s.pole.p),
+                "pole_occupation_s": t_occ, "matsubara_occupation_s": t_mats,
+                "speedup_occupation_vs_matsubara": t_mats / t_occ,
+                "pole_find_mu_s": t_mu, "pole_find_mu_evaluations": it_p,
+                "pole_density_matrix_s": t_rho, "pole_local_s": t_gl, "pole_dos_2001_energies_s": t_dos,
+                "N_pole_minus_matsubara": float(n_p[0] - n_m[0]),
+                "G_loc_rel_diff_vs_matsubara": float((glp - glm).abs().max() / glm.abs().max()),
+                "N_rel_err_vs_pole_oracle_8k": abs(n_sub[0] - sub["N"]) / sub["N"]}
+            g.close()
     print(json.dumps(out, default=float), flush=True)
     return 0
 
@@ -499,6 +580,7 @@ def main():
                  "N_rel_err_vs_fp64_gpu": err_n, "G_loc_rel_err_vs_fp64_gpu": err_g,
                  "mu_star": mx["info"]["mu"],
                  "fp64_equivalent_tflops": mt["flops"] / (mt["kernel_ms"] / 1e3) / 1e12,
+                 "frac_of_fp32_pair_peak": mt["flops"] / (mt["kernel_ms"] / 1e3) / 1e12 / MIXED_PEAK_TFLOPS,
                  "arithmetic": "FP32 pairs (hi + lo, error-free transformations) on the FP32 pipes; "
                                "FP64 reductions, Matsubara tail and mu search",
                  "kernel_choice": gm.tuning_log(), "gpu_launches": mt["launches"]}
@@ -553,6 +635,11 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_sample(s, info["mu"], args.cpu_seconds)
 
+    if args.precision == "fp64":
+        peak, peak_source = FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz"
+    else:
+        peak, peak_source = MIXED_PEAK_TFLOPS, ("FP32 pipes: 152 SMs x 128 lanes x 2.07 GHz / 48 FP32 "
+                                                "operations per FP32-pair complex multiply-add x 8 flop")
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -568,10 +655,12 @@ def main():
                        "points_per_step": totals["points"] // args.steps,
                        "mu_evaluations_per_step": info["iters"], "mu_star": info["mu"],
                        "N_at_mu_star": info["N"]},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": ncu_traffic(), "kernel": "k_point_fp64",
-                         "peak_source": "FP64 DFMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": ncu_traffic() if args.precision == "fp64" else None,
+                         "kernel": "k_point_fp64" if args.precision == "fp64"
+                         else "k_point_df64 / k_point_df64r (autotuned)",
+                         "peak_source": peak_source,
                          "kernel_share_of_step": totals["kernel_ms"] / 1e3 / elapsed,
                          "by_pass_tflops": {k: v["flops"] / max(v["kernel_ms"], 1e-9) / 1e9
                                             for k, v in passes.items()},

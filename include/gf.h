@@ -83,6 +83,15 @@ typedef struct {
  * The library orders the replay after the context's stream and waits for it. */
 #define GF_FLAG_GRAPH 1
 
+/* gf_desc.flags: evaluate every (k, i w_n) point in the eigenbasis of H_k
+ * (Woodbury identity): H_k = U diag(eps) U^+ is diagonalised once per
+ * Hamiltonian upload (batched Jacobi kernel), after which a point costs
+ * 3 N_b m^2 + O(m^3) complex multiply-adds instead of N_b^3.  Same results as
+ * the direct inverse up to rounding; FP64 only, N_b <= 256, not with
+ * GF_FLAG_GRAPH.  U^+ G U = D + D Pt^+ K Pt D with D = diag(1/(i w + mu - eps)),
+ * Pt = P_k U, K = (I - Sigma Pt D Pt^+)^{-1} Sigma. */
+#define GF_FLAG_LOWRANK 2
+
 /* Create a context: validates the descriptor, copies it, selects the device
  * and allocates the device-side tables.  *out is NULL on failure.
  * Errors: GF_EINVAL, GF_ENOMEM, GF_ECUDA. */
@@ -185,6 +194,126 @@ gf_status gf_occupation_static(const void *h_dev, const void *p_dev, const void 
                                const void *sigma_inf_dev, int32_t n_k, int32_t nb, int32_t m,
                                int32_t n_iw, double beta, double mu, int32_t tail_order,
                                void *stream, double *n_out, double *dn_dmu_out);
+
+/* ---- Pole form of Sigma: the pseudo-Hamiltonian path (Sec. 3.3) ----------
+ * When Sigma has the pole form of Sec. 3.2.4 (Eq. se_pole),
+ *   Sigma(i w) = Sigma_inf + sum_i V_i^+ V_i / (i w - p_i),  V_i a 1 x m row,
+ * the band block of the resolvent of the pseudo-Hamiltonian (Eq. pseudo_H_k)
+ *   H_ps = [[H_k + P_k^+ Sigma_inf P_k, W^+], [W, diag(p_i + mu)]],  W_i = V_i P_k,
+ * equals G(k, i w_n) of Eq. dmftloop1 at every frequency, and rho_k, N(mu),
+ * n_corr and G_loc follow from its eigenpairs in closed form (Eqs.
+ * rho_LDA+DMFT_componet_final, fix_mu; no Matsubara truncation and no tail).
+ * The pole energies enter shifted by mu because Sigma is a function of i w
+ * (the reading the Matsubara path uses too), so each mu diagonalises H_ps
+ * again: one (N_b + n_poles)-square Hermitian eigenproblem per k, solved by
+ * the library's batched Jacobi kernel (N_b + n_poles <= 256). */
+
+/* Pole form of Sigma per system: n_poles [n_systems] (host), pole energies
+ * p [sum_s n_poles[s]] (real, eV, host or device), pole vectors
+ * V [sum_s n_poles[s] * m_s] (complex of the context's input dtype, row i of
+ * system s holds V_i), Sigma_inf [sum_s m_s^2] (complex, Hermitian).  The
+ * library copies them; the Matsubara-path Sigma of gf_set_sigma is untouched.
+ * Errors: GF_EINVAL (NULL pointers, negative n_poles, a non-finite pole,
+ * N_b + n_poles > 256, m > 32), GF_ENOMEM, GF_ECUDA. */
+gf_status gf_set_sigma_poles(gf_ctx *ctx, const int32_t *n_poles, const double *poles_ptr,
+                             const void *v_ptr, const void *sigma_inf_ptr);
+
+/* N(mu) = sum_k w_k sum_l |Psi_b,l|^2 n_F(E_l - mu) and its exact derivative
+ * dN/dmu per system (host arrays [n_systems]; dn_dmu_out may be NULL), from the
+ * eigenpairs (E_l, Psi_l) of H_ps(mu); Psi_b,l is the band block of Psi_l.
+ * Errors: GF_ESTATE (H, P or the poles missing), GF_ENOTCONV (Jacobi did not
+ * converge in 40 sweeps), GF_EINVAL, GF_ECUDA. */
+gf_status gf_pole_occupation(gf_ctx *ctx, const double *mu, double *n_out, double *dn_dmu_out);
+
+/* mu per system with |N(mu) - n_target[s]| <= tol on the pole-path N(mu), by
+ * the same safeguarded Newton iteration as gf_find_mu.
+ * Errors: as gf_find_mu and gf_pole_occupation. */
+gf_status gf_pole_find_mu(gf_ctx *ctx, const double *n_target, double tol, int32_t max_iter,
+                          double *mu_inout, int32_t *iters_out);
+
+/* rho_k = Psi_b diag(n_F(E - mu)) Psi_b^+ packed per k like gf_density_matrix
+ * (host or device, may be NULL) and n_corr = sum_k w_k Tr(P_k rho_k P_k^+) per
+ * system to host [n_systems] (may be NULL).
+ * Errors: as gf_pole_occupation. */
+gf_status gf_pole_density_matrix(gf_ctx *ctx, const double *mu, void *rho_out_ptr,
+                                 double *n_corr_out);
+
+/* G_loc(i w_n) = sum_k w_k sum_l phi_l phi_l^+ / (i w_n + mu - E_l), phi_l =
+ * P_k Psi_b,l, on the context's n_iw Matsubara frequencies, packed like
+ * gf_local's output (complex128, host or device).
+ * Errors: as gf_pole_occupation. */
+gf_status gf_pole_local(gf_ctx *ctx, const double *mu, void *gloc_out_ptr);
+
+/* Density of states on the real axis from the pseudo-Hamiltonian eigenpairs
+ * (Eqs. DOS and PDOS), broadened by a Lorentzian of half width eta > 0:
+ *   D(e) = -(1/pi) Im sum_k w_k sum_l |Psi_b,l|^2 / (e + mu - E_l + i eta),
+ *   D_alpha(e) = -(1/pi) Im sum_k w_k sum_l |(P_k Psi_b,l)_alpha|^2 / (same).
+ * eps [n_eps] energies relative to mu (host or device); dos_out host or device
+ * [n_systems][n_eps]; pdos_out (may be NULL) host or device, per system
+ * [n_eps][m_s], systems one after the other.
+ * Errors: as gf_pole_occupation, GF_EINVAL (n_eps < 1, eta <= 0). */
+gf_status gf_pole_spectral(gf_ctx *ctx, const double *mu, int32_t n_eps, const double *eps,
+                           double eta, double *dos_out, double *pdos_out);
+
+/* Energy terms of Sec. 3.4 from the pseudo-Hamiltonian eigenpairs, per system
+ * to host [n_systems] (either pointer may be NULL):
+ *   h_ks = sum_k w_k Tr(H_k rho_k)                              (Eq. H_KS)
+ *   e_ps = sum_k w_k sum_l (E_l - mu) |Psi_b,l|^2 n_F(E_l - mu)
+ * so that <H_U> = (e_ps - h_ks + <V_DC>) / 2 (Eq. H_U_energy).
+ * Errors: as gf_pole_occupation. */
+gf_status gf_pole_energy(gf_ctx *ctx, const double *mu, double *h_ks_out, double *e_ps_out);
+
+/* Batched Hermitian eigensolver (cyclic Jacobi, the kernel of the pole path),
+ * stateless: a [n_mat][n][n] complex128 on the device (its Hermitian part
+ * (A + A^+)/2 is used) -> eigenvalues w [n_mat][n] ascending and eigenvectors
+ * v [n_mat][n][n] (column l of each matrix is the vector of w[l]), both device
+ * arrays.  1 <= n <= 256; at most max_sweeps sweeps.  Enqueued on stream
+ * (NULL = legacy default) and synchronised before return; scratch comes from
+ * the stream-ordered allocator.  The paper needs it inside the pseudo-
+ * Hamiltonian method of Sec. 3.3; this entry exposes it on its own.
+ * Errors (message in gf_last_error(NULL)): GF_EINVAL (sizes, host pointers),
+ * GF_ENOTCONV, GF_ENOMEM, GF_ECUDA. */
+gf_status gf_heev_batched(const void *a_dev, int32_t n_mat, int32_t n, int32_t max_sweeps,
+                          double *w_dev, void *v_dev, void *stream);
+
+/* ---- Around the lattice sums: projectors and the DMFT step ----------------- */
+
+/* Orthonormal projectors (Eqs. 6 and 7): from raw projections W_k (packed like
+ * P, m x N_b(k) per k, input dtype, host or device) the library computes
+ * P_k = O_k^{-1/2} W_k with the overlap O_k = W_k W_k^+ (m x m), by one
+ * Hermitian eigenproblem of O_k per k, and makes P_k the context's projectors
+ * (as gf_set_projectors would).  p_out_ptr (may be NULL) receives P_k as
+ * complex128.  m <= 32.
+ * Errors: GF_ESINGULAR (an overlap eigenvalue <= 1e-12 of the largest: the
+ * projections of a k-point are linearly dependent), GF_EINVAL, GF_ECUDA. */
+gf_status gf_set_projectors_lowdin(gf_ctx *ctx, const void *w_ptr, void *p_out_ptr);
+
+/* Impurity levels (Eq. E^imp): E_imp = sum_k w_k P_k H_k P_k^+ - V_DC I per
+ * system, [sys][m][m] complex128 (host or device).  v_dc: host [n_systems]
+ * double-counting potentials V_DC (Eq. V_DC_component), or NULL for 0.
+ * Errors: GF_ESTATE (H or P missing), GF_EINVAL, GF_ECUDA. */
+gf_status gf_impurity_levels(gf_ctx *ctx, const double *v_dc, void *e_imp_out_ptr);
+
+/* Hybridization function of the DMFT self-consistency step (Eq. dmftloop2):
+ *   Delta(i w_n) = (i w_n + mu) I - E_imp - Sigma(i w_n) - G_loc(i w_n)^{-1}
+ * for every system and frequency, from G_loc (complex128, packed like
+ * gf_local's output, host or device; e.g. that output), the context's Sigma
+ * (gf_set_sigma) and E_imp with v_dc as in gf_impurity_levels.  delta_out_ptr:
+ * complex128 packed like Sigma (host or device).  m <= 32.
+ * Errors: GF_ESTATE (Sigma, H or P missing), GF_ESINGULAR (G_loc singular at a
+ * frequency), GF_EINVAL, GF_ECUDA. */
+gf_status gf_hybridization(gf_ctx *ctx, const double *mu, const void *gloc_ptr, const double *v_dc,
+                           void *delta_out_ptr);
+
+/* Double counting of Sec. 3.2.3 (host arithmetic, no context): for interaction
+ * U, Hund's coupling J, orbital quantum number l (M = 2l + 1) and occupation n
+ * of the correlated shell,
+ *   U_bar = (U + 2(M-1)(U-2J) - (M-1)J) / (2M-1)      (Eq. U_eff)
+ *   V_DC  = U_bar (n - 1/2)                           (Eq. V_DC_component)
+ *   E_DC  = U_bar n (n - 1) / 2                        (Eq. E_DC)
+ * Any output pointer may be NULL.  Errors: GF_EINVAL (non-finite input, l < 0). */
+gf_status gf_double_counting(double U, double J, int32_t l, double n, double *u_bar_out,
+                             double *v_dc_out, double *e_dc_out);
 
 /* Message of the last failed call on this context ("" if none).  Owned by the
  * context, valid until the next call on it. */

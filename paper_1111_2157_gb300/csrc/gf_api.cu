@@ -86,6 +86,15 @@ void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
 }  // namespace gf
 
+// Window buckets: one launch per bucket, tiles sized to the bucket's largest window.
+constexpr int kNumBuckets = 6;
+constexpr int kBucketBounds[kNumBuckets] = {8, 16, 40, 64, 96, 1 << 30};
+inline int gf_bucket(int nb) {
+  for (int i = 0; i < kNumBuckets - 1; ++i)
+    if (nb <= kBucketBounds[i]) return i;
+  return kNumBuckets - 1;
+}
+
 struct gf_ctx {
   int n_sys = 0, n_k = 0, n_iw = 0, precision = 0, in_dtype = 0, tail_order = 2, device = 0;
   cudaStream_t stream = nullptr;
@@ -101,6 +110,8 @@ struct gf_ctx {
   size_t gq_budget = 0;
   std::vector<Item> items;              // sorted by (k batch, -nb, k, chunk)
   std::vector<int> batch_k0, batch_item0;  // batch b: k in [batch_k0[b], batch_k0[b+1])
+  int n_items_batched = 0;  // items of the k-batched list; the window-ordered list follows
+  int all_item0 = 0;        // first item of the list used by modes without a k-reduction
   DevBuf H, P, Sig, Sinf, Einf, trHE, kinfo_d, sinfo_d, items_d, offD_d, mu, nbar, gbar, status,
       queue, stage, occ_part, rho_part, rho_out, gq, kN, kdN, kNc, sysout, a_scratch, mubar_part,
       mubar_sys, gacc, sysout2;
@@ -116,7 +127,8 @@ struct gf_ctx {
   double* hp_mubar() { return hpin + 4 * n_sys + 1; }
   double* hp_sys2() { return hpin + 5 * n_sys + 1; }
   std::string err;
-  std::map<int, bool> tuned;  // mixed path: register kernel chosen, per mode
+  std::map<int, int> tuned;  // candidate chosen by the autotuner, per (mode, bucket)
+  int bucket_nbmax[kNumBuckets] = {0, 0, 0, 0, 0, 0};
   // CUDA-graph replay of the N(mu) evaluation (GF_FLAG_GRAPH)
   bool use_graph = false;
   int occ_calls = 0;
@@ -132,6 +144,17 @@ struct gf_ctx {
   // CUDA event pairs around the point-kernel launches of the current call
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
+  // low-rank (eigenbasis) algorithm, GF_FLAG_LOWRANK
+  bool lowrank = false, lr_dirty = true;
+  DevBuf lr_eps, lr_U, lr_Pt, lr_T, lr_ws;
+  // DMFT step and projector construction
+  DevBuf eimp, eimp_part, gl_in, delta, wraw, vdc;
+  // pole form of Sigma (gf_set_sigma_poles) and the pseudo-Hamiltonian path
+  bool have_poles = false;
+  std::vector<gf::PInfo> pinfo;
+  int nps_max = 0;
+  DevBuf poles, Vp, Sinf_p, pinfo_d, eoff_d, phioff_d, eout, phiout, pole_ws, wbout, kHks, kEps,
+      eps_grid, dos, pdos, pdos_off, pole_part;
 };
 
 namespace {
@@ -176,6 +199,7 @@ gf_status sync_and_check(gf_ctx* c) {
   std::memcpy(&flags, c->hp_status(), sizeof(int));
   if (flags & gf::kFlagSingular)
     return fail(c, GF_ESINGULAR, "zero or non-finite pivot in a (k, i w_n) inverse");
+  if (flags & 2) return fail(c, GF_ENOTCONV, "Jacobi eigensolver did not converge in 40 sweeps");
   return GF_OK;
 }
 
@@ -186,6 +210,44 @@ gf_status ensure_einf(gf_ctx* c) {
                         c->trHE.as<double>(), c->stream));
   c->last_launches += 1;
   c->einf_dirty = false;
+  return GF_OK;
+}
+
+// Low-rank path: eigen-decomposition of every H_k and Pt = P_k U, once per
+// Hamiltonian / projector upload.
+gf_status ensure_lr(gf_ctx* c) {
+  if (!c->lowrank || !c->lr_dirty) return GF_OK;
+  if (c->nbmax > gf::heev_max_n())
+    return fail(c, GF_EINVAL, "GF_FLAG_LOWRANK takes N_b <= 256");
+  GF_CU(ensure(c->lr_eps, sizeof(double) * c->totNb));
+  GF_CU(ensure(c->lr_U, sizeof(double2) * c->totH));
+  GF_CU(ensure(c->lr_Pt, sizeof(double2) * c->totP));
+  const size_t smem = gf::heev_smem(c->nbmax);
+  const size_t limit = (size_t)c->smem_optin - 8192;
+  const int in_smem = smem <= limit ? 1 : 0;
+  int grid = std::min(c->n_k, c->sm_count * (in_smem ? std::max(1, (int)(limit / smem)) : 2));
+  grid = std::max(grid, 1);
+  if (!in_smem) GF_CU(ensure(c->lr_ws, sizeof(double2) * gf::heev_ws_elems(c->nbmax) * grid));
+  GF_CU(gf::launch_lr_setup(c->H.as<double2>(), c->P.as<double2>(), c->kinfo_d.as<KInfo>(),
+                            c->sinfo_d.as<SInfo>(), c->offD_d.as<int64_t>(), c->n_k, c->nbmax,
+                            c->lr_eps.as<double>(), c->lr_U.as<double2>(), c->lr_Pt.as<double2>(),
+                            c->lr_ws.as<double2>(), grid, in_smem, c->status.as<int>(), c->stream));
+  c->last_launches += 1;
+  c->lr_dirty = false;
+  return GF_OK;
+}
+
+// rho_k partial sums: the low-rank kernel leaves them in the eigenbasis of H_k;
+// sum the chunks and rotate back, leaving one chunk for k_rho_finalize.
+gf_status rho_partials(gf_ctx* c, int* n_chunks) {
+  *n_chunks = c->n_chunks;
+  if (!c->lowrank) return GF_OK;
+  GF_CU(ensure(c->lr_T, sizeof(double2) * c->totH));
+  GF_CU(gf::launch_lr_rotate(c->kinfo_d.as<KInfo>(), c->n_k, c->lr_U.as<double2>(),
+                             c->rho_part.as<double2>(), c->totH, c->n_chunks, c->lr_T.as<double2>(),
+                             c->stream));
+  c->last_launches += 1;
+  *n_chunks = 1;
   return GF_OK;
 }
 
@@ -207,45 +269,82 @@ gf_status upload_mu(gf_ctx* c, const double* mu) {
   return GF_OK;
 }
 
-// Autotuner of the mixed path: on the first call of a mode, run the first items
-// of the work list with each candidate kernel (the shared-memory one and the
-// register-resident one), time them with CUDA events, and keep the faster for
-// this context.  The sample runs write only scratch that the real run
-// overwrites.  GF_AUTOTUNE=0 skips the timing and takes the register kernel.
-gf_status autotune_df64(gf_ctx* c, int mode, gf::PointParams p, int grid, size_t smem, int rshape,
-                        int rgrid, int rthreads, size_t rsmem, bool* use_r) {
-  auto it = c->tuned.find(mode);
+// Kernel configuration of one launch, i.e. of one bucket of band-window sizes.
+struct LaunchCfg {
+  int kind = 0;        // 0 FP64, 1 FP32-pair shared-memory, 2 FP32-pair register-resident
+  int shape = -1;      // register tile shape (kind 2)
+  int threads = gf::kThreads;
+  size_t smem = 0;
+  int grid = 1;
+  int a_in_smem = 1;
+  int nbmax = 1;
+};
+
+gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_items) {
+  p.nbmax = cfg.nbmax;
+  p.a_in_smem = cfg.a_in_smem;
+  p.nmat = 1;
+  if (!cfg.a_in_smem) {
+    p.a_stride = (int64_t)cfg.nbmax * (cfg.nbmax | 1);
+    GF_CU(ensure(c->a_scratch, (size_t)cfg.grid * p.a_stride * sizeof(double2)));
+    p.a_scratch = c->a_scratch.as<double2>();
+  }
+  p.n_items = n_items;
+  const int grid = std::min(cfg.grid, std::max(1, n_items));
+  if (cfg.kind == 3) {
+    gf::LowRank lr{c->lr_eps.as<double>(), c->offD_d.as<int64_t>(), c->lr_Pt.as<double2>()};
+    GF_CU(gf::launch_point_lr(p, lr, grid, cfg.smem, c->stream));
+    return GF_OK;
+  }
+  if (cfg.kind == 2) GF_CU(gf::launch_point_df64r(cfg.shape, p, grid, cfg.threads, cfg.smem, c->stream));
+  else if (cfg.kind == 1) GF_CU(gf::launch_point_df64(p, grid, cfg.smem, c->stream));
+  else GF_CU(gf::launch_point_fp64(p, grid, cfg.smem, c->stream));
+  return GF_OK;
+}
+
+std::string cfg_name(const LaunchCfg& g) {
+  char buf[96];
+  if (g.kind == 2)
+    std::snprintf(buf, sizeof(buf), "register %dx%d tiles x %d threads", gf::df64r_tile(g.shape, 0),
+                  gf::df64r_tile(g.shape, 1), g.threads);
+  else
+    std::snprintf(buf, sizeof(buf), "%s, matrix in %s, %d CTAs", g.kind ? "FP32-pair" : "FP64",
+                  g.a_in_smem ? "shared memory" : "L2 (global scratch)", g.grid);
+  return buf;
+}
+
+// Autotuner: the first time a (mode, window bucket) runs with more than one
+// candidate configuration, the first items of that bucket are run with each
+// candidate, timed with CUDA events, and the fastest is kept for the context.
+// The sample runs write only scratch that the real run overwrites.
+// GF_AUTOTUNE=0 skips the timing and takes the last candidate.
+gf_status autotune(gf_ctx* c, int key, const std::vector<LaunchCfg>& cands, gf::PointParams p,
+                   const Item* items, int n_items, LaunchCfg* out) {
+  auto it = c->tuned.find(key);
   if (it != c->tuned.end()) {
-    *use_r = it->second;
+    *out = cands[std::min<size_t>(it->second, cands.size() - 1)];
     return GF_OK;
   }
   const char* env = std::getenv("GF_AUTOTUNE");
-  if (env && std::atoi(env) == 0) {
-    c->tuned[mode] = true;
-    *use_r = true;
+  if (cands.size() == 1 || (env && std::atoi(env) == 0)) {
+    c->tuned[key] = (int)cands.size() - 1;
+    *out = cands.back();
     return GF_OK;
   }
-  if (mode & (gf::kGloc | gf::kAdj)) {
-    GF_CU(ensure(c->gq, sizeof(double2) * (size_t)(c->batch_k0[1] - c->batch_k0[0]) * c->n_iw *
-                            c->mmax * c->mmax));
-    p.gq = c->gq.as<double2>();
-    p.kb0 = c->batch_k0[0];
-  }
-  const int n_sample = std::min(c->batch_item0[1] - c->batch_item0[0], 2 * std::max(grid, rgrid));
-  p.items = c->items_d.as<Item>();
-  p.n_items = n_sample;
+  int maxgrid = 1;
+  for (const LaunchCfg& g : cands) maxgrid = std::max(maxgrid, g.grid);
+  const int n_sample = std::min(n_items, 2 * maxgrid);
+  p.items = items;
   cudaEvent_t e0, e1;
   GF_CU(cudaEventCreate(&e0));
   GF_CU(cudaEventCreate(&e1));
-  float ms[2] = {0.f, 0.f};
-  for (int cand = 0; cand < 2; ++cand) {
+  std::vector<float> ms(cands.size(), 0.f);
+  for (size_t cand = 0; cand < cands.size(); ++cand) {
     for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the module
       GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
       GF_CU(cudaEventRecord(e0, c->stream));
-      if (cand == 0)
-        GF_CU(gf::launch_point_df64(p, std::min(grid, n_sample), smem, c->stream));
-      else
-        GF_CU(gf::launch_point_df64r(rshape, p, std::min(rgrid, n_sample), rthreads, rsmem, c->stream));
+      gf_status st = launch_cfg(c, cands[cand], p, n_sample);
+      if (st) return st;
       GF_CU(cudaEventRecord(e1, c->stream));
       GF_CU(cudaEventSynchronize(e1));
       GF_CU(cudaEventElapsedTime(&ms[cand], e0, e1));
@@ -254,16 +353,60 @@ gf_status autotune_df64(gf_ctx* c, int mode, gf::PointParams p, int grid, size_t
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  *use_r = ms[1] < ms[0];
-  c->tuned[mode] = *use_r;
-  char buf[200];
-  std::snprintf(buf, sizeof(buf),
-                "mixed mode %d: %s (sample of %d items: shared-memory %.3f ms, register %dx%d tiles "
-                "x %d threads %.3f ms)",
-                mode, *use_r ? "register-resident kernel" : "shared-memory kernel", n_sample, ms[0],
-                gf::df64r_tile(rshape, 0), gf::df64r_tile(rshape, 1), rthreads, ms[1]);
-  c->tune_log = buf;
+  int best = 0;
+  for (size_t cand = 1; cand < cands.size(); ++cand)
+    if (ms[cand] < ms[best]) best = (int)cand;
+  c->tuned[key] = best;
+  *out = cands[best];
+  std::string line = "mode " + std::to_string(key >> 3) + ", windows <= " +
+                     std::to_string(cands[0].nbmax) + ": " + cfg_name(cands[best]) + " (sample of " +
+                     std::to_string(n_sample) + " items:";
+  for (size_t cand = 0; cand < cands.size(); ++cand) {
+    char buf[48];
+    std::snprintf(buf, sizeof(buf), " %.3f ms", ms[cand]);
+    line += (cand ? "; " : " ") + cfg_name(cands[cand]) + buf;
+  }
+  c->tune_log += line + "); ";
   return GF_OK;
+}
+
+// Candidate launch configurations for the items of one window bucket (largest
+// window nbmax): the point kernel of the context's precision with the matrix in
+// shared memory (when it fits) and in an L2-resident global slice (more CTAs per
+// SM), and in the mixed path the register-resident kernel (windows <= 96).
+gf_status choose_cfg(gf_ctx* c, int mode, int bucket, int nbmax, const gf::PointParams& p,
+                     const Item* items, int n_items, LaunchCfg* cfg) {
+  const size_t limit = (size_t)c->smem_optin - 1024;
+  const int kind = (c->precision == GF_PREC_MIXED) ? 1 : 0;
+  std::vector<LaunchCfg> cands;
+  for (int in_smem = 1; in_smem >= 0; --in_smem) {
+    LaunchCfg a;
+    a.nbmax = nbmax;
+    a.kind = kind;
+    a.a_in_smem = in_smem;
+    a.smem = gf::point_fp64_smem(nbmax, c->mmax, mode, in_smem);  // same layout for both kernels
+    if (a.smem > limit) continue;
+    const int bps = kind ? gf::point_df64_blocks_per_sm(a.smem) : gf::point_fp64_blocks_per_sm(a.smem);
+    a.grid = c->sm_count * std::max(1, bps);
+    // the L2 variant only when it raises occupancy
+    if (!in_smem && !cands.empty() && a.grid <= cands[0].grid) continue;
+    cands.push_back(a);
+  }
+  if (cands.empty())
+    return fail(c, GF_EINVAL, "N_b or m too large for the shared-memory tiles of the point kernel");
+  const int shape = kind ? gf::df64r_shape(nbmax) : -1;
+  if (shape >= 0) {
+    LaunchCfg b;
+    b.kind = 2;
+    b.shape = shape;
+    b.nbmax = nbmax;
+    b.threads = gf::df64r_threads(shape, nbmax);
+    b.smem = gf::point_df64r_smem(nbmax, c->mmax, mode);
+    b.a_in_smem = 1;
+    b.grid = c->sm_count * std::max(1, gf::point_df64r_blocks_per_sm(shape, b.threads, b.smem));
+    if (b.smem <= limit) cands.push_back(b);
+  }
+  return autotune(c, mode * 8 + bucket, cands, p, items, n_items, cfg);
 }
 
 // Algorithmic floating-point operations of one (k, i w_n) point (8 per complex
@@ -279,6 +422,20 @@ double point_flops(int N, int M, int mode) {
   return 8.0 * cmac + f;
 }
 
+// Floating-point operations of one point of the low-rank kernel (8 per complex
+// multiply-add): g0 (and g1, g2) N_b m^2 each, Sigma g0 and the elimination
+// m^3 + m^2 (2m) / 2 ..., the products of the epilogue m^3 each.
+double point_flops_lr(int N, int M, int mode) {
+  const double n = N, m = M;
+  double cmac = m * m * n + m * m * m + m * m * m;  // g0, Sigma g0, [M | Sigma] elimination
+  if (mode & (gf::kOcc | gf::kAdj)) cmac += m * m * n + m * m * m;  // g1, K g1
+  if (mode & gf::kOcc) cmac += m * m * n;                          // g2
+  if (mode & (gf::kGloc | gf::kAdj)) cmac += 2.0 * m * m * m;       // K g0, g0 K g0
+  if (mode & gf::kRho) cmac += m * m * n + m * n * n;               // K Pt, Pt^+ (K Pt)
+  if (mode & gf::kAdj) cmac += 4.0 * m * m * m;                     // B, A^+ Gbar A^+
+  return 8.0 * cmac;
+}
+
 // Run the point kernel over every (k, chunk) item with the given mode.  For
 // kGloc / kAdj the per-(k, n) m x m results are reduced over k into c->gacc,
 // k-batch by k-batch, in increasing k order.
@@ -288,35 +445,9 @@ gf_status run_points(gf_ctx* c, int mode) {
   st = ensure_einf(c);
   if (st) return st;
   GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
-
-  int a_in_smem = 1;
-  size_t smem = gf::point_fp64_smem(c->nbmax, c->mmax, mode, 1);
-  const size_t limit = (size_t)c->smem_optin - 1024;
-  if (smem > limit) {
-    a_in_smem = 0;
-    smem = gf::point_fp64_smem(c->nbmax, c->mmax, mode, 0);
-    if (smem > limit)
-      return fail(c, GF_EINVAL, "N_b or m too large for the shared-memory tiles of the FP64 kernel");
-  }
+  st = ensure_lr(c);
+  if (st) return st;
   const bool df64 = (c->precision == GF_PREC_MIXED);
-  int nmat = 1;
-  int bps = 1;
-  int rshape = -1, rthreads = 0;
-  size_t rsmem = 0;
-  if (df64) {
-    // candidates: the shared-memory FP32-pair kernel and, for windows up to 96
-    // bands, the register-resident one; the autotuner picks between them
-    const int shape = gf::df64r_shape(c->nbmax);
-    if (shape >= 0) {
-      rsmem = gf::point_df64r_smem(c->nbmax, c->mmax, mode);
-      rthreads = gf::df64r_threads(shape, c->nbmax);
-      if (rsmem <= limit) rshape = shape;
-    }
-    bps = std::max(1, gf::point_df64_blocks_per_sm(smem));
-  } else {
-    bps = std::max(1, gf::point_fp64_blocks_per_sm(smem));
-  }
-  const int grid = c->sm_count * bps;
   gf::PointParams p{};
   p.H = c->H.as<double2>();
   p.P = c->P.as<double2>();
@@ -332,15 +463,8 @@ gf_status run_points(gf_ctx* c, int mode) {
   p.queue = c->queue.as<int>();
   p.mu = c->mu.as<double>();
   p.mode = mode;
-  p.nbmax = c->nbmax;
   p.mmax = c->mmax;
-  p.a_in_smem = a_in_smem;
-  p.nmat = nmat;
-  if (!a_in_smem) {
-    p.a_stride = (int64_t)c->nbmax * (c->nbmax | 1);
-    GF_CU(ensure(c->a_scratch, (size_t)grid * nmat * p.a_stride * sizeof(double2)));
-    p.a_scratch = c->a_scratch.as<double2>();
-  }
+  p.nmat = 1;
   if (mode & gf::kOcc) {
     GF_CU(ensure(c->occ_part, sizeof(double) * 2 * (size_t)c->n_k * c->n_chunks));
     p.occ_part = c->occ_part.as<double>();
@@ -365,18 +489,10 @@ gf_status run_points(gf_ctx* c, int mode) {
   }
   const bool kred = (mode & (gf::kGloc | gf::kAdj)) != 0;
   const int nb_batches = kred ? (int)c->batch_k0.size() - 1 : 1;
-  // mixed path: register-resident or shared-memory kernel, chosen once per mode
-  bool use_r = false;
-  int rgrid = 0;
-  if (rshape >= 0) {
-    rgrid = c->sm_count * std::max(1, gf::point_df64r_blocks_per_sm(rshape, rthreads, rsmem));
-    st = autotune_df64(c, mode, p, grid, smem, rshape, rgrid, rthreads, rsmem, &use_r);
-    if (st) return st;
-  }
   int64_t points = 0;
   for (int b = 0; b < nb_batches; ++b) {
-    const int i0 = kred ? c->batch_item0[b] : 0;
-    const int i1 = kred ? c->batch_item0[b + 1] : (int)c->items.size();
+    const int i0 = kred ? c->batch_item0[b] : c->all_item0;
+    const int i1 = kred ? c->batch_item0[b + 1] : c->all_item0 + c->n_items_batched;
     const int kb0 = kred ? c->batch_k0[b] : 0;
     const int kb1 = kred ? c->batch_k0[b + 1] : c->n_k;
     if (kred) {
@@ -384,31 +500,46 @@ gf_status run_points(gf_ctx* c, int mode) {
       p.gq = c->gq.as<double2>();
       p.kb0 = kb0;
     }
-    p.items = c->items_d.as<Item>() + i0;
-    p.n_items = i1 - i0;
-    GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
-    while ((int)c->ev.size() < c->ev_used + 2) {
-      cudaEvent_t e;
-      GF_CU(cudaEventCreate(&e));
-      c->ev.push_back(e);
+    // items are sorted by decreasing window: one launch per window bucket, with
+    // shared-memory tiles sized to the bucket's largest window
+    for (int s0 = i0; s0 < i1;) {
+      const int bucket = gf_bucket(c->nb[c->items[s0].k]);
+      int s1 = s0;
+      while (s1 < i1 && gf_bucket(c->nb[c->items[s1].k]) == bucket) ++s1;
+      const Item* items_dev = c->items_d.as<Item>() + s0;
+      LaunchCfg cfg;
+      if (c->lowrank) {
+        cfg.kind = 3;
+        cfg.nbmax = c->bucket_nbmax[bucket];
+        cfg.smem = gf::point_lr_smem(cfg.nbmax, c->mmax, mode);
+        if (cfg.smem > (size_t)c->smem_optin - 1024)
+          return fail(c, GF_EINVAL, "N_b or m too large for the shared-memory tiles of the low-rank kernel");
+        cfg.grid = c->sm_count * std::max(1, gf::point_lr_blocks_per_sm(cfg.smem));
+      } else {
+        st = choose_cfg(c, mode, bucket, c->bucket_nbmax[bucket], p, items_dev, s1 - s0, &cfg);
+        if (st) return st;
+      }
+      p.items = items_dev;
+      GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
+      while ((int)c->ev.size() < c->ev_used + 2) {
+        cudaEvent_t e;
+        GF_CU(cudaEventCreate(&e));
+        c->ev.push_back(e);
+      }
+      // (events recorded inside a CUDA graph cannot be timed: a replay is timed as a whole)
+      if (!c->capturing) GF_CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
+      st = launch_cfg(c, cfg, p, s1 - s0);
+      if (st) return st;
+      if (!c->capturing) {
+        GF_CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+        c->ev_used += 2;
+      }
+      c->last_launches += 1;
+      s0 = s1;
     }
-    // (events recorded inside a CUDA graph cannot be timed: a replay is timed as a whole)
-    if (!c->capturing) GF_CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
-    if (use_r)
-      GF_CU(gf::launch_point_df64r(rshape, p, std::min(rgrid, std::max(1, i1 - i0)), rthreads, rsmem,
-                                   c->stream));
-    else if (df64)
-      GF_CU(gf::launch_point_df64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
-    else
-      GF_CU(gf::launch_point_fp64(p, std::min(grid, std::max(1, i1 - i0)), smem, c->stream));
-    if (!c->capturing) {
-      GF_CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
-      c->ev_used += 2;
-    }
-    c->last_launches += 1;
     if (kred) {
       int max_total = 0;
-      for (const SInfo& s : c->sinfo) max_total = std::max(max_total, c->n_iw * s.m * s.m);
+      for (const SInfo& si : c->sinfo) max_total = std::max(max_total, c->n_iw * si.m * si.m);
       GF_CU(gf::launch_gq_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys, max_total,
                                  c->gq.as<double2>(), kb0, kb1, c->n_iw, c->mmax, b == 0,
                                  c->gacc.as<double2>(), c->stream));
@@ -417,7 +548,8 @@ gf_status run_points(gf_ctx* c, int mode) {
     for (int i = i0; i < i1; ++i) {
       const Item& it = c->items[i];
       points += it.n1 - it.n0;
-      c->last_flops += (it.n1 - it.n0) * point_flops(c->nb[it.k], c->msys[c->ksys[it.k]], mode);
+      c->last_flops += (it.n1 - it.n0) * (c->lowrank ? point_flops_lr(c->nb[it.k], c->msys[c->ksys[it.k]], mode)
+                                                     : point_flops(c->nb[it.k], c->msys[c->ksys[it.k]], mode));
     }
   }
   c->last_points += points;
@@ -547,6 +679,152 @@ gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn
   return finish_occupation(c, c->cap_stream, n_out, dn_out);
 }
 
+// Safeguarded Newton search of mu with N(mu) = n_target per system (Eq. fix_mu):
+// N is increasing in mu (dN/dmu > 0); a Newton step is capped at 4 eV while
+// the bracket is one-sided and replaced by bisection when it leaves the
+// bracket.  eval(mu, N, dN/dmu) evaluates all systems at once.
+template <class Eval>
+gf_status newton_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_iter,
+                    double* mu_inout, int32_t* iters_out, Eval eval) {
+  if (!n_target || !mu_inout) return fail(c, GF_EINVAL, "n_target or mu_inout is NULL");
+  if (!(tol > 0.0) || max_iter < 1) return fail(c, GF_EINVAL, "tol must be > 0 and max_iter >= 1");
+  const int S = c->n_sys;
+  const double inf = std::numeric_limits<double>::infinity();
+  std::vector<double> mu(mu_inout, mu_inout + S), lo(S, -inf), hi(S, inf), N(S), dN(S);
+  std::vector<double> best_mu(mu), best_f(S, inf);
+  std::vector<char> done(S, 0);
+  int it = 0;
+  for (; it < max_iter;) {
+    gf_status st = eval(mu.data(), N.data(), dN.data());
+    ++it;
+    if (st) return st;
+    bool all = true;
+    for (int s = 0; s < S; ++s) {
+      if (done[s]) continue;
+      const double f = N[s] - n_target[s];
+      if (std::fabs(f) < best_f[s]) { best_f[s] = std::fabs(f); best_mu[s] = mu[s]; }
+      if (std::fabs(f) <= tol) { done[s] = 1; continue; }
+      all = false;
+      if (f < 0) lo[s] = std::max(lo[s], mu[s]);
+      else hi[s] = std::min(hi[s], mu[s]);
+      double step = (dN[s] > 1e-300) ? -f / dN[s] : (f < 0 ? 1.0 : -1.0);
+      const double cap = 4.0;  // eV: no wild jumps while the bracket is one-sided
+      if (!(std::isfinite(lo[s]) && std::isfinite(hi[s]))) step = std::max(-cap, std::min(cap, step));
+      double mn = mu[s] + step;
+      if (std::isfinite(lo[s]) && std::isfinite(hi[s])) {
+        if (!(mn > lo[s] && mn < hi[s])) mn = 0.5 * (lo[s] + hi[s]);
+        if (hi[s] - lo[s] <= 4e-16 * std::max(1.0, std::fabs(mu[s]))) { done[s] = 2; continue; }
+      }
+      mu[s] = mn;
+    }
+    if (all) break;
+  }
+  bool conv = true;
+  for (int s = 0; s < S; ++s) {
+    if (done[s] != 1) conv = false;
+    mu_inout[s] = done[s] == 1 ? mu[s] : best_mu[s];
+  }
+  if (iters_out) *iters_out = it;
+  if (!conv) return fail(c, GF_ENOTCONV, "mu search did not reach tol within max_iter");
+  return GF_OK;
+}
+
+// Pole path: build H_ps(mu) per k, diagonalise, and run the epilogues of mode.
+gf_status pole_run(gf_ctx* c, int mode, bool gloc_kernel = true) {
+  if (!c->have_H || !c->have_P || !c->have_poles)
+    return fail(c, GF_ESTATE, "gf_set_hamiltonian, gf_set_projectors and gf_set_sigma_poles must "
+                              "all be called before a pole-path call");
+  GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
+  gf::PoleParams p{};
+  p.H = c->H.as<double2>();
+  p.P = c->P.as<double2>();
+  p.Sinf = c->Sinf_p.as<double2>();
+  p.poles = c->poles.as<double>();
+  p.Vp = c->Vp.as<double2>();
+  p.kinfo = c->kinfo_d.as<KInfo>();
+  p.sinfo = c->sinfo_d.as<SInfo>();
+  p.pinfo = c->pinfo_d.as<gf::PInfo>();
+  p.mu = c->mu.as<double>();
+  p.n_k = c->n_k;
+  p.n_iw = c->n_iw;
+  p.mode = mode;
+  p.max_sweeps = 40;
+  p.kN = c->kN.as<double>();
+  p.kdN = c->kdN.as<double>();
+  p.kNc = c->kNc.as<double>();
+  if (mode & gf::kRho) {
+    GF_CU(ensure(c->rho_out, sizeof(double2) * c->totH));
+    p.rho = c->rho_out.as<double2>();
+  }
+  p.eout = c->eout.as<double>();
+  p.phiout = c->phiout.as<double2>();
+  p.eoff = c->eoff_d.as<int64_t>();
+  p.phioff = c->phioff_d.as<int64_t>();
+  p.gloc = c->gacc.as<double2>();
+  p.wbout = c->wbout.as<double>();
+  p.kHks = c->kHks.as<double>();
+  p.kEps = c->kEps.as<double>();
+  p.status = c->status.as<int>();
+  const size_t smem = gf::heev_smem(c->nps_max);
+  const size_t limit = (size_t)c->smem_optin - 16384;  // static shared arrays of the kernel
+  p.in_smem = smem <= limit ? 1 : 0;
+  int grid = std::min(c->n_k, c->sm_count * (p.in_smem ? std::max(1, (int)(limit / smem)) : 2));
+  grid = std::max(grid, 1);
+  if (!p.in_smem) {
+    p.ws_stride = (int64_t)gf::heev_ws_elems(c->nps_max);
+    GF_CU(ensure(c->pole_ws, sizeof(double2) * (size_t)grid * p.ws_stride));
+    p.ws = c->pole_ws.as<double2>();
+  }
+  while ((int)c->ev.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    GF_CU(cudaEventCreate(&e));
+    c->ev.push_back(e);
+  }
+  GF_CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
+  GF_CU(gf::launch_pole_eig(p, grid, p.in_smem ? smem : 0, c->stream));
+  c->last_launches += 1;
+  if ((mode & gf::kGloc) && gloc_kernel) {
+    const int ns = gf::pole_gloc_splits(c->n_sys, c->n_iw, c->sm_count);
+    GF_CU(ensure(c->pole_part, sizeof(double2) * (size_t)ns * c->totSig));
+    GF_CU(gf::launch_pole_gloc(p, c->n_sys, c->mmax, ns, c->pole_part.as<double2>(), c->totSig,
+                               c->stream));
+    c->last_launches += 2;
+  }
+  GF_CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+  c->ev_used += 2;
+  c->last_points += (int64_t)c->n_k;
+  return GF_OK;
+}
+
+gf_status pole_check(gf_ctx* c) {
+  gf_status st = sync_and_check(c);
+  if (st) return st;
+  int flags = 0;
+  std::memcpy(&flags, c->hp_status(), sizeof(int));
+  if (flags & 2) return fail(c, GF_ENOTCONV, "Jacobi eigensolver did not converge in 40 sweeps");
+  return GF_OK;
+}
+
+gf_status pole_occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  st = pole_run(c, gf::kOcc);
+  if (st) return st;
+  GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                              c->kN.as<double>(), c->kdN.as<double>(), c->sysout.as<double>(),
+                              c->stream));
+  c->last_launches += 1;
+  GF_CU(cudaMemcpyAsync(c->hp_sys(), c->sysout.p, sizeof(double) * 2 * c->n_sys,
+                        cudaMemcpyDeviceToHost, c->stream));
+  st = pole_check(c);
+  if (st) return st;
+  for (int s = 0; s < c->n_sys; ++s) {
+    if (n_out) n_out[s] = c->hp_sys()[2 * s];
+    if (dn_out) dn_out[s] = c->hp_sys()[2 * s + 1];
+  }
+  return GF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -586,6 +864,15 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   c->device = d->device;
   c->stream = static_cast<cudaStream_t>(d->stream);
   c->use_graph = (d->flags & GF_FLAG_GRAPH) != 0;
+  c->lowrank = (d->flags & GF_FLAG_LOWRANK) != 0;
+  if (c->lowrank && c->precision != GF_PREC_FP64) {
+    delete c;
+    return bad("GF_FLAG_LOWRANK runs in FP64 only");
+  }
+  if (c->lowrank && c->use_graph) {
+    delete c;
+    return bad("GF_FLAG_LOWRANK and GF_FLAG_GRAPH cannot be combined");
+  }
   c->nb.resize(c->n_k);
   c->ksys.resize(c->n_k);
   for (int k = 0; k < c->n_k; ++k) {
@@ -648,6 +935,10 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   c->totH = offH;
   c->totP = offP;
   c->totNb = offD;
+  for (int k = 0; k < c->n_k; ++k) {
+    const int bk = gf_bucket(c->nb[k]);
+    c->bucket_nbmax[bk] = std::max(c->bucket_nbmax[bk], c->nb[k]);
+  }
 
   // device
   int ndev = 0;
@@ -661,25 +952,36 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   DeviceGuard guard(c->device);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
   cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  // k-batches for the k-reductions: gq holds (k1-k0) * n_iw * mmax^2 complex numbers
-  size_t budget = (size_t)8 << 30;
+  // k-batches for the k-reductions: gq holds (k1-k0) * n_iw * mmax^2 complex
+  // numbers, within a quarter of the free device memory and at most 32 GiB
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = (size_t)32 << 30;
+  }
+  size_t budget = std::min<size_t>((size_t)32 << 30, std::max<size_t>(free_b / 4, (size_t)1 << 28));
   if (const char* env = std::getenv("GF_GQ_BUDGET_MB")) budget = (size_t)std::atoll(env) << 20;
   c->gq_budget = budget;
   const size_t per_k = sizeof(double2) * (size_t)c->n_iw * c->mmax * c->mmax;
   const int kpb = (int)std::max<size_t>(1, std::min<size_t>(c->n_k, budget / per_k));
-  // chunk width: about 40 items per resident CTA
-  const size_t smem = gf::point_fp64_smem(c->nbmax, c->mmax, gf::kOcc, 1);
+  // chunk width: about 40 items per resident CTA in each window bucket's launch
+  // (resident CTAs: the larger of the two matrix placements of the point kernel)
   int bps = 1;
-  if (smem <= (size_t)c->smem_optin - 1024)
-    bps = (c->precision == GF_PREC_MIXED) ? gf::point_df64_blocks_per_sm(smem)
-                                          : gf::point_fp64_blocks_per_sm(smem);
-  if (bps < 1) bps = 1;
+  for (int in_smem = 0; in_smem <= 1; ++in_smem) {
+    const size_t smem = gf::point_fp64_smem(c->nbmax, c->mmax, gf::kOcc, in_smem);
+    if (smem <= (size_t)c->smem_optin - 1024)
+      bps = std::max(bps, (c->precision == GF_PREC_MIXED) ? gf::point_df64_blocks_per_sm(smem)
+                                                          : gf::point_fp64_blocks_per_sm(smem));
+  }
+  int n_buckets = 0;
+  for (int b = 0; b < kNumBuckets; ++b) n_buckets += c->bucket_nbmax[b] > 0;
   const double resident = (double)c->sm_count * bps;
-  const double want = (double)c->n_k * c->n_iw / (40.0 * resident);
+  const double want = (double)c->n_k * c->n_iw / (40.0 * resident * std::max(1, n_buckets));
   c->chunk_w = (int)std::min<double>(c->n_iw, std::max(4.0, std::ceil(want)));
   c->n_chunks = (c->n_iw + c->chunk_w - 1) / c->chunk_w;
   c->batch_k0.clear();
   c->batch_item0.clear();
+  auto by_window = [&](const Item& a, const Item& b) { return c->nb[a.k] > c->nb[b.k]; };
   for (int kb = 0; kb < c->n_k; kb += kpb) {
     const int ke = std::min(c->n_k, kb + kpb);
     c->batch_k0.push_back(kb);
@@ -689,12 +991,21 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
       for (int ch = 0; ch < c->n_chunks; ++ch)
         its.push_back(Item{k, ch * c->chunk_w, std::min(c->n_iw, (ch + 1) * c->chunk_w), ch});
     // most expensive first (N_b^3), stable in (k, chunk)
-    std::stable_sort(its.begin(), its.end(),
-                     [&](const Item& a, const Item& b) { return c->nb[a.k] > c->nb[b.k]; });
+    std::stable_sort(its.begin(), its.end(), by_window);
     c->items.insert(c->items.end(), its.begin(), its.end());
   }
   c->batch_k0.push_back(c->n_k);
   c->batch_item0.push_back((int)c->items.size());
+  // modes without a k-reduction take every item in one list ordered by window
+  // (one launch per bucket); with one k-batch that is the list above
+  c->n_items_batched = (int)c->items.size();
+  c->all_item0 = 0;
+  if (c->batch_k0.size() > 2) {
+    std::vector<Item> all(c->items.begin(), c->items.end());
+    std::stable_sort(all.begin(), all.end(), by_window);
+    c->all_item0 = (int)c->items.size();
+    c->items.insert(c->items.end(), all.begin(), all.end());
+  }
 
   auto alloc_all = [&]() -> cudaError_t {
     cudaError_t e;
@@ -762,7 +1073,12 @@ gf_status gf_destroy(gf_ctx* c) {
                     &c->items_d, &c->offD_d, &c->mu, &c->nbar, &c->gbar, &c->status, &c->queue,
                     &c->stage, &c->occ_part, &c->rho_part, &c->rho_out, &c->gq, &c->kN, &c->kdN,
                     &c->kNc, &c->sysout, &c->a_scratch, &c->mubar_part, &c->mubar_sys, &c->gacc,
-                    &c->sysout2, &c->Hd, &c->Pd, &c->Sd, &c->Gbd};
+                    &c->sysout2, &c->Hd, &c->Pd, &c->Sd, &c->Gbd, &c->poles, &c->Vp,
+                    &c->Sinf_p, &c->pinfo_d, &c->eoff_d, &c->phioff_d, &c->eout, &c->phiout,
+                    &c->pole_ws, &c->lr_eps, &c->lr_U, &c->lr_Pt, &c->lr_T, &c->lr_ws,
+                    &c->eimp, &c->eimp_part, &c->gl_in, &c->delta, &c->wraw, &c->vdc,
+                    &c->wbout, &c->kHks, &c->kEps, &c->eps_grid, &c->dos, &c->pdos, &c->pdos_off,
+                    &c->pole_part};
   for (DevBuf* b : bufs) release(*b);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->occ_exec) cudaGraphExecDestroy(c->occ_exec);
@@ -802,6 +1118,7 @@ gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) {
     GF_CU(cudaStreamSynchronize(c->stream));
   }
   c->have_H = true;
+  c->lr_dirty = true;
   c->einf_dirty = true;
   return GF_OK;
 }
@@ -816,6 +1133,7 @@ gf_status gf_set_projectors(gf_ctx* c, const void* p) {
     GF_CU(gf::launch_split_df64(c->P.as<double2>(), c->Pd.as<float4>(), c->totP, c->stream));
   GF_CU(cudaStreamSynchronize(c->stream));
   c->have_P = true;
+  c->lr_dirty = true;
   c->einf_dirty = true;
   return GF_OK;
 }
@@ -847,50 +1165,12 @@ gf_status gf_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_o
 gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_iter,
                      double* mu_inout, int32_t* iters_out) {
   if (!c) return GF_EINVAL;
-  if (!n_target || !mu_inout) return fail(c, GF_EINVAL, "n_target or mu_inout is NULL");
-  if (!(tol > 0.0) || max_iter < 1) return fail(c, GF_EINVAL, "tol must be > 0 and max_iter >= 1");
   DeviceGuard guard(c->device);
   reset_stats(c);
-  const int S = c->n_sys;
-  const double inf = std::numeric_limits<double>::infinity();
-  std::vector<double> mu(mu_inout, mu_inout + S), lo(S, -inf), hi(S, inf), N(S), dN(S);
-  std::vector<double> best_mu(mu), best_f(S, inf);
-  std::vector<char> done(S, 0);
-  int it = 0;
-  for (; it < max_iter;) {
-    gf_status st = occupation_impl(c, mu.data(), N.data(), dN.data());  // stats accumulate
-    ++it;
-    if (st) return st;
-    bool all = true;
-    for (int s = 0; s < S; ++s) {
-      if (done[s]) continue;
-      const double f = N[s] - n_target[s];
-      if (std::fabs(f) < best_f[s]) { best_f[s] = std::fabs(f); best_mu[s] = mu[s]; }
-      if (std::fabs(f) <= tol) { done[s] = 1; continue; }
-      all = false;
-      if (f < 0) lo[s] = std::max(lo[s], mu[s]);
-      else hi[s] = std::min(hi[s], mu[s]);
-      // safeguarded Newton: N is increasing in mu, dN/dmu > 0
-      double step = (dN[s] > 1e-300) ? -f / dN[s] : (f < 0 ? 1.0 : -1.0);
-      const double cap = 4.0;  // eV: no wild jumps while the bracket is one-sided
-      if (!(std::isfinite(lo[s]) && std::isfinite(hi[s]))) step = std::max(-cap, std::min(cap, step));
-      double mn = mu[s] + step;
-      if (std::isfinite(lo[s]) && std::isfinite(hi[s])) {
-        if (!(mn > lo[s] && mn < hi[s])) mn = 0.5 * (lo[s] + hi[s]);
-        if (hi[s] - lo[s] <= 4e-16 * std::max(1.0, std::fabs(mu[s]))) { done[s] = 2; continue; }
-      }
-      mu[s] = mn;
-    }
-    if (all) break;
-  }
-  bool conv = true;
-  for (int s = 0; s < S; ++s) {
-    if (done[s] != 1) conv = false;
-    mu_inout[s] = done[s] == 1 ? mu[s] : best_mu[s];
-  }
-  if (iters_out) *iters_out = it;
-  if (!conv) return fail(c, GF_ENOTCONV, "mu search did not reach tol within max_iter");
-  return GF_OK;
+  return newton_mu(c, n_target, tol, max_iter, mu_inout, iters_out,
+                   [c](const double* mu, double* n, double* dn) {
+                     return occupation_impl(c, mu, n, dn);  // stats accumulate
+                   });
 }
 
 gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) {
@@ -901,10 +1181,13 @@ gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* 
   if (st) return st;
   st = run_points(c, gf::kRho);
   if (st) return st;
+  int nch = 0;
+  st = rho_partials(c, &nch);
+  if (st) return st;
   GF_CU(ensure(c->rho_out, sizeof(double2) * c->totH));
   GF_CU(gf::launch_rho_finalize(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->H.as<double2>(),
                                 c->Einf.as<double2>(), c->P.as<double2>(), c->mu.as<double>(),
-                                c->rho_part.as<double2>(), c->totH, c->n_chunks, c->n_k,
+                                c->rho_part.as<double2>(), c->totH, nch, c->n_k,
                                 c->rho_out.as<double2>(), c->kN.as<double>(), c->kNc.as<double>(),
                                 c->stream));
   GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
@@ -962,10 +1245,13 @@ gf_status gf_evaluate(gf_ctx* c, const double* mu, void* gloc_out, void* rho_out
                           cudaMemcpyDeviceToHost, c->stream));
   }
   if (mode & gf::kRho) {
+    int nch = 0;
+    st = rho_partials(c, &nch);
+    if (st) return st;
     GF_CU(ensure(c->rho_out, sizeof(double2) * c->totH));
     GF_CU(gf::launch_rho_finalize(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->H.as<double2>(),
                                   c->Einf.as<double2>(), c->P.as<double2>(), c->mu.as<double>(),
-                                  c->rho_part.as<double2>(), c->totH, c->n_chunks, c->n_k,
+                                  c->rho_part.as<double2>(), c->totH, nch, c->n_k,
                                   c->rho_out.as<double2>(), c->kN.as<double>(), c->kNc.as<double>(),
                                   c->stream));
     GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
@@ -1053,6 +1339,351 @@ gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const doubl
 const char* gf_tuning_log(const gf_ctx* c) {
   if (!c) return "";
   return c->tune_log.c_str();
+}
+
+gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* poles,
+                             const void* v, const void* sinf) {
+  if (!c) return GF_EINVAL;
+  if (!n_poles || !sinf) return fail(c, GF_EINVAL, "n_poles or sigma_inf_ptr is NULL");
+  DeviceGuard guard(c->device);
+  std::vector<gf::PInfo> pinfo(c->n_sys);
+  int64_t offp = 0, offV = 0;
+  for (int s = 0; s < c->n_sys; ++s) {
+    if (n_poles[s] < 0) return fail(c, GF_EINVAL, "n_poles must be >= 0");
+    if (c->sinfo[s].m > 32) return fail(c, GF_EINVAL, "the pole path takes m <= 32 orbitals");
+    pinfo[s].np = n_poles[s];
+    pinfo[s].pad = 0;
+    pinfo[s].offp = offp;
+    pinfo[s].offV = offV;
+    offp += n_poles[s];
+    offV += (int64_t)n_poles[s] * c->sinfo[s].m;
+  }
+  if (offp > 0 && (!poles || !v)) return fail(c, GF_EINVAL, "poles_ptr or v_ptr is NULL");
+  std::vector<int64_t> eoff(c->n_k), phioff(c->n_k);
+  int64_t te = 0, tphi = 0;
+  int nps = 1;
+  for (int k = 0; k < c->n_k; ++k) {
+    const int s = c->ksys[k];
+    const int n = c->nb[k] + pinfo[s].np;
+    if (n > gf::heev_max_n())
+      return fail(c, GF_EINVAL, "N_b + n_poles exceeds 256, the eigensolver's largest matrix");
+    nps = std::max(nps, n);
+    eoff[k] = te;
+    phioff[k] = tphi;
+    te += n;
+    tphi += (int64_t)c->sinfo[s].m * n;
+  }
+  std::vector<double> hp(std::max<int64_t>(offp, 1));
+  if (offp > 0) {
+    GF_CU(cudaMemcpy(hp.data(), poles, sizeof(double) * offp, cudaMemcpyDefault));
+    for (int64_t i = 0; i < offp; ++i)
+      if (!std::isfinite(hp[i])) return fail(c, GF_EINVAL, "a pole energy is not finite");
+  }
+  GF_CU(ensure(c->poles, sizeof(double) * std::max<int64_t>(offp, 1)));
+  GF_CU(ensure(c->Vp, sizeof(double2) * std::max<int64_t>(offV, 1)));
+  GF_CU(ensure(c->Sinf_p, sizeof(double2) * c->totSinf));
+  GF_CU(ensure(c->pinfo_d, sizeof(gf::PInfo) * c->n_sys));
+  GF_CU(ensure(c->eoff_d, sizeof(int64_t) * c->n_k));
+  GF_CU(ensure(c->phioff_d, sizeof(int64_t) * c->n_k));
+  GF_CU(ensure(c->eout, sizeof(double) * te));
+  GF_CU(ensure(c->wbout, sizeof(double) * te));
+  GF_CU(ensure(c->kHks, sizeof(double) * c->n_k));
+  GF_CU(ensure(c->kEps, sizeof(double) * c->n_k));
+  GF_CU(ensure(c->phiout, sizeof(double2) * tphi));
+  GF_CU(ensure(c->kN, sizeof(double) * c->n_k));
+  GF_CU(ensure(c->kdN, sizeof(double) * c->n_k));
+  GF_CU(ensure(c->kNc, sizeof(double) * c->n_k));
+  GF_CU(ensure(c->gacc, sizeof(double2) * c->totSig));
+  if (offp > 0) {
+    GF_CU(cudaMemcpyAsync(c->poles.p, hp.data(), sizeof(double) * offp, cudaMemcpyHostToDevice,
+                          c->stream));
+    gf_status st = load_complex(c, v, offV, c->Vp.as<double2>());
+    if (st) return st;
+  }
+  gf_status st = load_complex(c, sinf, c->totSinf, c->Sinf_p.as<double2>());
+  if (st) return st;
+  GF_CU(cudaMemcpyAsync(c->pinfo_d.p, pinfo.data(), sizeof(gf::PInfo) * c->n_sys,
+                        cudaMemcpyHostToDevice, c->stream));
+  GF_CU(cudaMemcpyAsync(c->eoff_d.p, eoff.data(), sizeof(int64_t) * c->n_k, cudaMemcpyHostToDevice,
+                        c->stream));
+  GF_CU(cudaMemcpyAsync(c->phioff_d.p, phioff.data(), sizeof(int64_t) * c->n_k,
+                        cudaMemcpyHostToDevice, c->stream));
+  GF_CU(cudaStreamSynchronize(c->stream));
+  c->pinfo = pinfo;
+  c->nps_max = nps;
+  c->have_poles = true;
+  return GF_OK;
+}
+
+gf_status gf_pole_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+  if (!c) return GF_EINVAL;
+  if (!n_out) return fail(c, GF_EINVAL, "n_out is NULL");
+  DeviceGuard guard(c->device);
+  reset_stats(c);
+  return pole_occupation_impl(c, mu, n_out, dn_out);
+}
+
+gf_status gf_pole_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_iter,
+                          double* mu_inout, int32_t* iters_out) {
+  if (!c) return GF_EINVAL;
+  DeviceGuard guard(c->device);
+  reset_stats(c);
+  return newton_mu(c, n_target, tol, max_iter, mu_inout, iters_out,
+                   [c](const double* mu, double* n, double* dn) {
+                     return pole_occupation_impl(c, mu, n, dn);
+                   });
+}
+
+gf_status gf_pole_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) {
+  if (!c) return GF_EINVAL;
+  DeviceGuard guard(c->device);
+  reset_stats(c);
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  st = pole_run(c, gf::kRho);
+  if (st) return st;
+  GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                              c->kNc.as<double>(), nullptr, c->sysout.as<double>(), c->stream));
+  c->last_launches += 1;
+  if (rho_out)
+    GF_CU(cudaMemcpyAsync(rho_out, c->rho_out.p, sizeof(double2) * c->totH, cudaMemcpyDefault,
+                          c->stream));
+  GF_CU(cudaMemcpyAsync(c->hp_sys(), c->sysout.p, sizeof(double) * 2 * c->n_sys,
+                        cudaMemcpyDeviceToHost, c->stream));
+  st = pole_check(c);
+  if (st) return st;
+  if (n_corr_out)
+    for (int s = 0; s < c->n_sys; ++s) n_corr_out[s] = c->hp_sys()[2 * s];
+  return GF_OK;
+}
+
+gf_status gf_pole_local(gf_ctx* c, const double* mu, void* gloc_out) {
+  if (!c) return GF_EINVAL;
+  if (!gloc_out) return fail(c, GF_EINVAL, "gloc_out_ptr is NULL");
+  DeviceGuard guard(c->device);
+  reset_stats(c);
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  st = pole_run(c, gf::kGloc);
+  if (st) return st;
+  GF_CU(cudaMemcpyAsync(gloc_out, c->gacc.p, sizeof(double2) * c->totSig, cudaMemcpyDefault,
+                        c->stream));
+  return pole_check(c);
+}
+
+gf_status gf_set_projectors_lowdin(gf_ctx* c, const void* w, void* p_out) {
+  if (!c) return GF_EINVAL;
+  if (!w) return fail(c, GF_EINVAL, "w_ptr is NULL");
+  if (c->mmax > 32) return fail(c, GF_EINVAL, "the projector orthonormalisation takes m <= 32");
+  DeviceGuard guard(c->device);
+  GF_CU(ensure(c->wraw, sizeof(double2) * c->totP));
+  gf_status st = load_complex(c, w, c->totP, c->wraw.as<double2>());
+  if (st) return st;
+  GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
+  GF_CU(gf::launch_lowdin(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_k, c->mmax,
+                          c->wraw.as<double2>(), c->P.as<double2>(), c->status.as<int>(), c->stream));
+  if (c->precision == GF_PREC_MIXED)
+    GF_CU(gf::launch_split_df64(c->P.as<double2>(), c->Pd.as<float4>(), c->totP, c->stream));
+  if (p_out)
+    GF_CU(cudaMemcpyAsync(p_out, c->P.p, sizeof(double2) * c->totP, cudaMemcpyDefault, c->stream));
+  st = sync_and_check(c);
+  if (st == GF_ESINGULAR)
+    return fail(c, GF_ESINGULAR, "the projections of a k-point are linearly dependent (overlap "
+                                 "eigenvalue <= 1e-12 of the largest)");
+  if (st) return st;
+  c->have_P = true;
+  c->lr_dirty = true;
+  c->einf_dirty = true;
+  return GF_OK;
+}
+
+gf_status gf_impurity_levels(gf_ctx* c, const double* v_dc, void* e_imp_out) {
+  if (!c) return GF_EINVAL;
+  if (!e_imp_out) return fail(c, GF_EINVAL, "e_imp_out_ptr is NULL");
+  if (!c->have_H || !c->have_P)
+    return fail(c, GF_ESTATE, "gf_set_hamiltonian and gf_set_projectors must be called first");
+  DeviceGuard guard(c->device);
+  GF_CU(ensure(c->eimp, sizeof(double2) * c->totSinf));
+  GF_CU(ensure(c->eimp_part, sizeof(double2) * (size_t)c->n_k * c->mmax * c->mmax));
+  GF_CU(ensure(c->vdc, sizeof(double) * c->n_sys));
+  if (v_dc) {
+    for (int s = 0; s < c->n_sys; ++s) {
+      if (!std::isfinite(v_dc[s])) return fail(c, GF_EINVAL, "v_dc is not finite");
+      c->hp_nbar()[s] = v_dc[s];
+    }
+    GF_CU(cudaMemcpyAsync(c->vdc.p, c->hp_nbar(), sizeof(double) * c->n_sys, cudaMemcpyHostToDevice,
+                          c->stream));
+  }
+  GF_CU(gf::launch_eimp(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_k, c->n_sys,
+                        c->H.as<double2>(), c->P.as<double2>(), c->nbmax, c->mmax,
+                        c->eimp_part.as<double2>(), v_dc ? c->vdc.as<double>() : nullptr,
+                        c->eimp.as<double2>(), c->stream));
+  if (e_imp_out != c->eimp.p)
+    GF_CU(cudaMemcpyAsync(e_imp_out, c->eimp.p, sizeof(double2) * c->totSinf, cudaMemcpyDefault,
+                          c->stream));
+  return sync_and_check(c);
+}
+
+gf_status gf_hybridization(gf_ctx* c, const double* mu, const void* gloc, const double* v_dc,
+                           void* delta_out) {
+  if (!c) return GF_EINVAL;
+  if (!gloc || !delta_out) return fail(c, GF_EINVAL, "gloc_ptr or delta_out_ptr is NULL");
+  if (c->mmax > 32) return fail(c, GF_EINVAL, "the hybridization step takes m <= 32");
+  if (!c->have_S) return fail(c, GF_ESTATE, "gf_set_sigma must be called first");
+  DeviceGuard guard(c->device);
+  GF_CU(ensure(c->eimp, sizeof(double2) * c->totSinf));
+  gf_status st = gf_impurity_levels(c, v_dc, c->eimp.p);
+  if (st) return st;
+  st = upload_mu(c, mu);
+  if (st) return st;
+  GF_CU(ensure(c->gl_in, sizeof(double2) * c->totSig));
+  GF_CU(ensure(c->delta, sizeof(double2) * c->totSig));
+  GF_CU(cudaMemcpyAsync(c->gl_in.p, gloc, sizeof(double2) * c->totSig, cudaMemcpyDefault, c->stream));
+  GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
+  GF_CU(gf::launch_hybridization(c->sinfo_d.as<SInfo>(), c->n_sys, c->n_iw, c->mmax,
+                                 c->mu.as<double>(), c->eimp.as<double2>(), c->Sig.as<double2>(),
+                                 c->gl_in.as<double2>(), c->delta.as<double2>(), c->status.as<int>(),
+                                 c->stream));
+  GF_CU(cudaMemcpyAsync(delta_out, c->delta.p, sizeof(double2) * c->totSig, cudaMemcpyDefault,
+                        c->stream));
+  st = sync_and_check(c);
+  if (st == GF_ESINGULAR) return fail(c, GF_ESINGULAR, "G_loc(i w_n) is singular at some frequency");
+  return st;
+}
+
+gf_status gf_double_counting(double U, double J, int32_t l, double n, double* u_bar, double* v_dc,
+                             double* e_dc) {
+  if (!(std::isfinite(U) && std::isfinite(J) && std::isfinite(n)) || l < 0) {
+    gf::set_global_error("gf_double_counting: U, J, n must be finite and l >= 0");
+    return GF_EINVAL;
+  }
+  const double M = 2.0 * l + 1.0;
+  const double ub = (U + 2.0 * (M - 1.0) * (U - 2.0 * J) - (M - 1.0) * J) / (2.0 * M - 1.0);
+  if (u_bar) *u_bar = ub;
+  if (v_dc) *v_dc = ub * (n - 0.5);
+  if (e_dc) *e_dc = 0.5 * ub * n * (n - 1.0);
+  return GF_OK;
+}
+
+gf_status gf_pole_spectral(gf_ctx* c, const double* mu, int32_t n_eps, const double* eps,
+                           double eta, double* dos_out, double* pdos_out) {
+  if (!c) return GF_EINVAL;
+  if (n_eps < 1 || !eps || !dos_out) return fail(c, GF_EINVAL, "n_eps >= 1, eps and dos_out required");
+  if (!(eta > 0.0) || !std::isfinite(eta)) return fail(c, GF_EINVAL, "eta must be > 0");
+  DeviceGuard guard(c->device);
+  reset_stats(c);
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  st = pole_run(c, gf::kGloc, false);
+  if (st) return st;
+  int64_t tot_m = 0;
+  std::vector<int64_t> off(c->n_sys);
+  for (int s2 = 0; s2 < c->n_sys; ++s2) {
+    off[s2] = tot_m * n_eps;
+    tot_m += c->sinfo[s2].m;
+  }
+  GF_CU(ensure(c->eps_grid, sizeof(double) * n_eps));
+  GF_CU(ensure(c->dos, sizeof(double) * (size_t)n_eps * c->n_sys));
+  GF_CU(ensure(c->pdos, sizeof(double) * (size_t)n_eps * tot_m));
+  GF_CU(ensure(c->pdos_off, sizeof(int64_t) * c->n_sys));
+  GF_CU(cudaMemcpyAsync(c->eps_grid.p, eps, sizeof(double) * n_eps, cudaMemcpyDefault, c->stream));
+  GF_CU(cudaMemcpyAsync(c->pdos_off.p, off.data(), sizeof(int64_t) * c->n_sys, cudaMemcpyHostToDevice,
+                        c->stream));
+  gf::PoleParams p{};
+  p.kinfo = c->kinfo_d.as<KInfo>();
+  p.sinfo = c->sinfo_d.as<SInfo>();
+  p.pinfo = c->pinfo_d.as<gf::PInfo>();
+  p.mu = c->mu.as<double>();
+  p.eout = c->eout.as<double>();
+  p.wbout = c->wbout.as<double>();
+  p.phiout = c->phiout.as<double2>();
+  p.eoff = c->eoff_d.as<int64_t>();
+  p.phioff = c->phioff_d.as<int64_t>();
+  GF_CU(gf::launch_pole_dos(p, c->n_sys, c->eps_grid.as<double>(), n_eps, eta,
+                            c->pdos_off.as<int64_t>(), c->dos.as<double>(),
+                            pdos_out ? c->pdos.as<double>() : nullptr, c->stream));
+  c->last_launches += 1;
+  GF_CU(cudaMemcpyAsync(dos_out, c->dos.p, sizeof(double) * (size_t)n_eps * c->n_sys,
+                        cudaMemcpyDefault, c->stream));
+  if (pdos_out)
+    GF_CU(cudaMemcpyAsync(pdos_out, c->pdos.p, sizeof(double) * (size_t)n_eps * tot_m,
+                          cudaMemcpyDefault, c->stream));
+  return pole_check(c);
+}
+
+gf_status gf_pole_energy(gf_ctx* c, const double* mu, double* h_ks_out, double* e_ps_out) {
+  if (!c) return GF_EINVAL;
+  if (!h_ks_out && !e_ps_out) return fail(c, GF_EINVAL, "h_ks_out and e_ps_out are both NULL");
+  DeviceGuard guard(c->device);
+  reset_stats(c);
+  gf_status st = upload_mu(c, mu);
+  if (st) return st;
+  GF_CU(ensure(c->rho_out, sizeof(double2) * c->totH));
+  st = pole_run(c, gf::kRho);
+  if (st) return st;
+  GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
+                              c->kHks.as<double>(), c->kEps.as<double>(), c->sysout.as<double>(),
+                              c->stream));
+  c->last_launches += 1;
+  GF_CU(cudaMemcpyAsync(c->hp_sys(), c->sysout.p, sizeof(double) * 2 * c->n_sys,
+                        cudaMemcpyDeviceToHost, c->stream));
+  st = pole_check(c);
+  if (st) return st;
+  for (int s2 = 0; s2 < c->n_sys; ++s2) {
+    if (h_ks_out) h_ks_out[s2] = c->hp_sys()[2 * s2];
+    if (e_ps_out) e_ps_out[s2] = c->hp_sys()[2 * s2 + 1];
+  }
+  return GF_OK;
+}
+
+gf_status gf_heev_batched(const void* a_dev, int32_t n_mat, int32_t n, int32_t max_sweeps,
+                          double* w_dev, void* v_dev, void* stream) {
+  if (n_mat < 0 || n < 1 || n > gf::heev_max_n() || max_sweeps < 1 ||
+      (n_mat > 0 && (!a_dev || !w_dev || !v_dev))) {
+    gf::set_global_error("gf_heev_batched: invalid arguments (1 <= n <= 256, max_sweeps >= 1, "
+                         "non-null device pointers)");
+    return GF_EINVAL;
+  }
+  if (n_mat == 0) return GF_OK;
+  const void* ptrs[3] = {a_dev, w_dev, v_dev};
+  for (const void* q : ptrs) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      gf::set_global_error("gf_heev_batched: a, w and v must be device pointers");
+      return GF_EINVAL;
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 1, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t smem = gf::heev_smem(n);
+  const int in_smem = smem + 8192 <= (size_t)optin ? 1 : 0;
+  const int grid = std::max(1, std::min(n_mat, sms * (in_smem ? std::max(1, (int)((optin - 8192) / smem)) : 2)));
+  void* mem = nullptr;
+  const size_t ws = in_smem ? 0 : sizeof(double2) * gf::heev_ws_elems(n) * grid;
+  cudaError_t e = cudaMallocAsync(&mem, 16 + ws, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mem, 0, sizeof(int), s);
+  int* status = static_cast<int*>(mem);
+  double2* gws = reinterpret_cast<double2*>(static_cast<char*>(mem) + 16);
+  if (e == cudaSuccess)
+    e = gf::launch_heev_batched(static_cast<const double2*>(a_dev), n_mat, n, max_sweeps, w_dev,
+                                static_cast<double2*>(v_dev), gws, grid, in_smem, status, s);
+  int flags = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (mem) cudaFreeAsync(mem, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    gf::set_global_error((std::string("gf_heev_batched: ") + cudaGetErrorString(e)).c_str());
+    return e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA;
+  }
+  if (flags & 2) {
+    gf::set_global_error("gf_heev_batched: Jacobi did not converge within max_sweeps");
+    return GF_ENOTCONV;
+  }
+  return GF_OK;
 }
 
 const char* gf_last_error(const gf_ctx* c) {

@@ -77,6 +77,116 @@ struct PointParams {
   int* status;
 };
 
+struct PInfo {          // pole form of one system's Sigma
+  int np;               // number of poles
+  int pad;
+  int64_t offp;         // offset of its poles in the pole-energy array
+  int64_t offV;         // offset of its [np][m] pole vectors (complex elements)
+};
+
+struct PoleParams {
+  const double2* H;
+  const double2* P;
+  const double2* Sinf;  // [sys][m][m], offsets SInfo::offSinf
+  const double* poles;
+  const double2* Vp;
+  const KInfo* kinfo;
+  const SInfo* sinfo;
+  const PInfo* pinfo;
+  const double* mu;     // [n_sys]
+  int n_k, n_iw, mode, max_sweeps;
+  int in_smem;          // 1: H_ps and its eigenvectors in shared memory
+  double2* ws;          // else per-CTA slices of ws_stride elements
+  int64_t ws_stride;
+  double* kN;           // [n_k] N_k
+  double* kdN;          // [n_k] dN_k/dmu
+  double* kNc;          // [n_k] n_corr,k
+  double2* rho;         // packed like H
+  double* eout;         // eigenvalues per k at eoff[k]
+  double2* phiout;      // P Psi_b per k, [m][N_b + np] at phioff[k]
+  const int64_t* eoff;
+  const int64_t* phioff;
+  double2* gloc;        // [sys][n_iw][m][m] at SInfo::offSig
+  double* wbout;        // band weights |Psi_b,l|^2 per k at eoff[k] (kGloc), or null
+  double* kHks;         // [n_k] Re Tr(H_k rho_k) (kRho), or null
+  double* kEps;         // [n_k] sum_l (E_l - mu) |Psi_b,l|^2 n_F (kRho), or null
+  int* status;
+};
+
+__host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
+
+// Eigenbasis data of the low-rank path: H_k = U diag(eps) U^+, Pt = P_k U.
+struct LowRank {
+  const double* eps;     // [sum_k N_b] at offD[k]
+  const int64_t* offD;
+  const double2* Pt;     // [m][N_b] per k at KInfo::offP
+};
+
+// Shared-memory layout of k_point_lr (16-byte complex elements).
+struct LRLayout {
+  int offPt, offD, offS, offG, offAug, offC, offC2, offX, offCol, offU;
+  size_t bytes;
+};
+
+__host__ __device__ inline LRLayout make_lr_layout(int nbmax, int mmax, int mode) {
+  LRLayout L;
+  const int mm = mmax * mmax;
+  int o = 0;
+  L.offPt = o; o += mmax * nbmax;
+  L.offD = o; o += 3 * nbmax;
+  L.offS = o; o += mm;
+  L.offG = o; o += 3 * mm;
+  L.offAug = o; o += 2 * mm;
+  L.offC = o; o += mm;
+  L.offC2 = o; o += mm;
+  L.offX = o; o += imax((mode & kRho) ? mmax * nbmax : 0, (mode & kAdj) ? 4 * mm : 0);
+  L.offCol = o; o += 2 * mmax;
+  L.offU = o; o += 2 * mmax;
+  L.bytes = (size_t)o * 16;
+  return L;
+}
+
+size_t point_lr_smem(int nbmax, int mmax, int mode);
+int point_lr_blocks_per_sm(size_t smem);
+cudaError_t launch_point_lr(const PointParams& p, const LowRank& lr, int grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_lr_rotate(const KInfo* kinfo, int n_k, const double2* U, double2* rho_part,
+                             int64_t stride, int n_chunks, double2* T, cudaStream_t s);
+// Eigen-decomposition of every H_k (Jacobi): eps [offD], U [offH], Pt = P U [offP].
+cudaError_t launch_lr_setup(const double2* H, const double2* P, const KInfo* kinfo,
+                            const SInfo* sinfo, const int64_t* offD, int n_k, int nbmax,
+                            double* eps, double2* U, double2* Pt, double2* ws, int grid,
+                            int in_smem, int* status, cudaStream_t s);
+
+// DMFT self-consistency step: E_imp = sum_k w_k P H P^+ - V_DC (part: [n_k][mmax^2]
+// scratch; out: [sys][m][m] at SInfo::offSinf) and Delta(i w_n) (packed like Sigma).
+cudaError_t launch_eimp(const KInfo* kinfo, const SInfo* sinfo, int n_k, int n_sys, const double2* H,
+                        const double2* P, int nbmax, int mmax, double2* part, const double* v_dc,
+                        double2* out, cudaStream_t s);
+cudaError_t launch_hybridization(const SInfo* sinfo, int n_sys, int n_iw, int mmax, const double* mu,
+                                 const double2* eimp, const double2* Sig, const double2* gloc,
+                                 double2* delta, int* status, cudaStream_t s);
+// Lowdin-orthonormal projectors P_k = (W_k W_k^+)^{-1/2} W_k (packed like P).
+cudaError_t launch_lowdin(const KInfo* kinfo, const SInfo* sinfo, int n_k, int mmax,
+                          const double2* Wraw, double2* Pout, int* status, cudaStream_t s);
+
+// Batched Hermitian eigensolver (cyclic Jacobi) and the pole path.
+size_t heev_smem(int n);
+size_t heev_ws_elems(int n);
+int heev_max_n();
+cudaError_t launch_heev_batched(const double2* A, int n_mat, int n, int max_sweeps, double* w,
+                                double2* V, double2* gws, int grid, int in_smem, int* status,
+                                cudaStream_t s);
+cudaError_t launch_pole_eig(const PoleParams& p, int grid, size_t smem, cudaStream_t s);
+// G_loc from the eigenpairs, k split n_split ways into part [n_split][tot] and
+// summed in split order into p.gloc.
+int pole_gloc_splits(int n_sys, int n_iw, int sm_count);
+cudaError_t launch_pole_gloc(const PoleParams& p, int n_sys, int mmax, int n_split, double2* part,
+                             int64_t tot, cudaStream_t s);
+cudaError_t launch_pole_dos(const PoleParams& p, int n_sys, const double* eps_grid, int n_eps,
+                            double eta, const int64_t* pdos_off, double* dos, double* pdos,
+                            cudaStream_t s);
+
 // Shared-memory layout of the point kernels, in 16-byte complex elements (a
 // complex double or a complex FP32 pair): the N_b x N_b matrix (odd leading
 // dimension), P_k, T = Sigma P_k / Y = G P^+ / Gbar A^+, Z = P G (adjoint),
@@ -88,7 +198,6 @@ struct Layout {
   size_t bytes;
 };
 
-__host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
 
 __host__ __device__ inline Layout make_layout(int nbmax, int mmax, int mode, int a_in_smem) {
   Layout L;

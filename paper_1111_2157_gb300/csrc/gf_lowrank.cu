@@ -1,0 +1,423 @@
+// Low-rank (eigenbasis) point kernel of the lattice Green's function (sm_103a).
+//
+// With H_k = U diag(eps) U^+ (one Hermitian eigenproblem per k, computed once
+// per Hamiltonian by k_lr_setup in gf_eig.cu) and Pt = P_k U, the inverse of
+// Eq. dmftloop1 is, in the eigenbasis (Woodbury identity),
+//   U^+ G U = D + D Pt^+ K Pt D,   D = diag(1 / (i w_n + mu - eps)),
+//   K = M^{-1} Sigma,  M = I - Sigma g0,  g_j = Pt D^{j+1} Pt^+  (m x m),
+// so every output of the point kernel follows from m x m algebra:
+//   Tr G    = sum_b d_b + Tr(K g1)
+//   Tr G^2  = sum_b d_b^2 + 2 Tr(K g2) + Tr(K g1 K g1)
+//   P G P^+ = g0 + g0 K g0                                   (G_loc, A_k)
+//   P G^2 P^+ = g1 + g1 K g0 + g0 K g1 + g0 K g1 K g0         (B_k)
+//   U^+ G U (for rho_k) = D + D Pt^+ (K Pt) D, accumulated in the eigenbasis
+//   and rotated back once per k by k_lr_rotate.
+// Work per point: 3 N_b m^2 + O(m^3) complex multiply-adds instead of N_b^3;
+// the partial sums have exactly the layout of k_point_fp64's, so the same
+// finalize and reduction kernels consume them.
+#include <math.h>
+#include <stdint.h>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cmac_ca(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+// acc += a * conj(b)
+__device__ __forceinline__ void cmac_cb(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+  acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
+}
+
+// 1/a by Smith's algorithm (R. L. Smith, CACM 5(8), 1962).
+__device__ __forceinline__ double2 crcp(double2 a) {
+  if (fabs(a.x) >= fabs(a.y)) {
+    const double t = a.y / a.x;
+    const double id = 1.0 / fma(a.y, t, a.x);
+    return make_double2(id, -t * id);
+  } else {
+    const double t = a.x / a.y;
+    const double id = 1.0 / fma(a.x, t, a.y);
+    return make_double2(t * id, -id);
+  }
+}
+
+__device__ __forceinline__ unsigned long long pivot_key(double2 a) {
+  const unsigned long long mask = 0x7fffffffffffffffULL;
+  const unsigned long long r = (unsigned long long)__double_as_longlong(a.x) & mask;
+  const unsigned long long i = (unsigned long long)__double_as_longlong(a.y) & mask;
+  return r > i ? r : i;
+}
+
+__device__ __forceinline__ double lr_block_sum(double v, double* red) {
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < (kThreads / 32) ? red[lane] : 0.0;
+    for (int off = 16; off; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+  }
+  return r;  // valid in thread 0
+}
+
+// Gauss-Jordan reduction of the M x 2M augmented matrix [M_ | Sigma] (row-major,
+// leading dimension 2M) to [I | M_^{-1} Sigma], partial pivoting on the left
+// block.  col and urow: 2M complex scratch each.
+__device__ void gj_augmented(double2* aug, int M, double2* col, double2* urow, int* status) {
+  __shared__ int s_p;
+  __shared__ double2 s_r;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int W = 2 * M;
+  for (int j = 0; j < M; ++j) {
+    if (warp == 0) {
+      unsigned long long best = 0ULL;
+      int bi = 0x7fffffff;
+      for (int i = j + lane; i < M; i += 32) {
+        const unsigned long long key = pivot_key(aug[i * W + j]);
+        if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
+      }
+      for (int off = 16; off; off >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (best == 0ULL || best >= 0x7ff0000000000000ULL) atomicOr(status, kFlagSingular);
+        s_p = bi;
+        s_r = crcp(aug[bi * W + j]);
+      }
+    }
+    __syncthreads();
+    const int pr = s_p;
+    const double2 r = s_r;
+    for (int c = tid; c < W; c += kThreads) {
+      const double2 vp = aug[pr * W + c];
+      urow[c] = (c == j) ? make_double2(1.0, 0.0) : cmul(vp, r);
+      if (pr != j) aug[pr * W + c] = aug[j * W + c];
+    }
+    for (int i = tid; i < M; i += kThreads) col[i] = (i == pr) ? aug[j * W + j] : aug[i * W + j];
+    __syncthreads();
+    for (int e = tid; e < M * W; e += kThreads) {
+      const int i = e / W, c = e - (e / W) * W;
+      if (i == j) {
+        aug[e] = urow[c];
+      } else if (c == j) {
+        aug[e] = make_double2(0.0, 0.0);
+      } else {
+        const double2 l = col[i], u = urow[c];
+        double2 v = aug[e];
+        v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
+        v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
+        aug[e] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// C = X Y for M x M matrices (X with leading dimension ldx), all threads.
+__device__ __forceinline__ void mm(double2* C, const double2* X, int ldx, const double2* Y, int M) {
+  for (int e = threadIdx.x; e < M * M; e += kThreads) {
+    const int a = e / M, b = e - (e / M) * M;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < M; ++c) cmac(acc, X[a * ldx + c], Y[c * M + b]);
+    C[e] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, const LowRank lr) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* sm = reinterpret_cast<double2*>(smraw);
+  __shared__ int s_item;
+  __shared__ double s_red[kThreads / 32];
+  const LRLayout L = make_lr_layout(p.nbmax, p.mmax, p.mode);
+  double2* sPt = sm + L.offPt;
+  double2* sD = sm + L.offD;  // d, d^2, d^3 per band
+  double2* sS = sm + L.offS;
+  double2* g0 = sm + L.offG;
+  double2* g1 = g0 + p.mmax * p.mmax;
+  double2* g2 = g1 + p.mmax * p.mmax;
+  double2* aug = sm + L.offAug;
+  double2* sC = sm + L.offC;    // K g1
+  double2* sC2 = sm + L.offC2;  // K g0
+  double2* sX = sm + L.offX;    // K Pt (rho) / A, B, Gbar, Gbar A^+ (adjoint)
+  double2* sCol = sm + L.offCol;
+  double2* sU = sm + L.offU;
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1);
+    __syncthreads();
+    const int itx = s_item;
+    if (itx >= p.n_items) break;
+    const Item it = p.items[itx];
+    const KInfo ki = p.kinfo[it.k];
+    const SInfo si = p.sinfo[ki.sys];
+    const int N = ki.nb, M = si.m, W = 2 * M;
+    const double mu = p.mu[ki.sys];
+    const double beta = si.beta;
+    const double wk = ki.w;
+    const double* eps = lr.eps + lr.offD[it.k];
+    double nbar = 0.0;
+    if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
+    for (int e = tid; e < M * N; e += kThreads) sPt[e] = lr.Pt[ki.offP + e];
+    double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
+    for (int n = it.n0; n < it.n1; ++n) {
+      const double wn = (2.0 * n + 1.0) * M_PI / beta;
+      const double2* Sg = p.Sig + si.offSig + (int64_t)n * M * M;
+      __syncthreads();
+      for (int b = tid; b < N; b += kThreads) {
+        // d = 1 / (x + i w) = (x - i w) / (x^2 + w^2), x = mu - eps_b
+        const double x = mu - eps[b];
+        const double q = 1.0 / fma(x, x, wn * wn);
+        const double2 d = make_double2(x * q, -wn * q);
+        const double2 d2 = cmul(d, d);
+        sD[b] = d;
+        sD[N + b] = d2;
+        sD[2 * N + b] = cmul(d2, d);
+      }
+      for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
+      __syncthreads();
+      // g_j = Pt D^{j+1} Pt^+
+      const bool need_g2 = (p.mode & kOcc) != 0;
+      const bool need_g1 = (p.mode & (kOcc | kAdj)) != 0;
+      for (int e = tid; e < M * M; e += kThreads) {
+        const int a = e / M, c = e - (e / M) * M;
+        double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0;
+        for (int b = 0; b < N; ++b) {
+          double2 t = make_double2(0.0, 0.0);
+          cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
+          cmac(a0, t, sD[b]);
+          if (need_g1) cmac(a1, t, sD[N + b]);
+          if (need_g2) cmac(a2, t, sD[2 * N + b]);
+        }
+        g0[e] = a0;
+        g1[e] = a1;
+        g2[e] = a2;
+      }
+      __syncthreads();
+      // aug = [I - Sigma g0 | Sigma]
+      for (int e = tid; e < M * M; e += kThreads) {
+        const int a = e / M, c = e - (e / M) * M;
+        double2 acc = make_double2(a == c ? 1.0 : 0.0, 0.0);
+        for (int x = 0; x < M; ++x) {
+          const double2 s = sS[a * M + x], g = g0[x * M + c];
+          acc.x -= fma(s.x, g.x, -s.y * g.y);
+          acc.y -= fma(s.x, g.y, s.y * g.x);
+        }
+        aug[a * W + c] = acc;
+        aug[a * W + M + c] = sS[e];
+      }
+      __syncthreads();
+      gj_augmented(aug, M, sCol, sU, p.status);
+      const double2* K = aug + M;  // K[a * W + c]
+      if (p.mode & (kOcc | kAdj)) mm(sC, K, W, g1, M);
+      if (p.mode & (kGloc | kAdj)) mm(sC2, K, W, g0, M);
+      __syncthreads();
+      if (p.mode & kOcc) {
+        for (int b = tid; b < N; b += kThreads) {
+          acc_tr += sD[b].x;
+          acc_g2 += sD[N + b].x;
+        }
+        for (int e = tid; e < M * M; e += kThreads) {
+          const int a = e / M, c = e - (e / M) * M;
+          // Re of K_ac g1_ca, 2 K_ac g2_ca and (K g1)_ac (K g1)_ca
+          const double2 kk = K[a * W + c];
+          const double2 u = g1[c * M + a], v = g2[c * M + a];
+          const double2 x = sC[e], y = sC[c * M + a];
+          acc_tr += fma(kk.x, u.x, -kk.y * u.y);
+          acc_g2 += 2.0 * fma(kk.x, v.x, -kk.y * v.y) + fma(x.x, y.x, -x.y * y.y);
+        }
+      }
+      if (p.mode & kRho) {
+        // X = K Pt (M x N), then S' += D + D Pt^+ X D in the eigenbasis
+        for (int e = tid; e < M * N; e += kThreads) {
+          const int a = e / N, b = e - (e / N) * N;
+          double2 acc = make_double2(0.0, 0.0);
+          for (int c = 0; c < M; ++c) cmac(acc, K[a * W + c], sPt[c * N + b]);
+          sX[e] = acc;
+        }
+        __syncthreads();
+        double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
+        const bool first = (n == it.n0);
+        for (int e = tid; e < N * N; e += kThreads) {
+          const int b = e / N, c = e - (e / N) * N;
+          double2 acc = make_double2(0.0, 0.0);
+          for (int a = 0; a < M; ++a) cmac_ca(acc, sPt[a * N + b], sX[a * N + c]);
+          double2 g = cmul(cmul(sD[b], acc), sD[c]);
+          if (b == c) { g.x += sD[b].x; g.y += sD[b].y; }
+          if (first) {
+            S[e] = g;
+          } else {
+            double2 s = S[e];
+            s.x += g.x; s.y += g.y;
+            S[e] = s;
+          }
+        }
+      }
+      if (p.mode & kGloc) {
+        // P G P^+ = g0 + g0 (K g0)
+        double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
+        for (int e = tid; e < M * M; e += kThreads) {
+          const int a = e / M, c = e - (e / M) * M;
+          double2 acc = g0[e];
+          for (int x = 0; x < M; ++x) cmac(acc, g0[a * M + x], sC2[x * M + c]);
+          out[e] = make_double2(wk * acc.x, wk * acc.y);
+        }
+      }
+      if (p.mode & kAdj) {
+        double2* Aq = sX;
+        double2* Bq = sX + M * M;
+        double2* Gb = sX + 2 * M * M;
+        double2* Mt = sX + 3 * M * M;
+        double2* CC2 = aug;  // K no longer needed: (K g1)(K g0) in the left half of aug
+        __syncthreads();
+        for (int e = tid; e < M * M; e += kThreads) {
+          const int a = e / M, c = e - (e / M) * M;
+          double2 acc = make_double2(0.0, 0.0);
+          for (int x = 0; x < M; ++x) cmac(acc, sC[a * M + x], sC2[x * M + c]);
+          CC2[a * W + c] = acc;
+        }
+        __syncthreads();
+        // A = g0 + g0 C2;  B = g1 + g1 C2 + g0 (C + C C2)
+        for (int e = tid; e < M * M; e += kThreads) {
+          const int a = e / M, c = e - (e / M) * M;
+          double2 aa = g0[e], bb = g1[e];
+          for (int x = 0; x < M; ++x) {
+            const double2 c2 = sC2[x * M + c];
+            cmac(aa, g0[a * M + x], c2);
+            cmac(bb, g1[a * M + x], c2);
+            double2 t = sC[x * M + c];
+            const double2 u = CC2[x * W + c];
+            t.x += u.x;
+            t.y += u.y;
+            cmac(bb, g0[a * M + x], t);
+          }
+          Aq[e] = aa;
+          Bq[e] = bb;
+        }
+        __syncthreads();
+        const bool have_gbar = (p.gbar != nullptr);
+        if (have_gbar) {
+          const double2* Gsrc = p.gbar + si.offSig + (int64_t)n * M * M;
+          for (int e = tid; e < M * M; e += kThreads) Gb[e] = Gsrc[e];
+          __syncthreads();
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, b = e - (e / M) * M;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int c = 0; c < M; ++c) cmac_cb(acc, Gb[a * M + c], Aq[b * M + c]);
+            Mt[e] = acc;
+          }
+          __syncthreads();
+          for (int e = tid; e < M * M; e += kThreads) {
+            const double2 g = Gb[e], b = Bq[e];
+            acc_mu -= wk * fma(g.x, b.x, g.y * b.y);
+          }
+        }
+        double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
+        const double cb = nbar * 2.0 / beta;
+        for (int e = tid; e < M * M; e += kThreads) {
+          const int a = e / M, b = e - (e / M) * M;
+          double2 acc = make_double2(0.0, 0.0);
+          if (have_gbar)
+            for (int c = 0; c < M; ++c) cmac_ca(acc, Aq[c * M + a], Mt[c * M + b]);
+          const double2 bt = Bq[b * M + a];
+          acc.x = fma(cb, bt.x, acc.x);
+          acc.y = fma(-cb, bt.y, acc.y);
+          out[e] = make_double2(wk * acc.x, wk * acc.y);
+        }
+      }
+    }
+    if (p.mode & kOcc) {
+      const double tr = lr_block_sum(acc_tr, s_red);
+      const double g2s = lr_block_sum(acc_g2, s_red);
+      if (tid == 0) {
+        double* o = p.occ_part + ((int64_t)it.k * p.n_chunks + it.chunk) * 2;
+        o[0] = tr;
+        o[1] = g2s;
+      }
+    }
+    if (p.mode & kAdj) {
+      const double mb = lr_block_sum(acc_mu, s_red);
+      if (tid == 0) p.mubar_part[(int64_t)it.k * p.n_chunks + it.chunk] = mb;
+    }
+    __syncthreads();
+  }
+}
+
+// rho_part chunk 0 <- U (sum_c S'_c) U^+ for every k (one CTA per k); T is a
+// scratch of the size of H.
+__global__ void __launch_bounds__(kThreads)
+    k_lr_rotate(const KInfo* __restrict__ kinfo, const double2* __restrict__ U, double2* rho_part,
+                int64_t stride, int n_chunks, double2* T) {
+  const KInfo ki = kinfo[blockIdx.x];
+  const int N = ki.nb;
+  const double2* Uk = U + ki.offH;
+  double2* S0 = rho_part + ki.offH;
+  double2* Tk = T + ki.offH;
+  // T = (sum_c S'_c) U^+
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - (e / N) * N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < N; ++l) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int c = 0; c < n_chunks; ++c) {
+        const double2 v = rho_part[(int64_t)c * stride + ki.offH + i * N + l];
+        s.x += v.x;
+        s.y += v.y;
+      }
+      cmac_cb(acc, s, Uk[j * N + l]);
+    }
+    Tk[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - (e / N) * N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < N; ++l) cmac(acc, Uk[i * N + l], Tk[l * N + j]);
+    S0[e] = acc;
+  }
+}
+
+}  // namespace
+
+size_t point_lr_smem(int nbmax, int mmax, int mode) { return make_lr_layout(nbmax, mmax, mode).bytes; }
+
+int point_lr_blocks_per_sm(size_t smem) {
+  int n = 0;
+  cudaFuncSetAttribute(k_point_lr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_point_lr, kThreads, smem);
+  return n;
+}
+
+cudaError_t launch_point_lr(const PointParams& p, const LowRank& lr, int grid, size_t smem,
+                            cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_point_lr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_point_lr<<<grid, kThreads, smem, s>>>(p, lr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lr_rotate(const KInfo* kinfo, int n_k, const double2* U, double2* rho_part,
+                             int64_t stride, int n_chunks, double2* T, cudaStream_t s) {
+  k_lr_rotate<<<n_k, kThreads, 0, s>>>(kinfo, U, rho_part, stride, n_chunks, T);
+  return cudaGetLastError();
+}
+
+}  // namespace gf

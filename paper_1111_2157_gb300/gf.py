@@ -25,7 +25,10 @@ DTYPE = {"c128": 0, "c64": 1}
 EXPORTS = ["gf_create", "gf_destroy", "gf_set_hamiltonian", "gf_set_projectors", "gf_set_sigma",
            "gf_local", "gf_occupation", "gf_find_mu", "gf_density_matrix", "gf_backward",
            "gf_evaluate", "gf_occupation_static", "gf_last_error", "gf_last_stats",
-           "gf_tuning_log"]
+           "gf_tuning_log", "gf_set_sigma_poles", "gf_pole_occupation", "gf_pole_find_mu",
+           "gf_pole_density_matrix", "gf_pole_local", "gf_heev_batched",
+           "gf_set_projectors_lowdin", "gf_impurity_levels", "gf_hybridization",
+           "gf_double_counting", "gf_pole_spectral", "gf_pole_energy"]
 
 
 class GFError(RuntimeError):
@@ -44,6 +47,7 @@ class GFDesc(ctypes.Structure):
                 ("tail_order", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("flags", ctypes.c_int32)]
 GF_FLAG_GRAPH = 1
+GF_FLAG_LOWRANK = 2
 
 
 def load():
@@ -70,6 +74,19 @@ def load():
     lib.gf_occupation_static.argtypes = [vp, vp, vp, vp, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int32, vp, dp, dp]
+    lib.gf_set_sigma_poles.argtypes = [vp, ip, vp, vp, vp]
+    lib.gf_pole_occupation.argtypes = [vp, dp, dp, dp]
+    lib.gf_pole_find_mu.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int32, dp, ip]
+    lib.gf_pole_density_matrix.argtypes = [vp, dp, vp, dp]
+    lib.gf_pole_local.argtypes = [vp, dp, vp]
+    lib.gf_heev_batched.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp, vp]
+    lib.gf_pole_spectral.argtypes = [vp, dp, ctypes.c_int32, dp, ctypes.c_double, dp, dp]
+    lib.gf_pole_energy.argtypes = [vp, dp, dp, dp]
+    lib.gf_set_projectors_lowdin.argtypes = [vp, vp, vp]
+    lib.gf_impurity_levels.argtypes = [vp, dp, vp]
+    lib.gf_hybridization.argtypes = [vp, dp, vp, dp, vp]
+    lib.gf_double_counting.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                       ctypes.c_double, dp, dp, dp]
     lib.gf_last_error.argtypes = [vp]
     lib.gf_last_error.restype = ctypes.c_char_p
     lib.gf_tuning_log.argtypes = [vp]
@@ -81,6 +98,41 @@ def load():
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def _is_tensor(x):
+    import torch
+    return isinstance(x, torch.Tensor)
+
+
+def heev_batched(A, max_sweeps=40, stream=None):
+    """Eigen-decomposition of a batch of Hermitian matrices A [n_mat, n, n]
+    (complex128 CUDA tensor) by the library's Jacobi kernel: (w ascending, V)."""
+    import torch
+    lib = load()
+    A = A.to(torch.complex128).contiguous()
+    n_mat, n = A.shape[0], A.shape[-1]
+    w = torch.empty((n_mat, n), dtype=torch.float64, device=A.device)
+    V = torch.empty((n_mat, n, n), dtype=torch.complex128, device=A.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device).cuda_stream
+    st = lib.gf_heev_batched(ctypes.c_void_p(A.data_ptr()), n_mat, n, int(max_sweeps),
+                             ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                             ctypes.c_void_p(int(stream)))
+    if st != GF_OK:
+        raise GFError(st, lib.gf_last_error(None).decode())
+    return w, V
+
+
+def double_counting(U, J, l, n):
+    """(U_bar, V_DC, E_DC) of the double-counting formulas (host arithmetic in libgf)."""
+    lib = load()
+    ub, vdc, edc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = lib.gf_double_counting(float(U), float(J), int(l), float(n), ctypes.byref(ub),
+                                ctypes.byref(vdc), ctypes.byref(edc))
+    if st != GF_OK:
+        raise GFError(st, lib.gf_last_error(None).decode())
+    return ub.value, vdc.value, edc.value
 
 
 def _doubles(values, n):
@@ -116,7 +168,7 @@ class GreensFunction:
     """
 
     def __init__(self, nb, m, n_iw, beta, k_system=None, n_k=None, k_weight=None, precision="fp64",
-                 input_dtype="c128", tail_order=2, device=0, stream=None, graph=False):
+                 input_dtype="c128", tail_order=2, device=0, stream=None, graph=False, lowrank=False):
         import torch
         self.lib = load()
         self.device = int(device)
@@ -154,7 +206,7 @@ class GreensFunction:
         d.tail_order = int(tail_order)
         d.device = self.device
         d.stream = int(stream)
-        d.flags = GF_FLAG_GRAPH if graph else 0
+        d.flags = (GF_FLAG_GRAPH if graph else 0) | (GF_FLAG_LOWRANK if lowrank else 0)
         h = ctypes.c_void_p()
         st = self.lib.gf_create(ctypes.byref(h), ctypes.byref(d))
         if st != GF_OK:
@@ -168,14 +220,15 @@ class GreensFunction:
 
     @classmethod
     def for_systems(cls, systems, precision="fp64", input_dtype="c128", tail_order=2, device=0,
-                    graph=False):
+                    graph=False, lowrank=False):
         """Context for a list of ``synth.System`` (one or several, ragged or not)."""
         nb = np.concatenate([s.nb for s in systems])
         ks = np.concatenate([np.full(s.nk, i, np.int32) for i, s in enumerate(systems)])
         n_iw = systems[0].n_iw
         return cls(nb, [s.m for s in systems], n_iw, [s.beta for s in systems],
                    k_system=ks if len(systems) > 1 else None, precision=precision,
-                   input_dtype=input_dtype, tail_order=tail_order, device=device, graph=graph)
+                   input_dtype=input_dtype, tail_order=tail_order, device=device, graph=graph,
+                   lowrank=lowrank)
 
     def _check(self, st):
         if st != GF_OK:
@@ -281,6 +334,102 @@ class GreensFunction:
                                          ctypes.c_void_p(o.ptr),
                                          mub.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out, mub
+
+    # ------------------------------------- projectors and the DMFT step
+    def set_projectors_lowdin(self, W, out=None):
+        """Make P_k = (W_k W_k^+)^{-1/2} W_k the projectors; returns P (complex128)."""
+        a = _Arg(W, self._cdt())
+        out = self._out(self.tot_p, out)
+        o = _Arg(out)
+        self._check(self.lib.gf_set_projectors_lowdin(self.h, a.ptr, ctypes.c_void_p(o.ptr)))
+        return out
+
+    def impurity_levels(self, v_dc=None, out=None):
+        """E_imp = sum_k w_k P H P^+ - V_DC, packed [sum m_s^2] complex128."""
+        keep, vp_ = (None, None) if v_dc is None else _doubles(v_dc, self.n_sys)
+        out = self._out(self.tot_sinf, out)
+        o = _Arg(out)
+        self._check(self.lib.gf_impurity_levels(self.h, vp_, ctypes.c_void_p(o.ptr)))
+        return out
+
+    def hybridization(self, mu, gloc, v_dc=None, out=None):
+        """Delta(i w_n) = (i w_n + mu) - E_imp - Sigma - G_loc^{-1}, packed like Sigma."""
+        _, mp = _doubles(mu, self.n_sys)
+        keep, vp_ = (None, None) if v_dc is None else _doubles(v_dc, self.n_sys)
+        g = _Arg(gloc, "complex128")
+        out = self._out(self.tot_sig, out)
+        o = _Arg(out)
+        self._check(self.lib.gf_hybridization(self.h, mp, g.ptr, vp_, ctypes.c_void_p(o.ptr)))
+        return out
+
+    # ------------------------------------------------ pole (pseudo-H) path
+    def set_sigma_poles(self, n_poles, poles, V, sigma_inf):
+        """Pole form of Sigma per system: n_poles [n_sys], poles [sum n_p] real,
+        V [sum n_p * m_s] complex (row i = V_i), sigma_inf packed [sum m_s^2]."""
+        npl = np.ascontiguousarray(np.atleast_1d(n_poles), dtype=np.int32)
+        pa = _Arg(np.asarray(poles, dtype=np.float64).reshape(-1) if not _is_tensor(poles) else
+                  poles.double().reshape(-1))
+        va, sa = _Arg(V, self._cdt()), _Arg(sigma_inf, self._cdt())
+        self._check(self.lib.gf_set_sigma_poles(self.h, npl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                pa.ptr, va.ptr, sa.ptr))
+
+    def pole_occupation(self, mu):
+        """(N, dN/dmu) per system from the pseudo-Hamiltonian eigenpairs."""
+        _, mp = _doubles(mu, self.n_sys)
+        n, d = np.zeros(self.n_sys), np.zeros(self.n_sys)
+        self._check(self.lib.gf_pole_occupation(self.h, mp, n.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return n, d
+
+    def pole_find_mu(self, n_target, mu0=0.0, tol=1e-10, max_iter=60):
+        _, tp = _doubles(n_target, self.n_sys)
+        mu = np.ascontiguousarray(np.broadcast_to(np.asarray(mu0, np.float64), (self.n_sys,))).copy()
+        it = ctypes.c_int32()
+        self._check(self.lib.gf_pole_find_mu(self.h, tp, float(tol), int(max_iter),
+                                             mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             ctypes.byref(it)))
+        return mu, it.value
+
+    def pole_density_matrix(self, mu, out=None, want_rho=True):
+        _, mp = _doubles(mu, self.n_sys)
+        nc = np.zeros(self.n_sys)
+        o = _Arg(self._out(self.tot_h, out)) if want_rho else None
+        self._check(self.lib.gf_pole_density_matrix(self.h, mp, ctypes.c_void_p(o.ptr if o else 0),
+                                                    nc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return (o.obj if o else None), nc
+
+    def pole_local(self, mu, out=None):
+        _, mp = _doubles(mu, self.n_sys)
+        out = self._out(self.tot_sig, out)
+        o = _Arg(out)
+        self._check(self.lib.gf_pole_local(self.h, mp, ctypes.c_void_p(o.ptr)))
+        return out
+
+    def pole_spectral(self, mu, eps, eta, pdos=True):
+        """(DOS [n_sys, n_eps], PDOS per system [n_eps, m_s] or None) on the real axis."""
+        _, mp = _doubles(mu, self.n_sys)
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        dos = np.zeros((self.n_sys, len(e)))
+        pd = np.zeros(len(e) * int(np.sum(self.m))) if pdos else None
+        dp_ = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.gf_pole_spectral(self.h, mp, len(e), e.ctypes.data_as(dp_), float(eta),
+                                              dos.ctypes.data_as(dp_),
+                                              pd.ctypes.data_as(dp_) if pdos else None))
+        if not pdos:
+            return dos, None
+        out, off = [], 0
+        for m in self.m:
+            out.append(pd[off:off + len(e) * m].reshape(len(e), m))
+            off += len(e) * m
+        return dos, out
+
+    def pole_energy(self, mu):
+        """(h_ks, e_ps) per system: Tr(H rho) and sum_l (E_l - mu)|Psi_b,l|^2 n_F."""
+        _, mp = _doubles(mu, self.n_sys)
+        a, b = np.zeros(self.n_sys), np.zeros(self.n_sys)
+        dp_ = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.gf_pole_energy(self.h, mp, a.ctypes.data_as(dp_), b.ctypes.data_as(dp_)))
+        return a, b
 
     def tuning_log(self):
         """Kernel configuration chosen for this context (autotuner report)."""

@@ -16,10 +16,10 @@ def pack(blocks):
     return np.concatenate([np.asarray(b).reshape(-1) for b in blocks])
 
 
-def make_gf(systems, precision="fp64", tail_order=2, input_dtype="c128", graph=False):
+def make_gf(systems, precision="fp64", tail_order=2, input_dtype="c128", graph=False, lowrank=False):
     from paper_1111_2157_gb300.gf import GreensFunction
     g = GreensFunction.for_systems(systems, precision=precision, tail_order=tail_order,
-                                   input_dtype=input_dtype, graph=graph)
+                                   input_dtype=input_dtype, graph=graph, lowrank=lowrank)
     g.set_hamiltonian(pack([pack(s.H) for s in systems]))
     g.set_projectors(pack([pack(s.P) for s in systems]))
     g.set_sigma(pack([s.sigma for s in systems]), pack([s.sigma_inf for s in systems]))
@@ -43,9 +43,10 @@ def oracle_all(s, mu, tail_order=2, gloc=True):
 
 
 def check_system_set(systems, mus, tol, precision="fp64", tail_order=2, input_dtype="c128",
-                     report=None):
+                     report=None, lowrank=False):
     """Every output of the CUDA path (G_loc, N, dN/dmu, n_corr, rho) against the oracle."""
-    g = make_gf(systems, precision=precision, tail_order=tail_order, input_dtype=input_dtype)
+    g = make_gf(systems, precision=precision, tail_order=tail_order, input_dtype=input_dtype,
+                lowrank=lowrank)
     gl = g.local(mus).cpu().numpy()
     n, dn = g.occupation(mus)
     rho, nc = g.density_matrix(mus)

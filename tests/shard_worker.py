@@ -50,3 +50,35 @@ def run(rank, world_size, port, out_path):
             np.savez(out_path, mu=mu, evals=evals, gloc=g.numpy(), N=n, dN=dn, k0=k0, k1=k1)
     finally:
         dist.destroy_process_group()
+
+
+def run_gpu(rank, world_size, port, out_path):
+    """Each rank builds a GreensFunction for its k-slice (weights of the full set) on cuda:0;
+    gloo all-reduces host copies of the partial sums."""
+    import torch
+    from paper_1111_2157_gb300 import gf as gfm
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world_size, timeout=datetime.timedelta(seconds=120))
+    try:
+        s = sharded_case()
+        k0, k1 = shard.partition_k(s.nb, world_size)[rank]
+        nb = s.nb[k0:k1]
+        g = gfm.GreensFunction(nb, s.m, s.n_iw, s.beta, k_weight=s.weights[k0:k1])
+        g.set_hamiltonian(np.concatenate([h.reshape(-1) for h in s.H[k0:k1]]))
+        g.set_projectors(np.concatenate([p.reshape(-1) for p in s.P[k0:k1]]))
+        g.set_sigma(s.sigma, s.sigma_inf)
+        base = shard.greens_function_evaluator(g)
+        lat = shard.ShardedLattice(lambda mu, gl: _to_host(base(mu, gl)))
+        mu, evals = lat.find_mu(s.n_target, mu0=0.0, tol=1e-11)
+        gloc, n, dn = lat.evaluate(mu, gloc=True)
+        torch.cuda.synchronize()
+        if rank == 0:
+            np.savez(out_path, mu=mu, evals=evals, gloc=gloc.numpy(), N=n, dN=dn)
+        g.close()
+    finally:
+        dist.destroy_process_group()
+
+
+def _to_host(r):
+    g, n, dn = r
+    return (None if g is None else g.cpu()), n, dn

@@ -21,6 +21,7 @@ def test_one_launch_for_all_systems_matches_oracle(precision):
     g = make_gf(systems, precision=precision)
     mus = [0.1 * i for i in range(len(systems))]
     n, dn = g.occupation(mus)
+    g.local(mus)  # the first call of a mode may also run the autotuner's sample launches
     gl = g.local(mus).cpu().numpy()
     st = g.stats()
     off = 0
@@ -34,7 +35,8 @@ def test_one_launch_for_all_systems_matches_oracle(precision):
             glo = oracle.get().local(s.H, s.P, s.sigma, s.beta, mus[i])
             assert rel(gl[off:off + size], glo.reshape(-1)) < tol
         off += size
-    # G_loc of all systems comes from one point-kernel launch plus one k-reduction
+    # G_loc of all systems comes from one point-kernel launch per band-window bucket
+    # (N_b <= 64, <= 96, > 96) plus one k-reduction
     assert st["launches"] <= 4
 
 

@@ -52,3 +52,23 @@ def test_two_rank_lattice_sum_and_mu_search_match_single_process(tmp_path, world
     mu_ref, _, _ = o.find_mu(s.H, s.P, s.sigma, s.sigma_inf, s.beta, s.n_target, -5.0, 5.0,
                              weights=s.weights, tol=1e-12)
     assert abs(mu - mu_ref) <= 1e-9
+
+
+@pytest.mark.gpu
+def test_two_rank_sharding_over_the_cuda_path():
+    """Two ranks, each a CUDA context on its k-slice; the reduced sums match the oracle."""
+    import tempfile
+    from pathlib import Path
+    with tempfile.TemporaryDirectory() as d:
+        out = Path(d) / "rank0.npz"
+        tmp.start_processes(shard_worker.run_gpu, args=(2, _free_port(), str(out)), nprocs=2,
+                            join=True, start_method="spawn")
+        r = np.load(out)
+    s = shard_worker.sharded_case()
+    o = oracle.get()
+    mu = float(r["mu"][0])
+    full = o.density(s.H, s.P, s.sigma, s.sigma_inf, s.beta, mu, weights=s.weights, want_rho=False)
+    assert abs(full["N"] - s.n_target) <= 2e-11
+    assert abs(r["N"][0] - full["N"]) <= 1e-12 * full["N"]
+    gl = o.local(s.H, s.P, s.sigma, s.beta, mu, weights=s.weights)
+    assert np.max(np.abs(r["gloc"] - gl)) <= 1e-12 * np.max(np.abs(gl))
