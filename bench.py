@@ -389,22 +389,23 @@ def run_workload(args):
         gsub.close()
     elif args.workload == "lowrank":
         # eigenbasis (Woodbury) algorithm against the direct inverse, FP64, at fixed mu
-        out["config"] = "Ce-like full size; NiO-like with N_k = 1024 of its 4096 k-points"
-        for name, s in _lr_pole_cases(args, synth):
-            mu = 0.3
-            gd = _context(gf, [s], "fp64")
-            gl = _context(gf, [s], "fp64", lowrank=True)
+        out["config"] = ("Ce-like full size; NiO-like with N_k = 1024 of its 4096 k-points; the batched "
+                         f"workload with its k-sets scaled by {args.nk_scale}")
+        cases = [(name, [s]) for name, s in _lr_pole_cases(args, synth)]
+        if not (args.nk or args.n_iw):
+            cases.append(("batched", synth.batched(nk_scale=args.nk_scale).systems))
+        for name, systems in cases:
+            mu = [0.3] * len(systems)
+            gd = _context(gf, systems, "fp64")
+            gl = _context(gf, systems, "fp64", lowrank=True)
             gd.occupation(mu)
             (nd, dd), td = _sync_time(lambda: gd.occupation(mu))
             sd = gd.stats()
             _, t_setup = _sync_time(lambda: gl.occupation(mu))  # includes the eigen-decomposition
             (nl, dl), tl = _sync_time(lambda: gl.occupation(mu))
             sl = gl.stats()
-            ed, t_ed = _sync_time(lambda: gd.evaluate(mu, rho=True, n_corr=True))
-            el, t_el = _sync_time(lambda: gl.evaluate(mu, rho=True, n_corr=True))
-            (mu_l, it_l), t_mu = _sync_time(lambda: gl.find_mu(s.n_target, 0.0, tol=1e-10))
-            pts = s.nk * s.n_iw
-            out[name] = {
+            pts = sum(s.nk * s.n_iw for s in systems)
+            res = {
                 "points": pts,
                 "direct_occupation_s": td, "lowrank_occupation_s": tl,
                 "lowrank_first_call_s_with_eigendecomposition": t_setup,
@@ -413,11 +414,19 @@ def run_workload(args):
                 "lowrank_kernel_tflops": sl["flops"] / sl["kernel_ms"] / 1e9,
                 "lowrank_frac_of_fp64_peak": sl["flops"] / sl["kernel_ms"] / 1e9 / FP64_PEAK_TFLOPS,
                 "direct_kernel_tflops": sd["flops"] / sd["kernel_ms"] / 1e9,
-                "N_rel_diff": abs(nl[0] - nd[0]) / nd[0], "dN_rel_diff": abs(dl[0] - dd[0]) / dd[0],
-                "evaluate_direct_s": t_ed, "evaluate_lowrank_s": t_el,
-                "G_loc_rel_diff": float((el["gloc"] - ed["gloc"]).abs().max() / ed["gloc"].abs().max()),
-                "rho_rel_diff": float((el["rho"] - ed["rho"]).abs().max() / ed["rho"].abs().max()),
-                "find_mu_s": t_mu, "find_mu_evaluations": it_l}
+                "N_rel_diff": float(np.max(np.abs(nl - nd) / nd)),
+                "dN_rel_diff": float(np.max(np.abs(dl - dd) / dd))}
+            if len(systems) == 1:
+                s = systems[0]
+                ed, t_ed = _sync_time(lambda: gd.evaluate(mu, rho=True, n_corr=True))
+                el, t_el = _sync_time(lambda: gl.evaluate(mu, rho=True, n_corr=True))
+                (mu_l, it_l), t_mu = _sync_time(lambda: gl.find_mu(s.n_target, 0.0, tol=1e-10))
+                res.update({
+                    "evaluate_direct_s": t_ed, "evaluate_lowrank_s": t_el,
+                    "G_loc_rel_diff": float((el["gloc"] - ed["gloc"]).abs().max() / ed["gloc"].abs().max()),
+                    "rho_rel_diff": float((el["rho"] - ed["rho"]).abs().max() / ed["rho"].abs().max()),
+                    "find_mu_s": t_mu, "find_mu_evaluations": it_l})
+            out[name] = res
             gd.close()
             gl.close()
     elif args.workload == "pole":

@@ -71,4 +71,4 @@ def test_two_rank_sharding_over_the_cuda_path():
     assert abs(full["N"] - s.n_target) <= 2e-11
     assert abs(r["N"][0] - full["N"]) <= 1e-12 * full["N"]
     gl = o.local(s.H, s.P, s.sigma, s.beta, mu, weights=s.weights)
-    assert np.max(np.abs(r["gloc"] - gl)) <= 1e-12 * np.max(np.abs(gl))
+    assert np.max(np.abs(r["gloc"].reshape(gl.shape) - gl)) <= 1e-12 * np.max(np.abs(gl))
