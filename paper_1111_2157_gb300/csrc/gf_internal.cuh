@@ -110,6 +110,13 @@ struct PoleParams {
   double* wbout;        // band weights |Psi_b,l|^2 per k at eoff[k] (kGloc), or null
   double* kHks;         // [n_k] Re Tr(H_k rho_k) (kRho), or null
   double* kEps;         // [n_k] sum_l (E_l - mu) |Psi_b,l|^2 n_F (kRho), or null
+  // warm start of the mu search: eigenpairs of the previous evaluation
+  double2* vstore;      // eigenvectors per k, [n][n] at voff[k] (row i, column l), or null
+  double* estore;       // eigenvalues per k at eoff[k]
+  const int64_t* voff;
+  const double* mu_prev;  // [n_sys] mu of the stored eigenpairs
+  int warm;             // 1: start Jacobi from the stored eigenpairs
+  int save_v;           // 1: store this evaluation's eigenpairs
   int* status;
 };
 
@@ -120,15 +127,17 @@ struct LowRank {
   const double* eps;     // [sum_k N_b] at offD[k]
   const int64_t* offD;
   const double2* Pt;     // [m][N_b] per k at KInfo::offP
+  int t_in_smem;         // 1: the pair table Pt_ab conj(Pt_cb) of an item is kept in shared memory
 };
 
-// Shared-memory layout of k_point_lr (16-byte complex elements).
+// Shared-memory layout of k_point_lr (16-byte complex elements).  offT: the
+// pair table T[p][b] = Pt_ab conj(Pt_cb), p over the pairs a <= c (m(m+1)/2).
 struct LRLayout {
-  int offPt, offD, offS, offG, offAug, offC, offC2, offX, offCol, offU;
+  int offPt, offD, offS, offG, offAug, offC, offC2, offX, offCol, offU, offT;
   size_t bytes;
 };
 
-__host__ __device__ inline LRLayout make_lr_layout(int nbmax, int mmax, int mode) {
+__host__ __device__ inline LRLayout make_lr_layout(int nbmax, int mmax, int mode, int t_in_smem) {
   LRLayout L;
   const int mm = mmax * mmax;
   int o = 0;
@@ -142,11 +151,12 @@ __host__ __device__ inline LRLayout make_lr_layout(int nbmax, int mmax, int mode
   L.offX = o; o += imax((mode & kRho) ? mmax * nbmax : 0, (mode & kAdj) ? 4 * mm : 0);
   L.offCol = o; o += 2 * mmax;
   L.offU = o; o += 2 * mmax;
+  L.offT = o; o += t_in_smem ? (mmax * (mmax + 1) / 2) * nbmax : 0;
   L.bytes = (size_t)o * 16;
   return L;
 }
 
-size_t point_lr_smem(int nbmax, int mmax, int mode);
+size_t point_lr_smem(int nbmax, int mmax, int mode, int t_in_smem);
 int point_lr_blocks_per_sm(size_t smem);
 cudaError_t launch_point_lr(const PointParams& p, const LowRank& lr, int grid, size_t smem,
                             cudaStream_t s);

@@ -113,18 +113,20 @@ __device__ void gj_augmented(double2* aug, int M, double2* col, double2* urow, i
     }
     for (int i = tid; i < M; i += kThreads) col[i] = (i == pr) ? aug[j * W + j] : aug[i * W + j];
     __syncthreads();
-    for (int e = tid; e < M * W; e += kThreads) {
-      const int i = e / W, c = e - (e / W) * W;
+    // columns c < j of the left block are unit columns already: nothing to update
+    const int Wj = W - j;
+    for (int e = tid; e < M * Wj; e += kThreads) {
+      const int i = e / Wj, c = j + (e - (e / Wj) * Wj);
       if (i == j) {
-        aug[e] = urow[c];
+        aug[i * W + c] = urow[c];
       } else if (c == j) {
-        aug[e] = make_double2(0.0, 0.0);
+        aug[i * W + c] = make_double2(0.0, 0.0);
       } else {
         const double2 l = col[i], u = urow[c];
-        double2 v = aug[e];
+        double2 v = aug[i * W + c];
         v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
         v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
-        aug[e] = v;
+        aug[i * W + c] = v;
       }
     }
     __syncthreads();
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
   double2* sm = reinterpret_cast<double2*>(smraw);
   __shared__ int s_item;
   __shared__ double s_red[kThreads / 32];
-  const LRLayout L = make_lr_layout(p.nbmax, p.mmax, p.mode);
+  const LRLayout L = make_lr_layout(p.nbmax, p.mmax, p.mode, lr.t_in_smem);
   double2* sPt = sm + L.offPt;
   double2* sD = sm + L.offD;  // d, d^2, d^3 per band
   double2* sS = sm + L.offS;
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
   double2* sX = sm + L.offX;    // K Pt (rho) / A, B, Gbar, Gbar A^+ (adjoint)
   double2* sCol = sm + L.offCol;
   double2* sU = sm + L.offU;
+  double2* sTp = sm + L.offT;
   const int tid = threadIdx.x;
 
   for (;;) {
@@ -177,6 +180,21 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
     double nbar = 0.0;
     if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
     for (int e = tid; e < M * N; e += kThreads) sPt[e] = lr.Pt[ki.offP + e];
+    // pairs a <= c, enumerated row by row; S threads share one pair's band sum
+    const int NP = M * (M + 1) / 2;
+    const int S = NP >= kThreads ? 1 : (2 * NP <= kThreads ? (4 * NP <= kThreads ? 4 : 2) : 1);
+    if (lr.t_in_smem) {
+      __syncthreads();
+      for (int e = tid; e < NP * N; e += kThreads) {
+        const int pq = e / N, b = e - (e / N) * N;
+        int a = 0, rem = pq;
+        while (rem >= M - a) { rem -= M - a; ++a; }
+        const int c = a + rem;
+        double2 t = make_double2(0.0, 0.0);
+        cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
+        sTp[e] = t;
+      }
+    }
     double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
     for (int n = it.n0; n < it.n1; ++n) {
       const double wn = (2.0 * n + 1.0) * M_PI / beta;
@@ -194,22 +212,60 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
       }
       for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
       __syncthreads();
-      // g_j = Pt D^{j+1} Pt^+
+      // g_j = Pt D^{j+1} Pt^+.  With d = dr + i di and t = Pt_ab conj(Pt_cb):
+      // (g_j)_ac = Xr + i Xi and (g_j)_ca = conj(Xr) + i conj(Xi), Xr = sum t dr,
+      // Xi = sum t di, so only the pairs a <= c are summed.
       const bool need_g2 = (p.mode & kOcc) != 0;
       const bool need_g1 = (p.mode & (kOcc | kAdj)) != 0;
-      for (int e = tid; e < M * M; e += kThreads) {
-        const int a = e / M, c = e - (e / M) * M;
-        double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0;
-        for (int b = 0; b < N; ++b) {
-          double2 t = make_double2(0.0, 0.0);
-          cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
-          cmac(a0, t, sD[b]);
-          if (need_g1) cmac(a1, t, sD[N + b]);
-          if (need_g2) cmac(a2, t, sD[2 * N + b]);
+      // (the loop bound is uniform across the block, so every lane of a warp reaches the
+      // shuffles; lanes past the end sum nothing and write nothing)
+      for (int base = 0; base < NP * S; base += kThreads) {
+        const int e = base + tid;
+        const bool valid = e < NP * S;
+        const int pq = valid ? e / S : 0, part = valid ? e - (e / S) * S : 0;
+        int a = 0, rem = pq;
+        while (rem >= M - a) { rem -= M - a; ++a; }
+        const int c = a + rem;
+        double2 xr0 = make_double2(0.0, 0.0), xi0 = xr0, xr1 = xr0, xi1 = xr0, xr2 = xr0, xi2 = xr0;
+        for (int b = part; valid && b < N; b += S) {
+          double2 t;
+          if (lr.t_in_smem) {
+            t = sTp[pq * N + b];
+          } else {
+            t = make_double2(0.0, 0.0);
+            cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
+          }
+          const double2 d0 = sD[b];
+          xr0.x = fma(t.x, d0.x, xr0.x); xr0.y = fma(t.y, d0.x, xr0.y);
+          xi0.x = fma(t.x, d0.y, xi0.x); xi0.y = fma(t.y, d0.y, xi0.y);
+          if (need_g1) {
+            const double2 d1 = sD[N + b];
+            xr1.x = fma(t.x, d1.x, xr1.x); xr1.y = fma(t.y, d1.x, xr1.y);
+            xi1.x = fma(t.x, d1.y, xi1.x); xi1.y = fma(t.y, d1.y, xi1.y);
+          }
+          if (need_g2) {
+            const double2 d2 = sD[2 * N + b];
+            xr2.x = fma(t.x, d2.x, xr2.x); xr2.y = fma(t.y, d2.x, xr2.y);
+            xi2.x = fma(t.x, d2.y, xi2.x); xi2.y = fma(t.y, d2.y, xi2.y);
+          }
         }
-        g0[e] = a0;
-        g1[e] = a1;
-        g2[e] = a2;
+        // the S partial sums of a pair sit in consecutive lanes of one warp (S | 32 and
+        // base is a multiple of 32)
+        for (int off = 1; off < S; off <<= 1) {
+#define GF_LR_RED(v)                                        \
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, off);            \
+  v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+          GF_LR_RED(xr0) GF_LR_RED(xi0) GF_LR_RED(xr1) GF_LR_RED(xi1) GF_LR_RED(xr2) GF_LR_RED(xi2)
+#undef GF_LR_RED
+        }
+        if (valid && part == 0) {
+          g0[a * M + c] = make_double2(xr0.x - xi0.y, xr0.y + xi0.x);
+          g0[c * M + a] = make_double2(xr0.x + xi0.y, xi0.x - xr0.y);
+          g1[a * M + c] = make_double2(xr1.x - xi1.y, xr1.y + xi1.x);
+          g1[c * M + a] = make_double2(xr1.x + xi1.y, xi1.x - xr1.y);
+          g2[a * M + c] = make_double2(xr2.x - xi2.y, xr2.y + xi2.x);
+          g2[c * M + a] = make_double2(xr2.x + xi2.y, xi2.x - xr2.y);
+        }
       }
       __syncthreads();
       // aug = [I - Sigma g0 | Sigma]
@@ -397,7 +453,9 @@ __global__ void __launch_bounds__(kThreads)
 
 }  // namespace
 
-size_t point_lr_smem(int nbmax, int mmax, int mode) { return make_lr_layout(nbmax, mmax, mode).bytes; }
+size_t point_lr_smem(int nbmax, int mmax, int mode, int t_in_smem) {
+  return make_lr_layout(nbmax, mmax, mode, t_in_smem).bytes;
+}
 
 int point_lr_blocks_per_sm(size_t smem) {
   int n = 0;
