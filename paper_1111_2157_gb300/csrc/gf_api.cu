@@ -151,10 +151,11 @@ struct gf_ctx {
   DevBuf eimp, eimp_part, gl_in, delta, wraw, vdc;
   // pole form of Sigma (gf_set_sigma_poles) and the pseudo-Hamiltonian path
   bool have_poles = false;
+  int64_t pole_v_elems = 0, pole_e_elems = 0;
   std::vector<gf::PInfo> pinfo;
   int nps_max = 0;
   DevBuf poles, Vp, Sinf_p, pinfo_d, eoff_d, phioff_d, eout, phiout, pole_ws, wbout, kHks, kEps,
-      eps_grid, dos, pdos, pdos_off, pole_part;
+      eps_grid, dos, pdos, pdos_off, pole_part, pole_vs, pole_es, voff_d, mu_prev;
 };
 
 namespace {
@@ -278,6 +279,7 @@ struct LaunchCfg {
   int grid = 1;
   int a_in_smem = 1;
   int nbmax = 1;
+  int pair_table = 0;  // low-rank kernel: pair table of the item in shared memory
 };
 
 gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_items) {
@@ -292,7 +294,8 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
   p.n_items = n_items;
   const int grid = std::min(cfg.grid, std::max(1, n_items));
   if (cfg.kind == 3) {
-    gf::LowRank lr{c->lr_eps.as<double>(), c->offD_d.as<int64_t>(), c->lr_Pt.as<double2>()};
+    gf::LowRank lr{c->lr_eps.as<double>(), c->offD_d.as<int64_t>(), c->lr_Pt.as<double2>(),
+                   cfg.pair_table};
     GF_CU(gf::launch_point_lr(p, lr, grid, cfg.smem, c->stream));
     return GF_OK;
   }
@@ -511,10 +514,17 @@ gf_status run_points(gf_ctx* c, int mode) {
       if (c->lowrank) {
         cfg.kind = 3;
         cfg.nbmax = c->bucket_nbmax[bucket];
-        cfg.smem = gf::point_lr_smem(cfg.nbmax, c->mmax, mode);
-        if (cfg.smem > (size_t)c->smem_optin - 1024)
+        const size_t lim = (size_t)c->smem_optin - 1024;
+        const size_t s0 = gf::point_lr_smem(cfg.nbmax, c->mmax, mode, 0);
+        const size_t s1 = gf::point_lr_smem(cfg.nbmax, c->mmax, mode, 1);
+        if (s0 > lim)
           return fail(c, GF_EINVAL, "N_b or m too large for the shared-memory tiles of the low-rank kernel");
-        cfg.grid = c->sm_count * std::max(1, gf::point_lr_blocks_per_sm(cfg.smem));
+        const int b0 = std::max(1, gf::point_lr_blocks_per_sm(s0));
+        const int b1 = s1 <= lim ? gf::point_lr_blocks_per_sm(s1) : 0;
+        // keep the item's pair table in shared memory when that costs no occupancy
+        cfg.pair_table = (b1 >= b0) ? 1 : 0;
+        cfg.smem = cfg.pair_table ? s1 : s0;
+        cfg.grid = c->sm_count * (cfg.pair_table ? b1 : b0);
       } else {
         st = choose_cfg(c, mode, bucket, c->bucket_nbmax[bucket], p, items_dev, s1 - s0, &cfg);
         if (st) return st;
@@ -730,7 +740,7 @@ gf_status newton_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_i
 }
 
 // Pole path: build H_ps(mu) per k, diagonalise, and run the epilogues of mode.
-gf_status pole_run(gf_ctx* c, int mode, bool gloc_kernel = true) {
+gf_status pole_run(gf_ctx* c, int mode, bool gloc_kernel = true, int warm = 0, int save_v = 0) {
   if (!c->have_H || !c->have_P || !c->have_poles)
     return fail(c, GF_ESTATE, "gf_set_hamiltonian, gf_set_projectors and gf_set_sigma_poles must "
                               "all be called before a pole-path call");
@@ -764,6 +774,14 @@ gf_status pole_run(gf_ctx* c, int mode, bool gloc_kernel = true) {
   p.wbout = c->wbout.as<double>();
   p.kHks = c->kHks.as<double>();
   p.kEps = c->kEps.as<double>();
+  p.warm = warm;
+  p.save_v = save_v;
+  if (warm || save_v) {
+    p.vstore = c->pole_vs.as<double2>();
+    p.estore = c->pole_es.as<double>();
+    p.voff = c->voff_d.as<int64_t>();
+    p.mu_prev = c->mu_prev.as<double>();
+  }
   p.status = c->status.as<int>();
   const size_t smem = gf::heev_smem(c->nps_max);
   const size_t limit = (size_t)c->smem_optin - 16384;  // static shared arrays of the kernel
@@ -805,10 +823,11 @@ gf_status pole_check(gf_ctx* c) {
   return GF_OK;
 }
 
-gf_status pole_occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+gf_status pole_occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn_out,
+                               int warm = 0, int save_v = 0) {
   gf_status st = upload_mu(c, mu);
   if (st) return st;
-  st = pole_run(c, gf::kOcc);
+  st = pole_run(c, gf::kOcc, true, warm, save_v);
   if (st) return st;
   GF_CU(gf::launch_sys_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys,
                               c->kN.as<double>(), c->kdN.as<double>(), c->sysout.as<double>(),
@@ -1078,7 +1097,7 @@ gf_status gf_destroy(gf_ctx* c) {
                     &c->pole_ws, &c->lr_eps, &c->lr_U, &c->lr_Pt, &c->lr_T, &c->lr_ws,
                     &c->eimp, &c->eimp_part, &c->gl_in, &c->delta, &c->wraw, &c->vdc,
                     &c->wbout, &c->kHks, &c->kEps, &c->eps_grid, &c->dos, &c->pdos, &c->pdos_off,
-                    &c->pole_part};
+                    &c->pole_part, &c->pole_vs, &c->pole_es, &c->voff_d, &c->mu_prev};
   for (DevBuf* b : bufs) release(*b);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->occ_exec) cudaGraphExecDestroy(c->occ_exec);
@@ -1359,8 +1378,8 @@ gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* po
     offV += (int64_t)n_poles[s] * c->sinfo[s].m;
   }
   if (offp > 0 && (!poles || !v)) return fail(c, GF_EINVAL, "poles_ptr or v_ptr is NULL");
-  std::vector<int64_t> eoff(c->n_k), phioff(c->n_k);
-  int64_t te = 0, tphi = 0;
+  std::vector<int64_t> eoff(c->n_k), phioff(c->n_k), voff(c->n_k);
+  int64_t te = 0, tphi = 0, tv = 0;
   int nps = 1;
   for (int k = 0; k < c->n_k; ++k) {
     const int s = c->ksys[k];
@@ -1370,8 +1389,10 @@ gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* po
     nps = std::max(nps, n);
     eoff[k] = te;
     phioff[k] = tphi;
+    voff[k] = tv;
     te += n;
     tphi += (int64_t)c->sinfo[s].m * n;
+    tv += (int64_t)n * n;
   }
   std::vector<double> hp(std::max<int64_t>(offp, 1));
   if (offp > 0) {
@@ -1408,6 +1429,11 @@ gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* po
                         c->stream));
   GF_CU(cudaMemcpyAsync(c->phioff_d.p, phioff.data(), sizeof(int64_t) * c->n_k,
                         cudaMemcpyHostToDevice, c->stream));
+  GF_CU(ensure(c->voff_d, sizeof(int64_t) * c->n_k));
+  GF_CU(cudaMemcpyAsync(c->voff_d.p, voff.data(), sizeof(int64_t) * c->n_k, cudaMemcpyHostToDevice,
+                        c->stream));
+  c->pole_v_elems = tv;
+  c->pole_e_elems = te;
   GF_CU(cudaStreamSynchronize(c->stream));
   c->pinfo = pinfo;
   c->nps_max = nps;
@@ -1428,9 +1454,22 @@ gf_status gf_pole_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
   reset_stats(c);
+  // every evaluation after the first starts Jacobi from the previous eigenpairs
+  GF_CU(ensure(c->pole_vs, sizeof(double2) * std::max<int64_t>(c->pole_v_elems, 1)));
+  GF_CU(ensure(c->pole_es, sizeof(double) * std::max<int64_t>(c->pole_e_elems, 1)));
+  GF_CU(ensure(c->mu_prev, sizeof(double) * c->n_sys));
+  int evals = 0;
   return newton_mu(c, n_target, tol, max_iter, mu_inout, iters_out,
-                   [c](const double* mu, double* n, double* dn) {
-                     return pole_occupation_impl(c, mu, n, dn);
+                   [c, &evals](const double* mu, double* n, double* dn) {
+                     const int warm = evals > 0 ? 1 : 0;
+                     gf_status st2 = pole_occupation_impl(c, mu, n, dn, warm, 1);
+                     if (st2) return st2;
+                     ++evals;
+                     // the stored eigenpairs now belong to this mu
+                     cudaError_t e = cudaMemcpy(c->mu_prev.p, mu, sizeof(double) * c->n_sys,
+                                                cudaMemcpyHostToDevice);
+                     if (e != cudaSuccess) return fail(c, GF_ECUDA, cudaGetErrorString(e));
+                     return GF_OK;
                    });
 }
 

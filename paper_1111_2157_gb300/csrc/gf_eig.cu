@@ -270,32 +270,75 @@ __global__ void __launch_bounds__(kEigThreads) k_pole_eig(const PoleParams p) {
     const double2* P = p.P + ki.offP;
     const double2* Sinf = p.Sinf + si.offSinf;
     const double2* Vp = p.Vp + pi.offV;
-    // band block H + P^+ Sigma_inf P
-    for (int e = tid; e < nb * nb; e += kEigThreads) {
-      const int i = e / nb, j = e - (e / nb) * nb;
-      double2 acc = H[i * nb + j];
-      for (int a = 0; a < m; ++a) {
-        double2 t = make_double2(0.0, 0.0);
-        for (int b = 0; b < m; ++b) cmac(t, Sinf[a * m + b], P[b * nb + j]);
-        cmac_ca(acc, P[a * nb + i], t);
+    double2* Vs = p.vstore ? p.vstore + p.voff[k] : nullptr;  // eigenvectors kept between calls
+    double* Es = p.estore ? p.estore + p.eoff[k] : nullptr;
+    if (p.warm) {
+      // warm start from the eigenpairs (E', V') at mu' = mu_prev: H_ps(mu) = H_ps(mu') +
+      // (mu - mu') Pi_p, so V'^+ H_ps(mu) V' = diag(E') + (mu - mu') V_p'^+ V_p' with V_p'
+      // the pole rows of V'; Jacobi then only removes what the shift of mu added
+      const double dmu = mu - p.mu_prev[ki.sys];
+      for (int e = tid; e < n * n; e += kEigThreads) {
+        const int l = e / n, l2 = e - (e / n) * n;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int i = nb; i < n; ++i) cmac_ca(acc, Vs[i * n + l], Vs[i * n + l2]);
+        acc.x *= dmu;
+        acc.y *= dmu;
+        if (l == l2) acc.x += Es[l];
+        A[l * ld + l2] = acc;
       }
-      A[i * ld + j] = acc;
-    }
-    // pole rows/columns W_i = V_i P and the pole diagonal p_i + mu
-    for (int e = tid; e < npl * nb; e += kEigThreads) {
-      const int i = e / nb, b = e - (e / nb) * nb;
-      double2 w = make_double2(0.0, 0.0);
-      for (int a = 0; a < m; ++a) cmac(w, Vp[i * m + a], P[a * nb + b]);
-      A[(nb + i) * ld + b] = w;
-      A[b * ld + nb + i] = make_double2(w.x, -w.y);
-    }
-    for (int e = tid; e < npl * npl; e += kEigThreads) {
-      const int i = e / npl, j = e - (e / npl) * npl;
-      A[(nb + i) * ld + nb + j] = make_double2(i == j ? p.poles[pi.offp + i] + mu : 0.0, 0.0);
+    } else {
+      // band block H + P^+ Sigma_inf P
+      for (int e = tid; e < nb * nb; e += kEigThreads) {
+        const int i = e / nb, j = e - (e / nb) * nb;
+        double2 acc = H[i * nb + j];
+        for (int a = 0; a < m; ++a) {
+          double2 t = make_double2(0.0, 0.0);
+          for (int b = 0; b < m; ++b) cmac(t, Sinf[a * m + b], P[b * nb + j]);
+          cmac_ca(acc, P[a * nb + i], t);
+        }
+        A[i * ld + j] = acc;
+      }
+      // pole rows/columns W_i = V_i P and the pole diagonal p_i + mu
+      for (int e = tid; e < npl * nb; e += kEigThreads) {
+        const int i = e / nb, b = e - (e / nb) * nb;
+        double2 w = make_double2(0.0, 0.0);
+        for (int a = 0; a < m; ++a) cmac(w, Vp[i * m + a], P[a * nb + b]);
+        A[(nb + i) * ld + b] = w;
+        A[b * ld + nb + i] = make_double2(w.x, -w.y);
+      }
+      for (int e = tid; e < npl * npl; e += kEigThreads) {
+        const int i = e / npl, j = e - (e / npl) * npl;
+        A[(nb + i) * ld + nb + j] = make_double2(i == j ? p.poles[pi.offp + i] + mu : 0.0, 0.0);
+      }
     }
     __syncthreads();
     const int sw = jacobi_heev(A, V, n, ld, p.max_sweeps, rot, ph, red);
     if (sw < 0 && tid == 0) atomicOr(p.status, 2);
+    if (p.warm) {
+      // eigenvectors of H_ps(mu) = V' R: the product goes to A's storage (its
+      // diagonal, the eigenvalues, is kept in s_x first) and A, V swap roles
+      for (int l = tid; l < n; l += kEigThreads) s_x[l] = A[l * ld + l].x;
+      __syncthreads();
+      for (int e = tid; e < n * n; e += kEigThreads) {
+        const int i = e / n, l = e - (e / n) * n;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int q = 0; q < n; ++q) cmac(acc, Vs[i * n + q], V[q * ld + l]);
+        A[i * ld + l] = acc;
+      }
+      __syncthreads();
+      double2* t = A;
+      A = V;
+      V = t;
+      for (int l = tid; l < n; l += kEigThreads) A[l * ld + l] = make_double2(s_x[l], 0.0);
+      __syncthreads();
+    }
+    if (p.save_v) {
+      for (int e = tid; e < n * n; e += kEigThreads) {
+        const int i = e / n, l = e - (e / n) * n;
+        Vs[e] = V[i * ld + l];
+      }
+      for (int l = tid; l < n; l += kEigThreads) Es[l] = A[l * ld + l].x;
+    }
     // per eigenpair: x_l = E_l - mu, n_F(x_l), cosh(beta x_l / 2)
     for (int l = tid; l < n; l += kEigThreads) {
       const double x = A[l * ld + l].x - mu;

@@ -144,3 +144,16 @@ def test_pole_spectral_and_energy():
         h_ref, e_ref = pole_oracle.energy(s.H, s.P, s.sigma_inf, s.pole.p, s.pole.V, s.beta, mus[i])
         assert abs(hks[i] - h_ref) <= 1e-10 * max(1.0, abs(h_ref))
         assert abs(eps_sum[i] - e_ref) <= 1e-10 * max(1.0, abs(e_ref))
+
+
+def test_warm_started_mu_search_matches_a_cold_evaluation():
+    """pole_find_mu restarts Jacobi from the previous eigenpairs; a cold evaluation at its mu agrees."""
+    systems = _ragged_systems()
+    g = _pole_gf(systems)
+    targets = [s.n_target for s in systems]
+    mu, it = g.pole_find_mu(targets, mu0=0.0, tol=1e-11)
+    n_cold, _ = g.pole_occupation(mu)
+    assert np.max(np.abs(n_cold - np.array(targets))) <= 1e-10
+    for i, s in enumerate(systems):
+        ref = pole_oracle.density(s.H, s.P, s.sigma_inf, s.pole.p, s.pole.V, s.beta, mu[i])
+        assert abs(ref["N"] - targets[i]) <= 1e-10
