@@ -174,86 +174,71 @@ __device__ __forceinline__ void renorm_fast(float& h, float& l) {
   h = s;
 }
 
-// a' = a - l u for one entry (i, c) of a row i != j during the elimination of
-// column j.  Column j holds zeros by then and urow[j] = r, so its entries become
-// -l r with no special case; row j is written in the row-preparation phase.
 __device__ __forceinline__ void elim_entry(float4* A, int ld, const float4* col, const float4* urow,
-                                           int i, int c) {
+                                           int i, int c, int j) {
   float4* a = &A[i * ld + c];
-  const cf l = cneg(ld4(col[i]));
-  cf v = ld4(*a);
-  cacc(v, l, ld4(urow[c]));
-  renorm_fast(v.rh, v.rl);
-  renorm_fast(v.ih, v.il);
-  *a = st4(v);
+  const float4 u4 = urow[c];
+  if (i == j) {
+    *a = u4;
+  } else {
+    const cf l = cneg(ld4(col[i]));
+    const float4 a0 = *a;
+    cf v = (c == j) ? czero() : ld4(a0);
+    cacc(v, l, ld4(u4));
+    renorm_fast(v.rh, v.rl);
+    renorm_fast(v.ih, v.il);
+    *a = st4(v);
+  }
 }
 
 // In-place Gauss-Jordan inversion in FP32-pair arithmetic with one pivot of
 // lookahead; the same pivoting and bookkeeping as the FP64 kernel (pivot key
-// from the head words).  Step j: (b) scaled pivot row to urow and to row j, old
-// row j to row p, column j to col and then zeroed; (c) warp 0 eliminates column
-// j+1 first, then searches it for the next pivot and forms its reciprocal, while
-// warps 1..7 eliminate every other column.  Rows other than j only: the update
-// has no branch.  Two barriers per pivot; the pivot search is off the critical path.
+// from the head words).  Step j: (b) scaled pivot row to urow, old row j to row
+// p, column j to col; (c) warp 0 eliminates column j+1 first, then searches it
+// for the next pivot and forms its reciprocal, while warps 1..7 eliminate every
+// other column.  Two barriers per pivot; the pivot search is off the critical path.
 __device__ void gauss_jordan_df64(float4* A, int N, int ld, float4* col, float4* urow, int* piv,
                                   int* idx, int* status) {
   __shared__ int s_p[2];
   __shared__ float4 s_r[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (warp == 0) pivot_warp(A, N, ld, 0, lane, &s_p[0], &s_r[0], piv, status);
   __syncthreads();
   for (int j = 0; j < N; ++j) {
     const int bf = j & 1;
     const int pr = s_p[bf];
     const cf r = ld4(s_r[bf]);
-    // (b) one thread per column c touches A[pr][c] and A[j][c] only; one thread per
-    // row i (i != pr, j) touches A[i][j] only: no two threads share an element
     for (int c = tid; c < N; c += kThreads) {
       const cf vp = ld4(A[pr * ld + c]);
-      float4 u;
       if (c == j) {
-        u = st4(r);
+        urow[c] = st4(r);
       } else {
-        cf t = czero();
-        cacc(t, vp, r);
-        cnorm(t);
-        u = st4(t);
+        cf u = czero();
+        cacc(u, vp, r);
+        cnorm(u);
+        urow[c] = st4(u);
       }
-      urow[c] = u;
-      const float4 oldj = A[j * ld + c];
-      if (c == j) {
-        col[pr] = oldj;             // post-swap column j of row pr
-        A[pr * ld + j] = zero4;     // column j is zero before the update
-      } else if (pr != j) {
-        A[pr * ld + c] = oldj;      // old row j moves to row pr
-      }
-      A[j * ld + c] = u;            // row j is final
+      if (pr != j) A[pr * ld + c] = A[j * ld + c];
     }
-    for (int i = tid; i < N; i += kThreads) {
-      if (i == pr || i == j) continue;
-      col[i] = A[i * ld + j];
-      A[i * ld + j] = zero4;
-    }
+    for (int i = tid; i < N; i += kThreads) col[i] = (i == pr) ? A[j * ld + j] : A[i * ld + j];
     __syncthreads();
     const int jn = j + 1;
     if (jn < N && warp == 0) {
-      for (int i = lane; i < N; i += 32)
-        if (i != j) elim_entry(A, ld, col, urow, i, jn);
+      for (int i = lane; i < N; i += 32) elim_entry(A, ld, col, urow, i, jn, j);
       __syncwarp();
       pivot_warp(A, N, ld, jn, lane, &s_p[bf ^ 1], &s_r[bf ^ 1], piv, status);
     } else {
-      // every (i, c) with i != j and c != jn, over warps 1..7 (all warps on the last step)
+      // every (i, c) with c != jn, over warps 1..7 (all warps on the last step)
       const int w0 = (jn < N) ? 32 : 0;
       const int nt = kThreads - w0, me = tid - w0;
       const int ncol = (jn < N) ? N - 1 : N;
-      const int total = (N - 1) * ncol;
-      int ii = me / ncol, cc = me - (me / ncol) * ncol;
+      const int total = N * ncol;
+      int i = me / ncol, cc = me - (me / ncol) * ncol;
       const int di = nt / ncol, dc = nt - (nt / ncol) * ncol;
       for (int e = me; e < total; e += nt) {
-        elim_entry(A, ld, col, urow, ii + (ii >= j ? 1 : 0), cc + (cc >= jn ? 1 : 0));
-        ii += di; cc += dc;
-        if (cc >= ncol) { cc -= ncol; ++ii; }
+        elim_entry(A, ld, col, urow, i, cc + (cc >= jn ? 1 : 0), j);
+        i += di; cc += dc;
+        if (cc >= ncol) { cc -= ncol; ++i; }
       }
     }
     __syncthreads();

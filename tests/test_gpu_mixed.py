@@ -91,3 +91,20 @@ def test_ce_like_full_size_sampled():
     ks = [7, 500]
     r = o.density(s.H[ks], s.P[ks], s.sigma, s.sigma_inf, s.beta, mu, weights=np.full(2, 1e-3))
     assert rel(rho[ks], r["rho"]) < 1e-9
+
+
+def test_nio_like_full_size_sampled():
+    """Full NiO-like size (N_k=4096, N_b=96, m=20, N_w=2048) in the launch configuration of
+    bench.py --workload nio_like: G_loc at four frequencies over all k, and rho_k at two k."""
+    s = synth.nio_like().systems[0]
+    mu = 0.1
+    g = make_gf([s], precision="mixed")
+    out = g.evaluate([mu], gloc=True, rho=True, occupation=False, n_corr=False)
+    gl = out["gloc"].cpu().numpy().reshape(s.n_iw, s.m, s.m)
+    o = oracle.get()
+    idx = [0, 1, 1000, 2047]
+    assert rel(gl[idx], o.local(s.H, s.P, s.sigma, s.beta, mu, n_idx=idx)) < 1e-9
+    ks = [11, 4000]
+    rho = out["rho"].cpu().numpy().reshape(s.nk, 96, 96)
+    r = o.density(s.H[ks], s.P[ks], s.sigma, s.sigma_inf, s.beta, mu, weights=np.full(2, 0.5))
+    assert rel(rho[ks], r["rho"]) < 1e-9

@@ -157,3 +157,15 @@ def test_warm_started_mu_search_matches_a_cold_evaluation():
     for i, s in enumerate(systems):
         ref = pole_oracle.density(s.H, s.P, s.sigma_inf, s.pole.p, s.pole.V, s.beta, mu[i])
         assert abs(ref["N"] - targets[i]) <= 1e-10
+
+
+def test_heev_reports_non_convergence_without_a_fault():
+    """One sweep cannot diagonalise a dense 40 x 40 matrix: GF_ENOTCONV, and the context stays usable."""
+    import torch
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((2, 40, 40)) + 1j * rng.standard_normal((2, 40, 40))
+    A = torch.as_tensor(0.5 * (X + np.conj(np.swapaxes(X, 1, 2))), device="cuda")
+    with pytest.raises(gfm.GFError, match="ENOTCONV"):
+        gfm.heev_batched(A, max_sweeps=1)
+    w, V = gfm.heev_batched(A)
+    assert np.max(np.abs(w.cpu().numpy()[0] - np.linalg.eigvalsh(A.cpu().numpy()[0]))) < 1e-11
