@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         objs = list(ex.map(compile_one, srcs))
     if force or not LIB.exists() or any(o.stat().st_mtime > LIB.stat().st_mtime for o in objs):
         tmp = LIB.with_name(LIB.name + f".{os.getpid()}.tmp")
-        cmd = [cc, *ARCH, "-shared", "--cudart", "static", *map(str, objs), "-o", str(tmp)]
+        cmd = [cc, *ARCH, "-shared", "--cudart", "static", *map(str, objs), "-ldl", "-o", str(tmp)]
         if verbose:
             print(" ".join(cmd))
         subprocess.run(cmd, check=True)

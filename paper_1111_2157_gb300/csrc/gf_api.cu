@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gf.h"
 #include "gf_internal.cuh"
 
@@ -44,6 +46,14 @@ void release(DevBuf& b) {
   b.p = nullptr;
   b.bytes = 0;
 }
+
+// NVTX range around a C-ABI call (visible in Nsight timelines; no cost without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct DeviceGuard {
   int prev = -1;
@@ -1109,6 +1119,7 @@ gf_status gf_destroy(gf_ctx* c) {
 }
 
 gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) {
+  NvtxRange nvtx_range_("gf_set_hamiltonian");
   if (!c) return GF_EINVAL;
   if (!h) return fail(c, GF_EINVAL, "h_ptr is NULL");
   DeviceGuard guard(c->device);
@@ -1143,6 +1154,7 @@ gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) {
 }
 
 gf_status gf_set_projectors(gf_ctx* c, const void* p) {
+  NvtxRange nvtx_range_("gf_set_projectors");
   if (!c) return GF_EINVAL;
   if (!p) return fail(c, GF_EINVAL, "p_ptr is NULL");
   DeviceGuard guard(c->device);
@@ -1158,6 +1170,7 @@ gf_status gf_set_projectors(gf_ctx* c, const void* p) {
 }
 
 gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) {
+  NvtxRange nvtx_range_("gf_set_sigma");
   if (!c) return GF_EINVAL;
   if (!sig || !sinf) return fail(c, GF_EINVAL, "sigma_iw_ptr or sigma_inf_ptr is NULL");
   DeviceGuard guard(c->device);
@@ -1174,6 +1187,7 @@ gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) {
 }
 
 gf_status gf_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+  NvtxRange nvtx_range_("gf_occupation");
   if (!c) return GF_EINVAL;
   if (!n_out) return fail(c, GF_EINVAL, "n_out is NULL");
   DeviceGuard guard(c->device);
@@ -1183,6 +1197,7 @@ gf_status gf_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_o
 
 gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_iter,
                      double* mu_inout, int32_t* iters_out) {
+  NvtxRange nvtx_range_("gf_find_mu");
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
   reset_stats(c);
@@ -1193,6 +1208,7 @@ gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_
 }
 
 gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) {
+  NvtxRange nvtx_range_("gf_density_matrix");
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
   reset_stats(c);
@@ -1226,6 +1242,7 @@ gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* 
 }
 
 gf_status gf_local(gf_ctx* c, const double* mu, void* gloc_out) {
+  NvtxRange nvtx_range_("gf_local");
   if (!c) return GF_EINVAL;
   if (!gloc_out) return fail(c, GF_EINVAL, "gloc_out_ptr is NULL");
   DeviceGuard guard(c->device);
@@ -1241,6 +1258,7 @@ gf_status gf_local(gf_ctx* c, const double* mu, void* gloc_out) {
 
 gf_status gf_evaluate(gf_ctx* c, const double* mu, void* gloc_out, void* rho_out, double* n_out,
                       double* dn_out, double* n_corr_out) {
+  NvtxRange nvtx_range_("gf_evaluate");
   if (!c) return GF_EINVAL;
   const int mode = (gloc_out ? gf::kGloc : 0) | ((rho_out || n_corr_out) ? gf::kRho : 0) |
                    ((n_out || dn_out) ? gf::kOcc : 0);
@@ -1299,6 +1317,7 @@ gf_status gf_evaluate(gf_ctx* c, const double* mu, void* gloc_out, void* rho_out
 
 gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const double* nbar,
                       void* sbar_out, double* mubar_out) {
+  NvtxRange nvtx_range_("gf_backward");
   if (!c) return GF_EINVAL;
   if (!sbar_out || !mubar_out) return fail(c, GF_EINVAL, "sigma_bar_out_ptr or mu_bar_out is NULL");
   DeviceGuard guard(c->device);
@@ -1362,6 +1381,7 @@ const char* gf_tuning_log(const gf_ctx* c) {
 
 gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* poles,
                              const void* v, const void* sinf) {
+  NvtxRange nvtx_range_("gf_set_sigma_poles");
   if (!c) return GF_EINVAL;
   if (!n_poles || !sinf) return fail(c, GF_EINVAL, "n_poles or sigma_inf_ptr is NULL");
   DeviceGuard guard(c->device);
@@ -1442,6 +1462,7 @@ gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* po
 }
 
 gf_status gf_pole_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+  NvtxRange nvtx_range_("gf_pole_occupation");
   if (!c) return GF_EINVAL;
   if (!n_out) return fail(c, GF_EINVAL, "n_out is NULL");
   DeviceGuard guard(c->device);
@@ -1451,6 +1472,7 @@ gf_status gf_pole_occupation(gf_ctx* c, const double* mu, double* n_out, double*
 
 gf_status gf_pole_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_iter,
                           double* mu_inout, int32_t* iters_out) {
+  NvtxRange nvtx_range_("gf_pole_find_mu");
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
   reset_stats(c);
@@ -1474,6 +1496,7 @@ gf_status gf_pole_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t
 }
 
 gf_status gf_pole_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) {
+  NvtxRange nvtx_range_("gf_pole_density_matrix");
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
   reset_stats(c);
@@ -1497,6 +1520,7 @@ gf_status gf_pole_density_matrix(gf_ctx* c, const double* mu, void* rho_out, dou
 }
 
 gf_status gf_pole_local(gf_ctx* c, const double* mu, void* gloc_out) {
+  NvtxRange nvtx_range_("gf_pole_local");
   if (!c) return GF_EINVAL;
   if (!gloc_out) return fail(c, GF_EINVAL, "gloc_out_ptr is NULL");
   DeviceGuard guard(c->device);
@@ -1511,6 +1535,7 @@ gf_status gf_pole_local(gf_ctx* c, const double* mu, void* gloc_out) {
 }
 
 gf_status gf_set_projectors_lowdin(gf_ctx* c, const void* w, void* p_out) {
+  NvtxRange nvtx_range_("gf_set_projectors_lowdin");
   if (!c) return GF_EINVAL;
   if (!w) return fail(c, GF_EINVAL, "w_ptr is NULL");
   if (c->mmax > 32) return fail(c, GF_EINVAL, "the projector orthonormalisation takes m <= 32");
@@ -1537,6 +1562,7 @@ gf_status gf_set_projectors_lowdin(gf_ctx* c, const void* w, void* p_out) {
 }
 
 gf_status gf_impurity_levels(gf_ctx* c, const double* v_dc, void* e_imp_out) {
+  NvtxRange nvtx_range_("gf_impurity_levels");
   if (!c) return GF_EINVAL;
   if (!e_imp_out) return fail(c, GF_EINVAL, "e_imp_out_ptr is NULL");
   if (!c->have_H || !c->have_P)
@@ -1565,6 +1591,7 @@ gf_status gf_impurity_levels(gf_ctx* c, const double* v_dc, void* e_imp_out) {
 
 gf_status gf_hybridization(gf_ctx* c, const double* mu, const void* gloc, const double* v_dc,
                            void* delta_out) {
+  NvtxRange nvtx_range_("gf_hybridization");
   if (!c) return GF_EINVAL;
   if (!gloc || !delta_out) return fail(c, GF_EINVAL, "gloc_ptr or delta_out_ptr is NULL");
   if (c->mmax > 32) return fail(c, GF_EINVAL, "the hybridization step takes m <= 32");
@@ -1606,6 +1633,7 @@ gf_status gf_double_counting(double U, double J, int32_t l, double n, double* u_
 
 gf_status gf_pole_spectral(gf_ctx* c, const double* mu, int32_t n_eps, const double* eps,
                            double eta, double* dos_out, double* pdos_out) {
+  NvtxRange nvtx_range_("gf_pole_spectral");
   if (!c) return GF_EINVAL;
   if (n_eps < 1 || !eps || !dos_out) return fail(c, GF_EINVAL, "n_eps >= 1, eps and dos_out required");
   if (!(eta > 0.0) || !std::isfinite(eta)) return fail(c, GF_EINVAL, "eta must be > 0");
@@ -1651,6 +1679,7 @@ gf_status gf_pole_spectral(gf_ctx* c, const double* mu, int32_t n_eps, const dou
 }
 
 gf_status gf_pole_energy(gf_ctx* c, const double* mu, double* h_ks_out, double* e_ps_out) {
+  NvtxRange nvtx_range_("gf_pole_energy");
   if (!c) return GF_EINVAL;
   if (!h_ks_out && !e_ps_out) return fail(c, GF_EINVAL, "h_ks_out and e_ps_out are both NULL");
   DeviceGuard guard(c->device);
@@ -1677,6 +1706,7 @@ gf_status gf_pole_energy(gf_ctx* c, const double* mu, double* h_ks_out, double* 
 
 gf_status gf_heev_batched(const void* a_dev, int32_t n_mat, int32_t n, int32_t max_sweeps,
                           double* w_dev, void* v_dev, void* stream) {
+  NvtxRange nvtx_range_("gf_heev_batched");
   if (n_mat < 0 || n < 1 || n > gf::heev_max_n() || max_sweeps < 1 ||
       (n_mat > 0 && (!a_dev || !w_dev || !v_dev))) {
     gf::set_global_error("gf_heev_batched: invalid arguments (1 <= n <= 256, max_sweeps >= 1, "
