@@ -82,3 +82,22 @@ def run_gpu(rank, world_size, port, out_path):
 def _to_host(r):
     g, n, dn = r
     return (None if g is None else g.cpu()), n, dn
+
+
+def run_dropout(rank, world_size, port, out_path):
+    """Rank 1 fails before its first evaluation; rank 0's all-reduce must end with an error
+    within the process-group timeout instead of waiting forever."""
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world_size, timeout=datetime.timedelta(seconds=5))
+    s = sharded_case()
+    k0, k1 = shard.partition_k(s.nb, world_size)[rank]
+    if rank == 1:
+        raise RuntimeError("rank 1 drops out")
+    lat = shard.ShardedLattice(oracle_slice_evaluator(oracle.get(), s, k0, k1))
+    try:
+        lat.evaluate([0.0], gloc=False)
+        outcome = "no error"
+    except Exception as e:  # the collective reports the lost peer
+        outcome = type(e).__name__
+    with open(out_path, "w") as f:
+        f.write(outcome)

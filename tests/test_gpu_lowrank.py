@@ -80,3 +80,13 @@ def test_rejects_mixed_and_graph():
         make_gf([s], precision="mixed", lowrank=True)
     with pytest.raises(GFError):
         make_gf([s], graph=True, lowrank=True)
+
+
+def test_tail_order_one_and_complex64_inputs():
+    s = synth.ce_like(nk=4, n_iw=24).systems[0]
+    check_system_set([s], [0.1], TOL, tail_order=1, lowrank=True)
+    # complex64 inputs: the oracle gets the same rounded values in complex128
+    c = lambda a: a.astype(np.complex64).astype(np.complex128)  # noqa: E731
+    rounded = synth.System(c(s.H), c(s.P), synth.PoleSigma(c(s.pole.sigma_inf), s.pole.p, s.pole.V),
+                           c(s.sigma), s.beta, s.n_target)
+    check_system_set([rounded], [0.1], TOL, input_dtype="c64", lowrank=True)

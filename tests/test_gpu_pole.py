@@ -169,3 +169,16 @@ def test_heev_reports_non_convergence_without_a_fault():
         gfm.heev_batched(A, max_sweeps=1)
     w, V = gfm.heev_batched(A)
     assert np.max(np.abs(w.cpu().numpy()[0] - np.linalg.eigvalsh(A.cpu().numpy()[0]))) < 1e-11
+
+
+def test_zero_poles_is_the_static_self_energy_limit():
+    """n_poles = 0: H_ps = H + P^+ Sigma_inf P, N = band Fermi sum of its eigenvalues."""
+    s = _ce_small(nk=3, n_iw=8)
+    g = make_gf([s])
+    g.set_sigma_poles([0], np.zeros(0), np.zeros(0, np.complex128), s.sigma_inf.reshape(-1))
+    mu = 0.5
+    n, dn = g.pole_occupation(mu)
+    m = s.m
+    ref = pole_oracle.density(s.H, s.P, s.sigma_inf, np.zeros(0), np.zeros((0, m)), s.beta, mu)
+    assert abs(n[0] - ref["N"]) <= 1e-10 * ref["N"]
+    assert abs(dn[0] - ref["dN_dmu"]) <= 1e-10 * ref["dN_dmu"]

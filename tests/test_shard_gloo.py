@@ -72,3 +72,22 @@ def test_two_rank_sharding_over_the_cuda_path():
     assert abs(r["N"][0] - full["N"]) <= 1e-12 * full["N"]
     gl = o.local(s.H, s.P, s.sigma, s.beta, mu, weights=s.weights)
     assert np.max(np.abs(r["gloc"].reshape(gl.shape) - gl)) <= 1e-12 * np.max(np.abs(gl))
+
+
+def test_a_rank_that_drops_out_is_reported_not_waited_for(tmp_path):
+    import multiprocessing as mp
+    out = tmp_path / "rank0.txt"
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=shard_worker.run_dropout, args=(r, 2, port, str(out))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=60)
+    alive = [p for p in procs if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank was still waiting after 60 s"
+    assert procs[1].exitcode != 0
+    # rank 0 saw its collective fail (it neither hung nor got a result)
+    assert out.exists() and out.read_text() != "no error"
