@@ -640,10 +640,18 @@ gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn
     if (st) return st;
     return finish_occupation(c, c->stream, n_out, dn_out);
   }
-  // graph mode: E_inf outside the graph (inputs may have changed), then replay
+  // graph mode: E_inf and the low-rank eigenbasis outside the graph (inputs may
+  // have changed), then replay
   GF_CU(cudaStreamSynchronize(c->stream));
   st = ensure_einf(c);
   if (st) return st;
+  if (c->lowrank && c->lr_dirty) {
+    GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
+    st = ensure_lr(c);
+    if (st) return st;
+    st = sync_and_check(c);
+    if (st) return st;
+  }
   for (int s2 = 0; s2 < c->n_sys; ++s2) c->hp_mu()[s2] = mu[s2];
   if (!c->occ_exec) {
     GF_CU(cudaStreamSynchronize(c->stream));
@@ -897,10 +905,6 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   if (c->lowrank && c->precision != GF_PREC_FP64) {
     delete c;
     return bad("GF_FLAG_LOWRANK runs in FP64 only");
-  }
-  if (c->lowrank && c->use_graph) {
-    delete c;
-    return bad("GF_FLAG_LOWRANK and GF_FLAG_GRAPH cannot be combined");
   }
   c->nb.resize(c->n_k);
   c->ksys.resize(c->n_k);
