@@ -820,7 +820,7 @@ gf_status pole_run(gf_ctx* c, int mode, bool gloc_kernel = true, int warm = 0, i
   GF_CU(gf::launch_pole_eig(p, grid, p.in_smem ? smem : 0, c->stream));
   c->last_launches += 1;
   if ((mode & gf::kGloc) && gloc_kernel) {
-    const int ns = gf::pole_gloc_splits(c->n_sys, c->n_iw, c->sm_count);
+    const int ns = gf::pole_gloc_splits(c->n_sys, c->n_iw, c->sm_count, c->mmax);
     GF_CU(ensure(c->pole_part, sizeof(double2) * (size_t)ns * c->totSig));
     GF_CU(gf::launch_pole_gloc(p, c->n_sys, c->mmax, ns, c->pole_part.as<double2>(), c->totSig,
                                c->stream));

@@ -442,19 +442,20 @@ __global__ void __launch_bounds__(kEigThreads) k_pole_eig(const PoleParams p) {
 }
 
 // G_loc(i w_n) = sum_k w_k sum_l phi_l phi_l^+ / (i w_n + mu - E_l) for one
-// system and kF consecutive frequencies per CTA; each thread owns QP (a, b)
-// pairs.  phi and E are staged in shared memory kCh eigenpairs at a time.  The
-// sum runs over k, then l, in increasing order: the result is reproducible.
-constexpr int kF = 8;
+// system and F consecutive frequencies per CTA.  With t = phi_a conj(phi_b)
+// and g = w_k / (i w + mu - E) = gr + i gi: G_ab = Xr + i Xi and
+// G_ba = conj(Xr) + i conj(Xi) with Xr = sum t gr, Xi = sum t gi, so each
+// thread sums QP pairs a <= b.  phi and E are staged in shared memory kCh
+// eigenpairs at a time; the sums run over k, then l, in increasing order.
 constexpr int kCh = 32;
 
-template <int QP>
+template <int QP, int F>
 __global__ void __launch_bounds__(kEigThreads)
     k_pole_gloc(const PoleParams p, int blocks_per_sys, int n_split, double2* part, int64_t tot) {
   __shared__ double2 s_phi[32 * kCh];  // m <= 32
-  __shared__ double2 s_g[kF * kCh];
+  __shared__ double2 s_g[F * kCh];
   const int s = blockIdx.x / blocks_per_sys;
-  const int f0 = (blockIdx.x - s * blocks_per_sys) * kF;
+  const int f0 = (blockIdx.x - s * blocks_per_sys) * F;
   const int split = blockIdx.y;
   const SInfo si = p.sinfo[s];
   // k-points [ka, kb) of this split of the system
@@ -462,13 +463,26 @@ __global__ void __launch_bounds__(kEigThreads)
   const int ka = si.k0 + (int)((int64_t)nks * split / n_split);
   const int kb = si.k0 + (int)((int64_t)nks * (split + 1) / n_split);
   const int m = si.m;
+  const int npairs = m * (m + 1) / 2;
   const double mu = p.mu[s];
   const int tid = threadIdx.x;
-  double2 acc[QP][kF];
+  int pa[QP], pb[QP];
+#pragma unroll
+  for (int q = 0; q < QP; ++q) {
+    int rem = tid + q * kEigThreads, a = 0;
+    if (rem >= npairs) rem = 0;
+    while (rem >= m - a) { rem -= m - a; ++a; }
+    pa[q] = a;
+    pb[q] = a + rem;
+  }
+  double2 xr[QP][F], xi[QP][F];
 #pragma unroll
   for (int q = 0; q < QP; ++q)
 #pragma unroll
-    for (int f = 0; f < kF; ++f) acc[q][f] = make_double2(0.0, 0.0);
+    for (int f = 0; f < F; ++f) {
+      xr[q][f] = make_double2(0.0, 0.0);
+      xi[q][f] = make_double2(0.0, 0.0);
+    }
   for (int k = ka; k < kb; ++k) {
     const int n = p.kinfo[k].nb + p.pinfo[s].np;
     const double wk = p.kinfo[k].w;
@@ -481,7 +495,7 @@ __global__ void __launch_bounds__(kEigThreads)
         const int a = e / cl, l = e - (e / cl) * cl;
         s_phi[a * kCh + l] = phi[a * n + l0 + l];
       }
-      for (int e = tid; e < kF * cl; e += kEigThreads) {
+      for (int e = tid; e < F * cl; e += kEigThreads) {
         const int f = e / cl, l = e - (e / cl) * cl;
         const int nn = f0 + f;
         const double wn = (2.0 * nn + 1.0) * 3.14159265358979323846 / si.beta;
@@ -493,26 +507,34 @@ __global__ void __launch_bounds__(kEigThreads)
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < QP; ++q) {
-        const int ab = tid + q * kEigThreads;
-        if (ab >= m * m) continue;
-        const int a = ab / m, b = ab - (ab / m) * m;
+        if (tid + q * kEigThreads >= npairs) continue;
+        const int a = pa[q], b = pb[q];
         for (int l = 0; l < cl; ++l) {
           double2 t = make_double2(0.0, 0.0);
           cmac_cb(t, s_phi[a * kCh + l], s_phi[b * kCh + l]);
 #pragma unroll
-          for (int f = 0; f < kF; ++f) cmac(acc[q][f], t, s_g[f * kCh + l]);
+          for (int f = 0; f < F; ++f) {
+            const double2 g = s_g[f * kCh + l];
+            xr[q][f].x = fma(t.x, g.x, xr[q][f].x);
+            xr[q][f].y = fma(t.y, g.x, xr[q][f].y);
+            xi[q][f].x = fma(t.x, g.y, xi[q][f].x);
+            xi[q][f].y = fma(t.y, g.y, xi[q][f].y);
+          }
         }
       }
     }
   }
 #pragma unroll
   for (int q = 0; q < QP; ++q) {
-    const int ab = tid + q * kEigThreads;
-    if (ab >= m * m) continue;
+    if (tid + q * kEigThreads >= npairs) continue;
+    const int a = pa[q], b = pb[q];
 #pragma unroll
-    for (int f = 0; f < kF; ++f) {
+    for (int f = 0; f < F; ++f) {
       const int nn = f0 + f;
-      if (nn < p.n_iw) part[(int64_t)split * tot + si.offSig + (int64_t)nn * m * m + ab] = acc[q][f];
+      if (nn >= p.n_iw) continue;
+      double2* out = part + (int64_t)split * tot + si.offSig + (int64_t)nn * m * m;
+      out[a * m + b] = make_double2(xr[q][f].x - xi[q][f].y, xr[q][f].y + xi[q][f].x);
+      out[b * m + a] = make_double2(xr[q][f].x + xi[q][f].y, xi[q][f].x - xr[q][f].y);
     }
   }
 }
@@ -731,19 +753,24 @@ cudaError_t launch_pole_eig(const PoleParams& p, int grid, size_t smem, cudaStre
   return cudaGetLastError();
 }
 
-int pole_gloc_splits(int n_sys, int n_iw, int sm_count) {
-  const int blocks = n_sys * ((n_iw + kF - 1) / kF);
+// frequencies per CTA of k_pole_gloc: 8 with one pair per thread, else 4
+int pole_gloc_f(int mmax) { return mmax * (mmax + 1) / 2 <= kEigThreads ? 8 : 4; }
+
+int pole_gloc_splits(int n_sys, int n_iw, int sm_count, int mmax) {
+  const int F = pole_gloc_f(mmax);
+  const int blocks = n_sys * ((n_iw + F - 1) / F);
   return std::max(1, std::min(64, (2 * sm_count + blocks - 1) / blocks));
 }
 
 cudaError_t launch_pole_gloc(const PoleParams& p, int n_sys, int mmax, int n_split, double2* part,
                              int64_t tot, cudaStream_t s) {
-  const int bps = (p.n_iw + kF - 1) / kF;
+  const int F = pole_gloc_f(mmax);
+  const int bps = (p.n_iw + F - 1) / F;
   const dim3 grid(n_sys * bps, n_split);
-  const int qp = (mmax * mmax + kEigThreads - 1) / kEigThreads;
-  if (qp <= 1) k_pole_gloc<1><<<grid, kEigThreads, 0, s>>>(p, bps, n_split, part, tot);
-  else if (qp <= 2) k_pole_gloc<2><<<grid, kEigThreads, 0, s>>>(p, bps, n_split, part, tot);
-  else k_pole_gloc<4><<<grid, kEigThreads, 0, s>>>(p, bps, n_split, part, tot);
+  const int qp = (mmax * (mmax + 1) / 2 + kEigThreads - 1) / kEigThreads;  // 1..3 for m <= 32
+  if (qp <= 1) k_pole_gloc<1, 8><<<grid, kEigThreads, 0, s>>>(p, bps, n_split, part, tot);
+  else if (qp <= 2) k_pole_gloc<2, 4><<<grid, kEigThreads, 0, s>>>(p, bps, n_split, part, tot);
+  else k_pole_gloc<3, 4><<<grid, kEigThreads, 0, s>>>(p, bps, n_split, part, tot);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_split_reduce<<<std::min<int64_t>(4096, (tot + 255) / 256), 256, 0, s>>>(part, n_split, tot, p.gloc);

@@ -190,7 +190,7 @@ cudaError_t launch_heev_batched(const double2* A, int n_mat, int n, int max_swee
 cudaError_t launch_pole_eig(const PoleParams& p, int grid, size_t smem, cudaStream_t s);
 // G_loc from the eigenpairs, k split n_split ways into part [n_split][tot] and
 // summed in split order into p.gloc.
-int pole_gloc_splits(int n_sys, int n_iw, int sm_count);
+int pole_gloc_splits(int n_sys, int n_iw, int sm_count, int mmax);
 cudaError_t launch_pole_gloc(const PoleParams& p, int n_sys, int mmax, int n_split, double2* part,
                              int64_t tot, cudaStream_t s);
 cudaError_t launch_pole_dos(const PoleParams& p, int n_sys, const double* eps_grid, int n_eps,

@@ -102,3 +102,23 @@ def test_graph_replay_of_the_low_rank_mu_search():
     r = oracle.get().density(shifted[0].H, shifted[0].P, shifted[0].sigma, shifted[0].sigma_inf,
                              shifted[0].beta, 0.0, want_rho=False)
     assert abs(b[0][0] - r["N"]) < 1e-10 * r["N"]
+
+
+def test_ce_like_full_size_sampled():
+    """Full Ce-like size in the low-rank mode: G_loc at four frequencies over all k and rho_k at
+    two k against the oracle; N against the direct GPU path (itself checked against the oracle)."""
+    s = synth.ce_like().systems[0]
+    mu = 0.15
+    g = make_gf([s], lowrank=True)
+    out = g.evaluate([mu], gloc=True, rho=True, occupation=True, n_corr=False)
+    gl = out["gloc"].cpu().numpy().reshape(s.n_iw, s.m, s.m)
+    o = oracle.get()
+    idx = [0, 3, 511, 1023]
+    assert rel(gl[idx], o.local(s.H, s.P, s.sigma, s.beta, mu, n_idx=idx)) < 1e-10
+    ks = [7, 500]
+    rho = out["rho"].cpu().numpy().reshape(s.nk, 40, 40)
+    r = o.density(s.H[ks], s.P[ks], s.sigma, s.sigma_inf, s.beta, mu, weights=np.full(2, 0.5))
+    assert rel(rho[ks], r["rho"]) < 1e-10
+    gd = make_gf([s])
+    nd, _ = gd.occupation([mu])
+    assert abs(out["N"][0] - nd[0]) < 1e-12 * nd[0]

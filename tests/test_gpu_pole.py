@@ -182,3 +182,20 @@ def test_zero_poles_is_the_static_self_energy_limit():
     ref = pole_oracle.density(s.H, s.P, s.sigma_inf, np.zeros(0), np.zeros((0, m)), s.beta, mu)
     assert abs(n[0] - ref["N"]) <= 1e-10 * ref["N"]
     assert abs(dn[0] - ref["dN_dmu"]) <= 1e-10 * ref["dN_dmu"]
+
+
+def test_ce_like_full_size():
+    """Full Ce-like size (N_k=1000, 28 poles, matrices of 68): N, dN/dmu, n_corr against the pole
+    oracle over every k, G_loc at four frequencies against the Matsubara oracle."""
+    s = synth.ce_like().systems[0]
+    g = _pole_gf([s])
+    mu = 0.9
+    n, dn = g.pole_occupation(mu)
+    _, nc = g.pole_density_matrix(mu, want_rho=False)
+    gl = g.pole_local(mu).cpu().numpy().reshape(s.n_iw, s.m, s.m)
+    ref = pole_oracle.density(s.H, s.P, s.sigma_inf, s.pole.p, s.pole.V, s.beta, mu)
+    assert abs(n[0] - ref["N"]) <= 1e-10 * ref["N"]
+    assert abs(dn[0] - ref["dN_dmu"]) <= 1e-10 * ref["dN_dmu"]
+    assert abs(nc[0] - ref["n_corr"]) <= 1e-10 * ref["n_corr"]
+    idx = [0, 5, 700, 1023]
+    assert rel(gl[idx], oracle.get().local(s.H, s.P, s.sigma, s.beta, mu, n_idx=idx)) <= 1e-10
