@@ -270,8 +270,9 @@ def run_workload(args):
     o.set_threads(cpu_cores())
     out = {"workload": args.workload}
     if args.workload == "nio_like":
-        s = synth.nio_like().systems[0]
-        out["config"] = "N_k=4096, N_b=96, m=20 (2 atoms x 5 d x 2 spin, AFM Sigma), N_w=2048, beta=40, U=8"
+        s = synth.nio_like(nk=args.nk or 4096, n_iw=args.n_iw or 2048).systems[0]
+        out["config"] = (f"N_k={s.nk}, N_b=96, m=20 (2 atoms x 5 d x 2 spin, AFM Sigma), N_w={s.n_iw}, "
+                         "beta=40, U=8")
         gm = _context(gf, [s], "mixed", graph=True)
         (mu, it), t_mu = _sync_time(lambda: gm.find_mu([s.n_target], 0.0, tol=1e-10))
         n_pass = gm.stats()
@@ -286,7 +287,7 @@ def run_workload(args):
         out["N_rel_err_mixed_vs_fp64_gpu"] = abs(ev["N"][0] - ev64["N"][0]) / ev64["N"][0]
         gl_m, gl_d = ev["gloc"], ev64["gloc"]
         out["G_loc_rel_err_mixed_vs_fp64_gpu"] = float((gl_m - gl_d).abs().max() / gl_d.abs().max())
-        idx = [0, 1, 1000, 2047]
+        idx = [0, 1, s.n_iw // 2, s.n_iw - 1]
         glo = o.local(s.H, s.P, s.sigma, s.beta, float(mu[0]), n_idx=idx)
         glm = gl_m.cpu().numpy().reshape(s.n_iw, 20, 20)[idx]
         gld = gl_d.cpu().numpy().reshape(s.n_iw, 20, 20)[idx]
@@ -333,6 +334,21 @@ def run_workload(args):
                          "graph_points_per_s": pts_g / t_g, "kernel_choice": log}
         out.update(res)
         out["mixed_speedup_one_launch"] = res["fp64"]["one_launch_s"] / res["mixed"]["one_launch_s"]
+        # the same passes with the low-rank algorithm (one launch per window bucket, graph replay)
+        gl = _context(gf, systems, "fp64", lowrank=True)
+        gl.occupation(mus)
+        _, t_one = _sync_time(lambda: gl.occupation(mus))
+        pts = gl.stats()["points"]
+        gl.close()
+        gg = _context(gf, systems, "fp64", graph=True, lowrank=True)
+        targets = [sy.n_target for sy in systems]
+        (mu_g, it_g), t_g = _sync_time(lambda: gg.find_mu(targets, 0.0, tol=1e-10))
+        pts_g = gg.stats()["points"]
+        gg.close()
+        out["lowrank"] = {"one_launch_s": t_one, "one_launch_points_per_s": pts / t_one,
+                          "speedup_vs_fp64_direct": res["fp64"]["one_launch_s"] / t_one,
+                          "graph_find_mu_s": t_g, "graph_find_mu_evaluations": it_g,
+                          "graph_points_per_s": pts_g / t_g}
     elif args.workload == "adjoint":
         from paper_1111_2157_gb300.autograd import lattice_green, newton_mu
         s = synth.adjoint_case().systems[0]
