@@ -190,3 +190,20 @@ def test_evaluate_fused_pass():
     assert abs(only_n["N"][0] - r["N"]) < TOL * r["N"]
     st = g.stats()
     assert st["points"] == s.nk * s.n_iw and st["kernel_ms"] > 0 and st["flops"] > 0
+
+
+@pytest.mark.parametrize("beta", [0.5, 400.0])
+def test_extreme_temperatures(beta):
+    """beta = 0.5 (hot: the tail terms dominate) and beta = 400 (cold: w_0 = 0.008 eV)."""
+    s = synth.random_system(41, 4, 10, 3, 96, beta)
+    _check_system_set([s], [0.2])
+
+
+def test_mu_search_iteration_cap_reports_non_convergence():
+    from paper_1111_2157_gb300.gf import GFError
+    s = synth.random_system(42, 3, 8, 3, 32, 10.0)
+    g = make_gf([s])
+    with pytest.raises(GFError, match="ENOTCONV"):
+        g.find_mu([s.n_target], mu0=3.0, tol=1e-14, max_iter=1)
+    mu, it = g.find_mu([s.n_target], mu0=3.0, tol=1e-10)  # the context is still usable
+    assert it > 1
