@@ -50,8 +50,8 @@ typedef enum {
     GF_ENOMEM = 2,     /* device or host allocation failed                         */
     GF_ECUDA = 3,      /* a CUDA runtime call failed (message in gf_last_error)    */
     GF_ESINGULAR = 4,  /* a zero or non-finite pivot in some (k, i w_n) inverse    */
-    GF_ENOTCONV = 5,   /* the mu search did not reach tol within max_iter          */
-    GF_ETIMEOUT = 6,   /* reserved: a bounded device-side wait gave up             */
+    GF_ENOTCONV = 5,   /* a mu search missed tol in max_iter, or Jacobi its sweep cap */
+    GF_ETIMEOUT = 6,   /* reserved: no kernel waits on a flag or a peer            */
     GF_ESTATE = 7      /* inputs missing (e.g. gf_local before gf_set_sigma)        */
 } gf_status;
 
