@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="arithmetic of the point kernel (mixed: FP32 pairs on the FP32 pipes)")
     ap.add_argument("--workload", choices=["ce_like", "nio_like", "batched", "adjoint", "lowrank",
-                                           "pole"],
+                                           "pole", "dmft_step"],
                     default="ce_like", help="non-default workloads print one measurement line each")
     ap.add_argument("--peaks", action="store_true",
                     help="compile and run the pipe-throughput microbenchmark (peaks.cu) and exit")
@@ -277,13 +277,21 @@ def run_workload(args):
         (mu, it), t_mu = _sync_time(lambda: gm.find_mu([s.n_target], 0.0, tol=1e-10))
         n_pass = gm.stats()
         ev, t_ev = _sync_time(lambda: gm.evaluate(mu, rho=False, n_corr=False))
+        stm = gm.stats()
         out["mixed"] = {"mu_star": float(mu[0]), "mu_evaluations": it, "find_mu_s": t_mu,
                         "points_per_s": n_pass["points"] / t_mu, "evaluate_s": t_ev,
+                        "evaluate_kernel_s": stm["kernel_ms"] / 1e3,
                         "kernel_choice": gm.tuning_log()}
         g64 = _context(gf, [s], "fp64")
         (ev64), t64 = _sync_time(lambda: g64.evaluate(mu, rho=False, n_corr=False))
-        out["fp64"] = {"evaluate_s": t64, "points_per_s": s.nk * s.n_iw / t64}
+        st64 = g64.stats()
+        out["fp64"] = {"evaluate_s": t64, "points_per_s": s.nk * s.n_iw / t64,
+                       "kernel_tflops": st64["flops"] / st64["kernel_ms"] / 1e9,
+                       "kernel_choice": g64.tuning_log()}
+        # (the first pass of a mode also runs the autotuner's samples; kernel times exclude them)
         out["mixed_speedup_per_pass"] = t64 / t_ev
+        out["mixed_speedup_per_pass_kernel_time"] = st64["kernel_ms"] / stm["kernel_ms"]
+        out["fp64"]["evaluate_kernel_s"] = st64["kernel_ms"] / 1e3
         out["N_rel_err_mixed_vs_fp64_gpu"] = abs(ev["N"][0] - ev64["N"][0]) / ev64["N"][0]
         gl_m, gl_d = ev["gloc"], ev64["gloc"]
         out["G_loc_rel_err_mixed_vs_fp64_gpu"] = float((gl_m - gl_d).abs().max() / gl_d.abs().max())
@@ -479,6 +487,35 @@ def run_workload(args):
                 "N_pole_minus_matsubara": float(n_p[0] - n_m[0]),
                 "G_loc_rel_diff_vs_matsubara": float((glp - glm).abs().max() / glm.abs().max()),
                 "N_rel_err_vs_pole_oracle_8k": abs(n_sub[0] - sub["N"]) / sub["N"]}
+            g.close()
+    elif args.workload == "dmft_step":
+        # the steps around the lattice sums: Lowdin projectors (Eqs. 6-7), E_imp and Delta
+        # (Eqs. E^imp, dmftloop2), on the Ce-like and NiO-like (N_k = 1024) shapes
+        from oracle import dmft as dmft_oracle
+        out["config"] = "Ce-like full size; NiO-like generators with N_k = 1024"
+        for name, s in _lr_pole_cases(args, synth):
+            g = _context(gf, [s], "fp64")
+            rng = np.random.default_rng(17)
+            W = [np.diag(rng.uniform(0.5, 1.5, s.m)) @ p for p in s.P]
+            Wp = _pack(W)
+            g.set_projectors_lowdin(Wp)
+            P_new, t_low = _sync_time(lambda: g.set_projectors_lowdin(Wp))
+            mu = 0.3
+            gl = g.local(mu)
+            E, t_e = _sync_time(lambda: g.impurity_levels([1.0]))
+            D, t_d = _sync_time(lambda: g.hybridization(mu, gl, [1.0]))
+            ks = list(range(4))
+            ref = dmft_oracle.lowdin([W[k] for k in ks])
+            Pk = P_new.cpu().numpy().reshape(s.nk, s.m, -1)[ks]
+            idx = [0, s.n_iw - 1]
+            glh = gl.cpu().numpy().reshape(s.n_iw, s.m, s.m)
+            Dr = np.array([(1j * (2 * n + 1) * np.pi / s.beta + mu) * np.eye(s.m) - E.cpu().numpy().reshape(s.m, s.m)
+                           - s.sigma[n] - np.linalg.inv(glh[n]) for n in idx])
+            Dg = D.cpu().numpy().reshape(s.n_iw, s.m, s.m)[idx]
+            out[name] = {"lowdin_projectors_s": t_low, "impurity_levels_s": t_e, "hybridization_s": t_d,
+                         "lowdin_rel_err_vs_oracle_4k": float(np.max(np.abs(Pk - np.array(ref))) /
+                                                              np.max(np.abs(np.array(ref)))),
+                         "delta_rel_err_vs_formula": float(np.max(np.abs(Dg - Dr)) / np.max(np.abs(Dr)))}
             g.close()
     print(json.dumps(out, default=float), flush=True)
     return 0
