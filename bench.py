@@ -429,8 +429,18 @@ def run_workload(args):
             (nl, dl), tl = _sync_time(lambda: gl.occupation(mu))
             sl = gl.stats()
             pts = sum(s.nk * s.n_iw for s in systems)
+            # the same with GF_PREC_MIXED: FP32-pair band sums, FP64 m x m algebra
+            gx = _context(gf, systems, "mixed", lowrank=True)
+            gx.occupation(mu)
+            (nx, dx), tx = _sync_time(lambda: gx.occupation(mu))
+            gx.close()
             res = {
                 "points": pts,
+                "mixed_lowrank_occupation_s": tx,
+                "mixed_lowrank_speedup_vs_lowrank": tl / tx,
+                "mixed_lowrank_speedup_vs_direct_fp64": td / tx,
+                "mixed_lowrank_N_rel_diff_vs_direct": float(np.max(np.abs(nx - nd) / nd)),
+                "mixed_lowrank_dN_rel_diff_vs_direct": float(np.max(np.abs(dx - dd) / dd)),
                 "direct_occupation_s": td, "lowrank_occupation_s": tl,
                 "lowrank_first_call_s_with_eigendecomposition": t_setup,
                 "speedup_occupation": td / tl,

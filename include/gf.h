@@ -87,7 +87,9 @@ typedef struct {
  * (Woodbury identity): H_k = U diag(eps) U^+ is diagonalised once per
  * Hamiltonian upload (batched Jacobi kernel), after which a point costs
  * 3 N_b m^2 + O(m^3) complex multiply-adds instead of N_b^3.  Same results as
- * the direct inverse up to rounding; FP64 only, N_b <= 256.  With
+ * the direct inverse up to rounding; N_b <= 256.  With GF_PREC_MIXED the band
+ * sums of g0, g1, g2 (the N_b m^2 part) run in FP32-pair arithmetic and the
+ * m x m algebra in FP64.  With
  * GF_FLAG_GRAPH the eigen-decomposition runs outside the replayed graph, once
  * after each upload of H or P.  U^+ G U = D + D Pt^+ K Pt D with D = diag(1/(i w + mu - eps)),
  * Pt = P_k U, K = (I - Sigma Pt D Pt^+)^{-1} Sigma. */

@@ -305,7 +305,7 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
   const int grid = std::min(cfg.grid, std::max(1, n_items));
   if (cfg.kind == 3) {
     gf::LowRank lr{c->lr_eps.as<double>(), c->offD_d.as<int64_t>(), c->lr_Pt.as<double2>(),
-                   cfg.pair_table};
+                   cfg.pair_table, c->precision == GF_PREC_MIXED ? 1 : 0};
     GF_CU(gf::launch_point_lr(p, lr, grid, cfg.smem, c->stream));
     return GF_OK;
   }
@@ -525,12 +525,13 @@ gf_status run_points(gf_ctx* c, int mode) {
         cfg.kind = 3;
         cfg.nbmax = c->bucket_nbmax[bucket];
         const size_t lim = (size_t)c->smem_optin - 1024;
-        const size_t s0 = gf::point_lr_smem(cfg.nbmax, c->mmax, mode, 0);
-        const size_t s1 = gf::point_lr_smem(cfg.nbmax, c->mmax, mode, 1);
+        const int ps = c->precision == GF_PREC_MIXED ? 1 : 0;  // FP32-pair band sums
+        const size_t s0 = gf::point_lr_smem(cfg.nbmax, c->mmax, mode, 0, ps);
+        const size_t s1 = gf::point_lr_smem(cfg.nbmax, c->mmax, mode, 1, ps);
         if (s0 > lim)
           return fail(c, GF_EINVAL, "N_b or m too large for the shared-memory tiles of the low-rank kernel");
-        const int b0 = std::max(1, gf::point_lr_blocks_per_sm(s0));
-        const int b1 = s1 <= lim ? gf::point_lr_blocks_per_sm(s1) : 0;
+        const int b0 = std::max(1, gf::point_lr_blocks_per_sm(s0, ps));
+        const int b1 = s1 <= lim ? gf::point_lr_blocks_per_sm(s1, ps) : 0;
         // keep the item's pair table in shared memory when that costs no occupancy
         cfg.pair_table = (b1 >= b0) ? 1 : 0;
         cfg.smem = cfg.pair_table ? s1 : s0;
@@ -902,10 +903,6 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   c->stream = static_cast<cudaStream_t>(d->stream);
   c->use_graph = (d->flags & GF_FLAG_GRAPH) != 0;
   c->lowrank = (d->flags & GF_FLAG_LOWRANK) != 0;
-  if (c->lowrank && c->precision != GF_PREC_FP64) {
-    delete c;
-    return bad("GF_FLAG_LOWRANK runs in FP64 only");
-  }
   c->nb.resize(c->n_k);
   c->ksys.resize(c->n_k);
   for (int k = 0; k < c->n_k; ++k) {

@@ -128,16 +128,18 @@ struct LowRank {
   const int64_t* offD;
   const double2* Pt;     // [m][N_b] per k at KInfo::offP
   int t_in_smem;         // 1: the pair table Pt_ab conj(Pt_cb) of an item is kept in shared memory
+  int pair_sums;         // 1: the band sums of g0, g1, g2 in FP32-pair arithmetic (mixed precision)
 };
 
 // Shared-memory layout of k_point_lr (16-byte complex elements).  offT: the
 // pair table T[p][b] = Pt_ab conj(Pt_cb), p over the pairs a <= c (m(m+1)/2).
 struct LRLayout {
-  int offPt, offD, offS, offG, offAug, offC, offC2, offX, offCol, offU, offT;
+  int offPt, offD, offS, offG, offAug, offC, offC2, offX, offCol, offU, offT, offPtd, offDd;
   size_t bytes;
 };
 
-__host__ __device__ inline LRLayout make_lr_layout(int nbmax, int mmax, int mode, int t_in_smem) {
+__host__ __device__ inline LRLayout make_lr_layout(int nbmax, int mmax, int mode, int t_in_smem,
+                                                   int pair_sums) {
   LRLayout L;
   const int mm = mmax * mmax;
   int o = 0;
@@ -152,12 +154,14 @@ __host__ __device__ inline LRLayout make_lr_layout(int nbmax, int mmax, int mode
   L.offCol = o; o += 2 * mmax;
   L.offU = o; o += 2 * mmax;
   L.offT = o; o += t_in_smem ? (mmax * (mmax + 1) / 2) * nbmax : 0;
+  L.offPtd = o; o += pair_sums ? mmax * nbmax : 0;  // FP32-pair copies of Pt and of d, d^2, d^3
+  L.offDd = o; o += pair_sums ? 3 * nbmax : 0;
   L.bytes = (size_t)o * 16;
   return L;
 }
 
-size_t point_lr_smem(int nbmax, int mmax, int mode, int t_in_smem);
-int point_lr_blocks_per_sm(size_t smem);
+size_t point_lr_smem(int nbmax, int mmax, int mode, int t_in_smem, int pair_sums);
+int point_lr_blocks_per_sm(size_t smem, int pair_sums);
 cudaError_t launch_point_lr(const PointParams& p, const LowRank& lr, int grid, size_t smem,
                             cudaStream_t s);
 cudaError_t launch_lr_rotate(const KInfo* kinfo, int n_k, const double2* U, double2* rho_part,

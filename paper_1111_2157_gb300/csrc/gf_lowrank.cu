@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include "gf_internal.cuh"
+#include "gf_pair.cuh"
 
 namespace gf {
 
@@ -143,12 +144,88 @@ __device__ __forceinline__ void mm(double2* C, const double2* X, int ldx, const 
   }
 }
 
+// The band sums of g0, g1, g2 in FP32-pair arithmetic: the same pair loop as the
+// FP64 path (pairs a <= c, S threads per pair, warp-uniform bound), with
+// t = Pt_a conj(Pt_c) and the d^j as pairs; results converted to FP64.
+__device__ __forceinline__ void pair_band_sums(int NP, int S, int M, int N, bool need_g1,
+                                               bool need_g2, int t_in_smem, const float4* sPtd,
+                                               const float4* sTpd, const float4* sDd, double2* g0,
+                                               double2* g1, double2* g2) {
+  using pair::f2;
+  const int tid = threadIdx.x;
+  for (int base = 0; base < NP * S; base += kThreads) {
+    const int e = base + tid;
+    const bool valid = e < NP * S;
+    const int pq = valid ? e / S : 0, part = valid ? e - (e / S) * S : 0;
+    int a = 0, rem = pq;
+    while (rem >= M - a) { rem -= M - a; ++a; }
+    const int c = a + rem;
+    // x[j][0..3]: (Xr.re, Xr.im, Xi.re, Xi.im) of g_j
+    f2 x[3][4];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[j][q] = f2{0.f, 0.f};
+    for (int b = part; valid && b < N; b += S) {
+      f2 tr, ti;
+      if (t_in_smem) {
+        const float4 t4 = sTpd[pq * N + b];
+        tr = f2{t4.x, t4.y};
+        ti = f2{t4.z, t4.w};
+      } else {
+        // t = Pt_a conj(Pt_c): re = ar cr + ai ci, im = ai cr - ar ci
+        const float4 u = sPtd[a * N + b], v = sPtd[c * N + b];
+        const f2 ar{u.x, u.y}, ai{u.z, u.w}, cr{v.x, v.y}, ci{v.z, v.w};
+        tr = f2{0.f, 0.f};
+        ti = f2{0.f, 0.f};
+        pair::mac(tr, ar, cr);
+        pair::mac(tr, ai, ci);
+        pair::mac(ti, ai, cr);
+        pair::mac(ti, f2{-ar.h, -ar.l}, ci);
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if ((j == 1 && !need_g1) || (j == 2 && !need_g2)) continue;
+        const float4 d4 = sDd[j * N + b];
+        const f2 dr{d4.x, d4.y}, di{d4.z, d4.w};
+        pair::mac(x[j][0], tr, dr);
+        pair::mac(x[j][1], ti, dr);
+        pair::mac(x[j][2], tr, di);
+        pair::mac(x[j][3], ti, di);
+      }
+    }
+    for (int off = 1; off < S; off <<= 1) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const f2 o{__shfl_xor_sync(0xffffffffu, x[j][q].h, off),
+                     __shfl_xor_sync(0xffffffffu, x[j][q].l, off)};
+          pair::add(x[j][q], o);
+        }
+    }
+    if (valid && part == 0) {
+      double2* gs[3] = {g0, g1, g2};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double xrr = pair::value(x[j][0]), xri = pair::value(x[j][1]);
+        const double xir = pair::value(x[j][2]), xii = pair::value(x[j][3]);
+        gs[j][a * M + c] = make_double2(xrr - xii, xri + xir);
+        gs[j][c * M + a] = make_double2(xrr + xii, xir - xri);
+      }
+    }
+  }
+}
+
+// PAIR: the band sums of g0, g1, g2 in FP32-pair arithmetic (mixed precision);
+// everything else in FP64.
+template <bool PAIR>
 __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, const LowRank lr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* sm = reinterpret_cast<double2*>(smraw);
   __shared__ int s_item;
   __shared__ double s_red[kThreads / 32];
-  const LRLayout L = make_lr_layout(p.nbmax, p.mmax, p.mode, lr.t_in_smem);
+  const LRLayout L = make_lr_layout(p.nbmax, p.mmax, p.mode, lr.t_in_smem, PAIR ? 1 : 0);
   double2* sPt = sm + L.offPt;
   double2* sD = sm + L.offD;  // d, d^2, d^3 per band
   double2* sS = sm + L.offS;
@@ -162,6 +239,9 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
   double2* sCol = sm + L.offCol;
   double2* sU = sm + L.offU;
   double2* sTp = sm + L.offT;
+  float4* sPtd = reinterpret_cast<float4*>(sm + L.offPtd);  // (re.h, re.l, im.h, im.l)
+  float4* sDd = reinterpret_cast<float4*>(sm + L.offDd);
+  float4* sTpd = reinterpret_cast<float4*>(sTp);             // pair table (PAIR)
   const int tid = threadIdx.x;
 
   for (;;) {
@@ -183,6 +263,13 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
     // pairs a <= c, enumerated row by row; S threads share one pair's band sum
     const int NP = M * (M + 1) / 2;
     const int S = NP >= kThreads ? 1 : (2 * NP <= kThreads ? (4 * NP <= kThreads ? 4 : 2) : 1);
+    if (PAIR) {
+      for (int e = tid; e < M * N; e += kThreads) {
+        const double2 v = lr.Pt[ki.offP + e];
+        const pair::f2 re = pair::split(v.x), im = pair::split(v.y);
+        sPtd[e] = make_float4(re.h, re.l, im.h, im.l);
+      }
+    }
     if (lr.t_in_smem) {
       __syncthreads();
       for (int e = tid; e < NP * N; e += kThreads) {
@@ -192,7 +279,12 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
         const int c = a + rem;
         double2 t = make_double2(0.0, 0.0);
         cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
-        sTp[e] = t;
+        if (PAIR) {
+          const pair::f2 re = pair::split(t.x), im = pair::split(t.y);
+          sTpd[e] = make_float4(re.h, re.l, im.h, im.l);
+        } else {
+          sTp[e] = t;
+        }
       }
     }
     double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
@@ -209,6 +301,15 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
         sD[b] = d;
         sD[N + b] = d2;
         sD[2 * N + b] = cmul(d2, d);
+        if (PAIR) {
+          const double2 d3 = sD[2 * N + b];
+          const double2 dd[3] = {d, d2, d3};
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const pair::f2 re = pair::split(dd[j].x), im = pair::split(dd[j].y);
+            sDd[j * N + b] = make_float4(re.h, re.l, im.h, im.l);
+          }
+        }
       }
       for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
       __syncthreads();
@@ -219,6 +320,9 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
       const bool need_g1 = (p.mode & (kOcc | kAdj)) != 0;
       // (the loop bound is uniform across the block, so every lane of a warp reaches the
       // shuffles; lanes past the end sum nothing and write nothing)
+      if (PAIR) {
+        pair_band_sums(NP, S, M, N, need_g1, need_g2, lr.t_in_smem, sPtd, sTpd, sDd, g0, g1, g2);
+      } else
       for (int base = 0; base < NP * S; base += kThreads) {
         const int e = base + tid;
         const bool valid = e < NP * S;
@@ -453,22 +557,34 @@ __global__ void __launch_bounds__(kThreads)
 
 }  // namespace
 
-size_t point_lr_smem(int nbmax, int mmax, int mode, int t_in_smem) {
-  return make_lr_layout(nbmax, mmax, mode, t_in_smem).bytes;
+size_t point_lr_smem(int nbmax, int mmax, int mode, int t_in_smem, int pair_sums) {
+  return make_lr_layout(nbmax, mmax, mode, t_in_smem, pair_sums).bytes;
 }
 
-int point_lr_blocks_per_sm(size_t smem) {
+int point_lr_blocks_per_sm(size_t smem, int pair_sums) {
   int n = 0;
-  cudaFuncSetAttribute(k_point_lr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_point_lr, kThreads, smem);
+  if (pair_sums) {
+    cudaFuncSetAttribute(k_point_lr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_point_lr<true>, kThreads, smem);
+  } else {
+    cudaFuncSetAttribute(k_point_lr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_point_lr<false>, kThreads, smem);
+  }
   return n;
 }
 
 cudaError_t launch_point_lr(const PointParams& p, const LowRank& lr, int grid, size_t smem,
                             cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_point_lr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_point_lr<<<grid, kThreads, smem, s>>>(p, lr);
+  cudaError_t e;
+  if (lr.pair_sums) {
+    e = cudaFuncSetAttribute(k_point_lr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_point_lr<true><<<grid, kThreads, smem, s>>>(p, lr);
+  } else {
+    e = cudaFuncSetAttribute(k_point_lr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_point_lr<false><<<grid, kThreads, smem, s>>>(p, lr);
+  }
   return cudaGetLastError();
 }
 

@@ -73,11 +73,17 @@ def test_new_hamiltonian_refreshes_the_eigenbasis():
     assert abs(n[0] - r["N"]) < 1e-10 * r["N"]
 
 
-def test_rejects_mixed_precision():
-    from paper_1111_2157_gb300.gf import GFError
-    s = synth.random_system(63, 2, 4, 2, 8, 10.0)
-    with pytest.raises(GFError):
-        make_gf([s], precision="mixed", lowrank=True)
+@pytest.mark.parametrize("case", ["ce_like", "ragged"])
+def test_mixed_precision_band_sums(case):
+    """GF_PREC_MIXED with GF_FLAG_LOWRANK: FP32-pair band sums, FP64 m x m algebra."""
+    if case == "ce_like":
+        systems = [synth.ce_like(nk=6, n_iw=40).systems[0]]
+        mus = [0.4]
+    else:
+        systems = [synth.random_system(71, 5, 9, 3, 24, 12.0), synth.random_system(72, 4, 30, 20, 24, 20.0)]
+        mus = [0.2, -0.3]
+    check_system_set(systems, mus, {"G_loc": 1e-9, "N": 1e-9, "dN_dmu": 1e-9, "n_corr": 1e-9, "rho": 1e-9},
+                     precision="mixed", lowrank=True)
 
 
 def test_graph_replay_of_the_low_rank_mu_search():
