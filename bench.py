@@ -669,13 +669,24 @@ def main():
         gl_lr = gr.local([info["mu"]])
         gl_fp = g.local([info["mu"]])
         lt = lr["totals"]
+        # and with GF_PREC_MIXED (FP32-pair band sums, FP64 m x m algebra)
+        ml = run_leg("mixed", args.steps, args.warmup, False, lowrank=True)
+        gml = ml["g"]
+        n_ml, _ = gml.occupation([info["mu"]])
+        mlt = ml["totals"]
+        mixed_lowrank = {"value": mlt["points"] * ws / ml["elapsed"], "unit": UNIT,
+                         "ms_per_step": ml["elapsed"] / args.steps * 1e3,
+                         "speedup_vs_direct_fp64_gpu": (mlt["points"] / ml["elapsed"]) / (totals["points"] / elapsed),
+                         "N_rel_err_vs_direct": abs(n_ml[0] - info["N"]) / abs(info["N"]),
+                         "gpu_launches": mlt["launches"]}
+        gml.close()
         lowrank = {"value": lt["points"] * ws / lr["elapsed"], "unit": UNIT,
                    "ms_per_step": lr["elapsed"] / args.steps * 1e3,
                    "speedup_vs_direct_fp64_gpu": (lt["points"] / lr["elapsed"]) / (totals["points"] / elapsed),
                    "N_rel_err_vs_direct": abs(n_lr[0] - info["N"]) / abs(info["N"]),
                    "G_loc_rel_err_vs_direct": float((gl_lr - gl_fp).abs().max() / gl_fp.abs().max()),
                    "algorithm": "G in the eigenbasis of H_k (Woodbury identity), FP64; H_k diagonalised once",
-                   "gpu_launches": lt["launches"]}
+                   "gpu_launches": lt["launches"], "mixed_precision": mixed_lowrank}
         gr.close()
 
     e2e = None

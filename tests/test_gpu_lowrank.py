@@ -128,3 +128,18 @@ def test_ce_like_full_size_sampled():
     gd = make_gf([s])
     nd, _ = gd.occupation([mu])
     assert abs(out["N"][0] - nd[0]) < 1e-12 * nd[0]
+
+
+def test_mixed_precision_backward_and_mu_search():
+    s = synth.ce_like(nk=5, n_iw=32).systems[0]
+    g = make_gf([s], precision="mixed", lowrank=True)
+    mu, it = g.find_mu(s.n_target, 0.0, tol=1e-10)
+    r = oracle.get().density(s.H, s.P, s.sigma, s.sigma_inf, s.beta, mu[0], want_rho=False)
+    assert abs(r["N"] - s.n_target) < 1e-9
+    rng = np.random.default_rng(4)
+    gbar = rng.standard_normal(s.sigma.shape) + 1j * rng.standard_normal(s.sigma.shape)
+    sb, mb = g.backward(mu, gloc_bar=gbar.reshape(-1), n_bar=[0.7])
+    sref, mref = oracle.get().backward(s.H, s.P, s.sigma, s.sigma_inf, s.beta, mu[0],
+                                       gloc_bar=gbar, n_bar=0.7)
+    assert rel(sb.cpu().numpy(), sref.reshape(-1)) < 1e-9
+    assert abs(mb[0] - mref) < 1e-9 * abs(mref)
