@@ -144,13 +144,122 @@ __device__ __forceinline__ void mm(double2* C, const double2* X, int ldx, const 
   }
 }
 
+// Complex FP32 pairs: c = (re, im) as float4 (re.h, re.l, im.h, im.l).
+__device__ __forceinline__ void cp_mac(pair::f2& re, pair::f2& im, float4 a, float4 b) {
+  using pair::f2;
+  const f2 ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
+  pair::mac(re, ar, br);
+  pair::mac(re, f2{-ai.h, -ai.l}, bi);
+  pair::mac(im, ar, bi);
+  pair::mac(im, ai, br);
+}
+__device__ __forceinline__ float4 cp_pack(pair::f2 re, pair::f2 im) {
+  float s, e;
+  pair::two_sum(re.h, re.l, s, e);  // renormalise: |lo| <= ulp(hi) / 2
+  re = pair::f2{s, e};
+  pair::two_sum(im.h, im.l, s, e);
+  im = pair::f2{s, e};
+  return make_float4(re.h, re.l, im.h, im.l);
+}
+__device__ __forceinline__ unsigned pivot_key_p(float4 a) {
+  const unsigned r = __float_as_uint(a.x) & 0x7fffffffu, i = __float_as_uint(a.z) & 0x7fffffffu;
+  return r > i ? r : i;
+}
+
+// [I - Sigma g0 | Sigma] in FP32 pairs, reduced by Gauss-Jordan with partial
+// pivoting (key from the head words) to [I | K], then K converted to FP64 in
+// place: the float4 pairs and the double2 values have the same size, and each
+// thread converts the entries it owns.  Sp, g0p: M x M pairs; augp aliases aug.
+__device__ void pair_solve(const float4* Sp, const float4* g0p, double2* aug, int M, float4* colp,
+                           float4* urowp, int* status) {
+  using pair::f2;
+  __shared__ int s_p;
+  __shared__ float4 s_r;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int W = 2 * M;
+  float4* augp = reinterpret_cast<float4*>(aug);
+  for (int e = tid; e < M * M; e += kThreads) {
+    const int a = e / M, c = e - (e / M) * M;
+    f2 re{a == c ? 1.f : 0.f, 0.f}, im{0.f, 0.f};
+    for (int x = 0; x < M; ++x) {
+      const float4 sv = Sp[a * M + x];
+      cp_mac(re, im, make_float4(-sv.x, -sv.y, -sv.z, -sv.w), g0p[x * M + c]);
+    }
+    augp[a * W + c] = cp_pack(re, im);
+    augp[a * W + M + c] = Sp[e];
+  }
+  __syncthreads();
+  for (int j = 0; j < M; ++j) {
+    if (warp == 0) {
+      unsigned best = 0u;
+      int bi = 0x7fffffff;
+      for (int i = j + lane; i < M; i += 32) {
+        const unsigned key = pivot_key_p(augp[i * W + j]);
+        if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
+      }
+      for (int off = 16; off; off >>= 1) {
+        const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (best == 0u || best >= 0x7f800000u) atomicOr(status, kFlagSingular);
+        s_p = bi;
+        // reciprocal of the pivot in FP64 (one per step), split into pairs
+        const float4 pv = augp[bi * W + j];
+        const double2 r = crcp(make_double2((double)pv.x + (double)pv.y, (double)pv.z + (double)pv.w));
+        const f2 rr = pair::split(r.x), ri = pair::split(r.y);
+        s_r = make_float4(rr.h, rr.l, ri.h, ri.l);
+      }
+    }
+    __syncthreads();
+    const int pr = s_p;
+    const float4 r = s_r;
+    for (int c = tid; c < W; c += kThreads) {
+      const float4 vp = augp[pr * W + c];
+      if (c == j) {
+        urowp[c] = make_float4(1.f, 0.f, 0.f, 0.f);
+      } else {
+        f2 re{0.f, 0.f}, im{0.f, 0.f};
+        cp_mac(re, im, vp, r);
+        urowp[c] = cp_pack(re, im);
+      }
+      if (pr != j) augp[pr * W + c] = augp[j * W + c];
+    }
+    for (int i = tid; i < M; i += kThreads) colp[i] = (i == pr) ? augp[j * W + j] : augp[i * W + j];
+    __syncthreads();
+    const int Wj = W - j;
+    for (int e = tid; e < M * Wj; e += kThreads) {
+      const int i = e / Wj, c = j + (e - (e / Wj) * Wj);
+      if (i == j) {
+        augp[i * W + c] = urowp[c];
+      } else if (c == j) {
+        augp[i * W + c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const float4 v = augp[i * W + c], l = colp[i];
+        f2 re{v.x, v.y}, im{v.z, v.w};
+        cp_mac(re, im, make_float4(-l.x, -l.y, -l.z, -l.w), urowp[c]);
+        augp[i * W + c] = cp_pack(re, im);
+      }
+    }
+    __syncthreads();
+  }
+  // K (right half) to FP64 in place; the left half (the identity) is not read again
+  for (int e = tid; e < M * M; e += kThreads) {
+    const int a = e / M, c = e - (e / M) * M;
+    const float4 v = augp[a * W + M + c];
+    aug[a * W + M + c] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+  __syncthreads();
+}
+
 // The band sums of g0, g1, g2 in FP32-pair arithmetic: the same pair loop as the
 // FP64 path (pairs a <= c, S threads per pair, warp-uniform bound), with
 // t = Pt_a conj(Pt_c) and the d^j as pairs; results converted to FP64.
 __device__ __forceinline__ void pair_band_sums(int NP, int S, int M, int N, bool need_g1,
                                                bool need_g2, int t_in_smem, const float4* sPtd,
                                                const float4* sTpd, const float4* sDd, double2* g0,
-                                               double2* g1, double2* g2) {
+                                               double2* g1, double2* g2, float4* g0p) {
   using pair::f2;
   const int tid = threadIdx.x;
   for (int base = 0; base < NP * S; base += kThreads) {
@@ -213,6 +322,15 @@ __device__ __forceinline__ void pair_band_sums(int NP, int S, int M, int N, bool
         gs[j][a * M + c] = make_double2(xrr - xii, xri + xir);
         gs[j][c * M + a] = make_double2(xrr + xii, xir - xri);
       }
+      // g0 also as pairs for the pair elimination: (g0)_ac = Xr + i Xi, (g0)_ca = conj(Xr) + i conj(Xi)
+      const f2 rr = x[0][0], ri = x[0][1], ir = x[0][2], ii = x[0][3];
+      f2 ac_re = rr, ac_im = ri, ca_re = rr, ca_im = ir;
+      pair::add(ac_re, f2{-ii.h, -ii.l});
+      pair::add(ac_im, ir);
+      pair::add(ca_re, ii);
+      pair::add(ca_im, f2{-ri.h, -ri.l});
+      g0p[a * M + c] = make_float4(ac_re.h, ac_re.l, ac_im.h, ac_im.l);
+      g0p[c * M + a] = make_float4(ca_re.h, ca_re.l, ca_im.h, ca_im.l);
     }
   }
 }
@@ -321,7 +439,8 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
       // (the loop bound is uniform across the block, so every lane of a warp reaches the
       // shuffles; lanes past the end sum nothing and write nothing)
       if (PAIR) {
-        pair_band_sums(NP, S, M, N, need_g1, need_g2, lr.t_in_smem, sPtd, sTpd, sDd, g0, g1, g2);
+        pair_band_sums(NP, S, M, N, need_g1, need_g2, lr.t_in_smem, sPtd, sTpd, sDd, g0, g1, g2,
+                       reinterpret_cast<float4*>(sC));
       } else
       for (int base = 0; base < NP * S; base += kThreads) {
         const int e = base + tid;
@@ -372,20 +491,32 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
         }
       }
       __syncthreads();
-      // aug = [I - Sigma g0 | Sigma]
-      for (int e = tid; e < M * M; e += kThreads) {
-        const int a = e / M, c = e - (e / M) * M;
-        double2 acc = make_double2(a == c ? 1.0 : 0.0, 0.0);
-        for (int x = 0; x < M; ++x) {
-          const double2 s = sS[a * M + x], g = g0[x * M + c];
-          acc.x -= fma(s.x, g.x, -s.y * g.y);
-          acc.y -= fma(s.x, g.y, s.y * g.x);
+      if (PAIR) {
+        // Sigma as pairs in sC2's storage (sC holds g0 as pairs); both are free until K exists
+        float4* Sp = reinterpret_cast<float4*>(sC2);
+        for (int e = tid; e < M * M; e += kThreads) {
+          const pair::f2 re = pair::split(sS[e].x), im = pair::split(sS[e].y);
+          Sp[e] = make_float4(re.h, re.l, im.h, im.l);
         }
-        aug[a * W + c] = acc;
-        aug[a * W + M + c] = sS[e];
+        __syncthreads();
+        pair_solve(Sp, reinterpret_cast<const float4*>(sC), aug, M, reinterpret_cast<float4*>(sCol),
+                   reinterpret_cast<float4*>(sU), p.status);
+      } else {
+        // aug = [I - Sigma g0 | Sigma]
+        for (int e = tid; e < M * M; e += kThreads) {
+          const int a = e / M, c = e - (e / M) * M;
+          double2 acc = make_double2(a == c ? 1.0 : 0.0, 0.0);
+          for (int x = 0; x < M; ++x) {
+            const double2 s = sS[a * M + x], g = g0[x * M + c];
+            acc.x -= fma(s.x, g.x, -s.y * g.y);
+            acc.y -= fma(s.x, g.y, s.y * g.x);
+          }
+          aug[a * W + c] = acc;
+          aug[a * W + M + c] = sS[e];
+        }
+        __syncthreads();
+        gj_augmented(aug, M, sCol, sU, p.status);
       }
-      __syncthreads();
-      gj_augmented(aug, M, sCol, sU, p.status);
       const double2* K = aug + M;  // K[a * W + c]
       if (p.mode & (kOcc | kAdj)) mm(sC, K, W, g1, M);
       if (p.mode & (kGloc | kAdj)) mm(sC2, K, W, g0, M);
