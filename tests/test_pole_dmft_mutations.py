@@ -9,6 +9,7 @@ import pytest
 
 from oracle import dmft, pole
 from tests import test_dmft_oracle as dpins
+from tests import test_golden_double_counting as gpins
 from tests import test_pole_oracle as ppins
 
 POLE_PINS = [ppins.test_local_equals_matsubara_oracle, ppins.test_density_is_the_infinite_matsubara_limit,
@@ -20,7 +21,10 @@ DMFT_PINS = [dpins.test_single_k_with_identity_projector_gives_v_dc,
              dpins.test_high_frequency_decay_and_causality,
              dpins.test_hybridization_numbering_matches_direct_formula,
              dpins.test_lowdin_against_library_sqrtm_and_special_cases,
-             dpins.test_double_counting_special_cases]
+             dpins.test_double_counting_special_cases,
+             gpins.test_u_bar_is_the_pair_average_of_h_u,
+             gpins.test_e_dc_is_the_mean_configuration_energy,
+             gpins.test_v_dc_is_the_central_difference_of_the_mean_energy]
 
 _ph, _dens, _spec, _energy = pole.pseudo_hamiltonian, pole.density, pole.spectral, pole.energy
 _lowdin, _eimp, _hyb, _dc = dmft.lowdin, dmft.impurity_levels, dmft.hybridization, dmft.double_counting
@@ -81,6 +85,18 @@ def dc_sign(U, J, l, n):
     return ub, ub * (n - 0.5), 0.5 * ub * n * (n - 1)
 
 
+def dc_hund_all_orbitals(U, J, l, n):
+    ub, _, _ = _dc(U, J, l, n)
+    M = 2 * l + 1
+    ub = ub - J / (2 * M - 1)
+    return ub, ub * (n - 0.5), 0.5 * ub * n * (n - 1)
+
+
+def dc_energy_n_squared(U, J, l, n):
+    ub, vdc, _ = _dc(U, J, l, n)
+    return ub, vdc, 0.5 * ub * n * n
+
+
 MUTATIONS = [
     (pole, "pseudo_hamiltonian", ph_no_mu_shift, POLE_PINS),
     (pole, "pseudo_hamiltonian", ph_conjugated_coupling, POLE_PINS),
@@ -93,6 +109,8 @@ MUTATIONS = [
     (dmft, "impurity_levels", eimp_plus_vdc, DMFT_PINS),
     (dmft, "hybridization", hyb_plus_inverse, DMFT_PINS),
     (dmft, "double_counting", dc_sign, DMFT_PINS),
+    (dmft, "double_counting", dc_hund_all_orbitals, DMFT_PINS),
+    (dmft, "double_counting", dc_energy_n_squared, DMFT_PINS),
 ]
 
 
