@@ -30,7 +30,9 @@
  *  - Every compute call is ordered on the context's stream and returns after
  *    the stream has drained, so host outputs are valid on return.
  *  - Calls on one context are not thread-safe.  No entry point throws; each
- *    returns a gf_status and records a message for gf_last_error().
+ *    returns a gf_status and records a message for gf_last_error().  A host
+ *    allocation that fails inside the library returns GF_ENOMEM (gf_create
+ *    then frees what it had built and leaves *out NULL).
  *  - There is no CPU fallback: gf_create fails with GF_ECUDA without a device.
  */
 #ifndef GF_H

@@ -30,7 +30,13 @@ double tail_coefficient(double beta, int n_iw, int tail_order) {
   return -beta / (2.0 * M_PI * M_PI) * trigamma(n_iw + 0.5);
 }
 
-void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+void set_global_error(const char* msg) noexcept {
+  try {
+    g_create_error = msg ? msg : "";
+  } catch (...) {
+    g_create_error.clear();
+  }
+}
 
 }  // namespace gf
 
@@ -514,34 +520,15 @@ gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-gf_status gf_create(gf_ctx** out, const gf_desc* d) {
-  g_create_error.clear();
-  if (!out) {
-    g_create_error = "out is NULL";
-    return GF_EINVAL;
-  }
-  *out = nullptr;
+// Fills a new context from its descriptor and allocates its device workspace.  It never
+// frees the context: gf_create discards it on a failed status and on a C++ exception alike.
+gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
   auto bad = [](const char* m) {
-    g_create_error = m;
+    gf::set_global_error(m);
     return GF_EINVAL;
   };
-  if (!d) return bad("desc is NULL");
-  if (d->n_systems < 1) return bad("n_systems must be >= 1");
-  if (d->n_k < 1) return bad("n_k must be >= 1");
-  if (d->n_iw < 1) return bad("n_iw must be >= 1");
-  if (!d->m_system) return bad("m_system is NULL");
-  if (!d->beta) return bad("beta is NULL");
-  if (!d->nb && d->nb_uniform < 1) return bad("nb is NULL and nb_uniform < 1");
-  if (d->precision != GF_PREC_FP64 && d->precision != GF_PREC_MIXED) return bad("bad precision");
-  if (d->input_dtype != GF_C128 && d->input_dtype != GF_C64) return bad("bad input_dtype");
-  if (d->tail_order != 1 && d->tail_order != 2) return bad("tail_order must be 1 or 2");
-  gf_ctx* c = new (std::nothrow) gf_ctx();
-  if (!c) {
-    g_create_error = "host allocation failed";
-    return GF_ENOMEM;
-  }
   c->n_sys = d->n_systems;
   c->n_k = d->n_k;
   c->n_iw = d->n_iw;
@@ -557,15 +544,15 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   for (int k = 0; k < c->n_k; ++k) {
     c->nb[k] = d->nb ? d->nb[k] : d->nb_uniform;
     c->ksys[k] = d->k_system ? d->k_system[k] : 0;
-    if (c->nb[k] < 1) { delete c; return bad("every N_b(k) must be >= 1"); }
-    if (c->ksys[k] < 0 || c->ksys[k] >= c->n_sys) { delete c; return bad("k_system out of range"); }
-    if (k > 0 && c->ksys[k] < c->ksys[k - 1]) { delete c; return bad("k_system must be non-decreasing"); }
+    if (c->nb[k] < 1) return bad("every N_b(k) must be >= 1");
+    if (c->ksys[k] < 0 || c->ksys[k] >= c->n_sys) return bad("k_system out of range");
+    if (k > 0 && c->ksys[k] < c->ksys[k - 1]) return bad("k_system must be non-decreasing");
   }
   c->msys.assign(d->m_system, d->m_system + c->n_sys);
   c->beta.assign(d->beta, d->beta + c->n_sys);
   for (int s = 0; s < c->n_sys; ++s) {
-    if (c->msys[s] < 1) { delete c; return bad("every m must be >= 1"); }
-    if (!(c->beta[s] > 0.0) || !std::isfinite(c->beta[s])) { delete c; return bad("beta must be > 0"); }
+    if (c->msys[s] < 1) return bad("every m must be >= 1");
+    if (!(c->beta[s] > 0.0) || !std::isfinite(c->beta[s])) return bad("beta must be > 0");
   }
   // systems, k ranges and weights
   c->sinfo.resize(c->n_sys);
@@ -574,7 +561,7 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   int64_t offSig = 0, offSinf = 0;
   int k0 = 0;
   for (int s = 0; s < c->n_sys; ++s) {
-    if (count[s] == 0) { delete c; return bad("a system has no k-points"); }
+    if (count[s] == 0) return bad("a system has no k-points");
     SInfo& si = c->sinfo[s];
     si.m = c->msys[s];
     si.k0 = k0;
@@ -603,7 +590,7 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
     ki.offP = offP;
     const SInfo& si = c->sinfo[ki.sys];
     ki.w = d->k_weight ? d->k_weight[k] : 1.0 / (si.k1 - si.k0);
-    if (!std::isfinite(ki.w)) { delete c; return bad("k_weight is not finite"); }
+    if (!std::isfinite(ki.w)) return bad("k_weight is not finite");
     c->wk[k] = ki.w;
     c->offD[k] = offD;
     offH += (int64_t)ki.nb * ki.nb;
@@ -623,11 +610,11 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
-    delete c;
-    g_create_error = "no CUDA device";
+    gf::set_global_error("no CUDA device");
     return GF_ECUDA;
   }
-  if (c->device < 0 || c->device >= ndev) { delete c; return bad("device ordinal out of range"); }
+  if (c->device < 0 || c->device >= ndev) return bad("device ordinal out of range");
+  c->device_checked = true;
   DeviceGuard guard(c->device);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
   cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -736,12 +723,69 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) {
   };
   cudaError_t e = alloc_all();
   if (e != cudaSuccess) {
-    g_create_error = std::string("device setup failed: ") + cudaGetErrorString(e);
-    gf_destroy(c);
+    char msg[160];
+    std::snprintf(msg, sizeof(msg), "device setup failed: %s", cudaGetErrorString(e));
+    gf::set_global_error(msg);
     return e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA;
+  }
+  return GF_OK;
+}
+
+// Frees a context that gf_create does not hand out: by gf_destroy once its device ordinal
+// has been checked, before that by a plain delete, so that no CUDA call is made on an
+// invalid device and no CUDA error is left behind.
+void discard_ctx(gf_ctx* c) noexcept {
+  if (c->device_checked)
+    gf_destroy(c);
+  else
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+gf_status gf_create(gf_ctx** out, const gf_desc* d) try {
+  gf::set_global_error("");
+  if (!out) {
+    gf::set_global_error("out is NULL");
+    return GF_EINVAL;
+  }
+  *out = nullptr;
+  auto bad = [](const char* m) {
+    gf::set_global_error(m);
+    return GF_EINVAL;
+  };
+  if (!d) return bad("desc is NULL");
+  if (d->n_systems < 1) return bad("n_systems must be >= 1");
+  if (d->n_k < 1) return bad("n_k must be >= 1");
+  if (d->n_iw < 1) return bad("n_iw must be >= 1");
+  if (!d->m_system) return bad("m_system is NULL");
+  if (!d->beta) return bad("beta is NULL");
+  if (!d->nb && d->nb_uniform < 1) return bad("nb is NULL and nb_uniform < 1");
+  if (d->precision != GF_PREC_FP64 && d->precision != GF_PREC_MIXED) return bad("bad precision");
+  if (d->input_dtype != GF_C128 && d->input_dtype != GF_C64) return bad("bad input_dtype");
+  if (d->tail_order != 1 && d->tail_order != 2) return bad("tail_order must be 1 or 2");
+  gf_ctx* c = new (std::nothrow) gf_ctx();
+  if (!c) {
+    gf::set_global_error("host allocation failed");
+    return GF_ENOMEM;
+  }
+  gf_status st;
+  try {
+    st = init_ctx(c, d);
+  } catch (...) {
+    discard_ctx(c);
+    throw;
+  }
+  if (st != GF_OK) {
+    discard_ctx(c);
+    return st;
   }
   *out = c;
   return GF_OK;
+} catch (...) {
+  return caught(nullptr);
 }
 
 gf_status gf_destroy(gf_ctx* c) {
@@ -768,7 +812,7 @@ gf_status gf_destroy(gf_ctx* c) {
   return GF_OK;
 }
 
-gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) {
+gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) try {
   NvtxRange nvtx_range_("gf_set_hamiltonian");
   if (!c) return GF_EINVAL;
   if (!h) return fail(c, GF_EINVAL, "h_ptr is NULL");
@@ -801,9 +845,11 @@ gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) {
   c->lr_dirty = true;
   c->einf_dirty = true;
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_set_projectors(gf_ctx* c, const void* p) {
+gf_status gf_set_projectors(gf_ctx* c, const void* p) try {
   NvtxRange nvtx_range_("gf_set_projectors");
   if (!c) return GF_EINVAL;
   if (!p) return fail(c, GF_EINVAL, "p_ptr is NULL");
@@ -817,9 +863,11 @@ gf_status gf_set_projectors(gf_ctx* c, const void* p) {
   c->lr_dirty = true;
   c->einf_dirty = true;
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) {
+gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) try {
   NvtxRange nvtx_range_("gf_set_sigma");
   if (!c) return GF_EINVAL;
   if (!sig || !sinf) return fail(c, GF_EINVAL, "sigma_iw_ptr or sigma_inf_ptr is NULL");
@@ -834,19 +882,23 @@ gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) {
   c->have_S = true;
   c->einf_dirty = true;
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+gf_status gf_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_out) try {
   NvtxRange nvtx_range_("gf_occupation");
   if (!c) return GF_EINVAL;
   if (!n_out) return fail(c, GF_EINVAL, "n_out is NULL");
   DeviceGuard guard(c->device);
   reset_stats(c);
   return occupation_impl(c, mu, n_out, dn_out);
+} catch (...) {
+  return caught(c);
 }
 
 gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_iter,
-                     double* mu_inout, int32_t* iters_out) {
+                     double* mu_inout, int32_t* iters_out) try {
   NvtxRange nvtx_range_("gf_find_mu");
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
@@ -855,9 +907,11 @@ gf_status gf_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_
                    [c](const double* mu, double* n, double* dn) {
                      return occupation_impl(c, mu, n, dn);  // stats accumulate
                    });
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) {
+gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) try {
   NvtxRange nvtx_range_("gf_density_matrix");
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
@@ -889,9 +943,11 @@ gf_status gf_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* 
   if (n_corr_out)
     for (int s = 0; s < c->n_sys; ++s) n_corr_out[s] = c->hp_sys()[2 * s];
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_local(gf_ctx* c, const double* mu, void* gloc_out) {
+gf_status gf_local(gf_ctx* c, const double* mu, void* gloc_out) try {
   NvtxRange nvtx_range_("gf_local");
   if (!c) return GF_EINVAL;
   if (!gloc_out) return fail(c, GF_EINVAL, "gloc_out_ptr is NULL");
@@ -904,10 +960,12 @@ gf_status gf_local(gf_ctx* c, const double* mu, void* gloc_out) {
   GF_CU(cudaMemcpyAsync(gloc_out, c->gacc.p, sizeof(double2) * c->totSig, cudaMemcpyDefault,
                         c->stream));
   return sync_and_check(c);
+} catch (...) {
+  return caught(c);
 }
 
 gf_status gf_evaluate(gf_ctx* c, const double* mu, void* gloc_out, void* rho_out, double* n_out,
-                      double* dn_out, double* n_corr_out) {
+                      double* dn_out, double* n_corr_out) try {
   NvtxRange nvtx_range_("gf_evaluate");
   if (!c) return GF_EINVAL;
   const int mode = (gloc_out ? gf::kGloc : 0) | ((rho_out || n_corr_out) ? gf::kRho : 0) |
@@ -963,10 +1021,12 @@ gf_status gf_evaluate(gf_ctx* c, const double* mu, void* gloc_out, void* rho_out
   if (n_corr_out)
     for (int s = 0; s < c->n_sys; ++s) n_corr_out[s] = c->hp_sys2()[2 * s];
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
 gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const double* nbar,
-                      void* sbar_out, double* mubar_out) {
+                      void* sbar_out, double* mubar_out) try {
   NvtxRange nvtx_range_("gf_backward");
   if (!c) return GF_EINVAL;
   if (!sbar_out || !mubar_out) return fail(c, GF_EINVAL, "sigma_bar_out_ptr or mu_bar_out is NULL");
@@ -1022,6 +1082,8 @@ gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const doubl
     mubar_out[s] = c->hp_nbar()[s] * dn + c->hp_mubar()[s];
   }
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
 const char* gf_tuning_log(const gf_ctx* c) {

@@ -114,7 +114,7 @@ gf_status pole_occupation_impl(gf_ctx* c, const double* mu, double* n_out, doubl
 extern "C" {
 
 gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* poles,
-                             const void* v, const void* sinf) {
+                             const void* v, const void* sinf) try {
   NvtxRange nvtx_range_("gf_set_sigma_poles");
   if (!c) return GF_EINVAL;
   if (!n_poles || !sinf) return fail(c, GF_EINVAL, "n_poles or sigma_inf_ptr is NULL");
@@ -193,19 +193,23 @@ gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* po
   c->nps_max = nps;
   c->have_poles = true;
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_pole_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_out) {
+gf_status gf_pole_occupation(gf_ctx* c, const double* mu, double* n_out, double* dn_out) try {
   NvtxRange nvtx_range_("gf_pole_occupation");
   if (!c) return GF_EINVAL;
   if (!n_out) return fail(c, GF_EINVAL, "n_out is NULL");
   DeviceGuard guard(c->device);
   reset_stats(c);
   return pole_occupation_impl(c, mu, n_out, dn_out);
+} catch (...) {
+  return caught(c);
 }
 
 gf_status gf_pole_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t max_iter,
-                          double* mu_inout, int32_t* iters_out) {
+                          double* mu_inout, int32_t* iters_out) try {
   NvtxRange nvtx_range_("gf_pole_find_mu");
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
@@ -227,9 +231,11 @@ gf_status gf_pole_find_mu(gf_ctx* c, const double* n_target, double tol, int32_t
                      if (e != cudaSuccess) return fail(c, GF_ECUDA, cudaGetErrorString(e));
                      return GF_OK;
                    });
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_pole_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) {
+gf_status gf_pole_density_matrix(gf_ctx* c, const double* mu, void* rho_out, double* n_corr_out) try {
   NvtxRange nvtx_range_("gf_pole_density_matrix");
   if (!c) return GF_EINVAL;
   DeviceGuard guard(c->device);
@@ -251,9 +257,11 @@ gf_status gf_pole_density_matrix(gf_ctx* c, const double* mu, void* rho_out, dou
   if (n_corr_out)
     for (int s = 0; s < c->n_sys; ++s) n_corr_out[s] = c->hp_sys()[2 * s];
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_pole_local(gf_ctx* c, const double* mu, void* gloc_out) {
+gf_status gf_pole_local(gf_ctx* c, const double* mu, void* gloc_out) try {
   NvtxRange nvtx_range_("gf_pole_local");
   if (!c) return GF_EINVAL;
   if (!gloc_out) return fail(c, GF_EINVAL, "gloc_out_ptr is NULL");
@@ -266,9 +274,11 @@ gf_status gf_pole_local(gf_ctx* c, const double* mu, void* gloc_out) {
   GF_CU(cudaMemcpyAsync(gloc_out, c->gacc.p, sizeof(double2) * c->totSig, cudaMemcpyDefault,
                         c->stream));
   return pole_check(c);
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_set_projectors_lowdin(gf_ctx* c, const void* w, void* p_out) {
+gf_status gf_set_projectors_lowdin(gf_ctx* c, const void* w, void* p_out) try {
   NvtxRange nvtx_range_("gf_set_projectors_lowdin");
   if (!c) return GF_EINVAL;
   if (!w) return fail(c, GF_EINVAL, "w_ptr is NULL");
@@ -293,9 +303,11 @@ gf_status gf_set_projectors_lowdin(gf_ctx* c, const void* w, void* p_out) {
   c->lr_dirty = true;
   c->einf_dirty = true;
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_impurity_levels(gf_ctx* c, const double* v_dc, void* e_imp_out) {
+gf_status gf_impurity_levels(gf_ctx* c, const double* v_dc, void* e_imp_out) try {
   NvtxRange nvtx_range_("gf_impurity_levels");
   if (!c) return GF_EINVAL;
   if (!e_imp_out) return fail(c, GF_EINVAL, "e_imp_out_ptr is NULL");
@@ -321,10 +333,12 @@ gf_status gf_impurity_levels(gf_ctx* c, const double* v_dc, void* e_imp_out) {
     GF_CU(cudaMemcpyAsync(e_imp_out, c->eimp.p, sizeof(double2) * c->totSinf, cudaMemcpyDefault,
                           c->stream));
   return sync_and_check(c);
+} catch (...) {
+  return caught(c);
 }
 
 gf_status gf_hybridization(gf_ctx* c, const double* mu, const void* gloc, const double* v_dc,
-                           void* delta_out) {
+                           void* delta_out) try {
   NvtxRange nvtx_range_("gf_hybridization");
   if (!c) return GF_EINVAL;
   if (!gloc || !delta_out) return fail(c, GF_EINVAL, "gloc_ptr or delta_out_ptr is NULL");
@@ -349,6 +363,8 @@ gf_status gf_hybridization(gf_ctx* c, const double* mu, const void* gloc, const 
   st = sync_and_check(c);
   if (st == GF_ESINGULAR) return fail(c, GF_ESINGULAR, "G_loc(i w_n) is singular at some frequency");
   return st;
+} catch (...) {
+  return caught(c);
 }
 
 gf_status gf_double_counting(double U, double J, int32_t l, double n, double* u_bar, double* v_dc,
@@ -366,7 +382,7 @@ gf_status gf_double_counting(double U, double J, int32_t l, double n, double* u_
 }
 
 gf_status gf_pole_spectral(gf_ctx* c, const double* mu, int32_t n_eps, const double* eps,
-                           double eta, double* dos_out, double* pdos_out) {
+                           double eta, double* dos_out, double* pdos_out) try {
   NvtxRange nvtx_range_("gf_pole_spectral");
   if (!c) return GF_EINVAL;
   if (n_eps < 1 || !eps || !dos_out) return fail(c, GF_EINVAL, "n_eps >= 1, eps and dos_out required");
@@ -410,9 +426,11 @@ gf_status gf_pole_spectral(gf_ctx* c, const double* mu, int32_t n_eps, const dou
     GF_CU(cudaMemcpyAsync(pdos_out, c->pdos.p, sizeof(double) * (size_t)n_eps * tot_m,
                           cudaMemcpyDefault, c->stream));
   return pole_check(c);
+} catch (...) {
+  return caught(c);
 }
 
-gf_status gf_pole_energy(gf_ctx* c, const double* mu, double* h_ks_out, double* e_ps_out) {
+gf_status gf_pole_energy(gf_ctx* c, const double* mu, double* h_ks_out, double* e_ps_out) try {
   NvtxRange nvtx_range_("gf_pole_energy");
   if (!c) return GF_EINVAL;
   if (!h_ks_out && !e_ps_out) return fail(c, GF_EINVAL, "h_ks_out and e_ps_out are both NULL");
@@ -436,10 +454,12 @@ gf_status gf_pole_energy(gf_ctx* c, const double* mu, double* h_ks_out, double* 
     if (e_ps_out) e_ps_out[s2] = c->hp_sys()[2 * s2 + 1];
   }
   return GF_OK;
+} catch (...) {
+  return caught(c);
 }
 
 gf_status gf_heev_batched(const void* a_dev, int32_t n_mat, int32_t n, int32_t max_sweeps,
-                          double* w_dev, void* v_dev, void* stream) {
+                          double* w_dev, void* v_dev, void* stream) try {
   NvtxRange nvtx_range_("gf_heev_batched");
   if (n_mat < 0 || n < 1 || n > gf::heev_max_n() || max_sweeps < 1 ||
       (n_mat > 0 && (!a_dev || !w_dev || !v_dev))) {
@@ -487,6 +507,8 @@ gf_status gf_heev_batched(const void* a_dev, int32_t n_mat, int32_t n, int32_t m
     return GF_ENOTCONV;
   }
   return GF_OK;
+} catch (...) {
+  return caught(nullptr);
 }
 
 }  // extern "C"

@@ -134,6 +134,9 @@ struct gf_ctx {
   int ev_used = 0;
   // low-rank (eigenbasis) algorithm, GF_FLAG_LOWRANK
   bool lowrank = false, lr_dirty = true;
+  // set by gf_create once the device ordinal is known to be valid: from then on a failed
+  // creation is undone by gf_destroy, before that by a plain delete (no CUDA call)
+  bool device_checked = false;
   DevBuf lr_eps, lr_U, lr_Pt, lr_T, lr_ws;
   // DMFT step and projector construction
   DevBuf eimp, eimp_part, gl_in, delta, wraw, vdc;
@@ -150,6 +153,21 @@ namespace gf_host {
 
 inline gf_status fail(gf_ctx* c, gf_status s, const std::string& msg) {
   if (c) c->err = msg;
+  return s;
+}
+
+// Handler of the function-try-block around every entry point that runs host code able to
+// throw (growth of std::vector and std::string, std::mutex), so that no C++ exception crosses
+// the C ABI: a failed or oversized host allocation becomes GF_ENOMEM, anything else GF_EINVAL.
+// The message goes to the context, or to gf_last_error(NULL) when there is none.
+inline gf_status caught(const gf_ctx* c) noexcept {
+  if (!c) return gf::caught_global();
+  const char* msg = "";
+  const gf_status s = gf::exception_status(&msg);
+  try {
+    const_cast<gf_ctx*>(c)->err = msg;
+  } catch (...) {
+  }
   return s;
 }
 

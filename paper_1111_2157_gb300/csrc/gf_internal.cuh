@@ -5,6 +5,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <new>
+#include <stdexcept>
+
+#include "gf.h"
+
 namespace gf {
 
 constexpr int kThreads = 256;          // threads per CTA of every point kernel
@@ -277,7 +282,34 @@ cudaError_t launch_mubar_reduce(const KInfo* kinfo, const SInfo* sinfo, int n_sy
 // (= -(beta / (2 pi^2)) psi'(n_iw + 1/2)), 0 for tail_order 1.
 double tail_coefficient(double beta, int n_iw, int tail_order);
 
-// Message returned by gf_last_error(NULL) (calls that have no context).
-void set_global_error(const char* msg);
+// Message returned by gf_last_error(NULL) (calls that have no context).  Never throws: if the
+// message cannot be stored the previous one is cleared.
+void set_global_error(const char* msg) noexcept;
+
+// Status of the C++ exception being handled (call only inside a catch block): GF_ENOMEM for a
+// failed or oversized host allocation, GF_EINVAL for anything else; *msg describes it.
+inline gf_status exception_status(const char** msg) noexcept {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    *msg = "host allocation failed";
+    return GF_ENOMEM;
+  } catch (const std::length_error&) {
+    *msg = "host allocation too large";
+    return GF_ENOMEM;
+  } catch (...) {
+    *msg = "unexpected C++ exception in host code";
+    return GF_EINVAL;
+  }
+}
+
+// Handler of the function-try-block around an entry point that has no context: the status of
+// the exception, with its message for gf_last_error(NULL).
+inline gf_status caught_global() noexcept {
+  const char* msg = "";
+  const gf_status s = exception_status(&msg);
+  set_global_error(msg);
+  return s;
+}
 
 }  // namespace gf

@@ -151,7 +151,7 @@ extern "C" gf_status gf_occupation_static(const void* h_dev, const void* p_dev, 
                                           const void* sigma_inf_dev, int32_t n_k, int32_t nb,
                                           int32_t m, int32_t n_iw, double beta, double mu,
                                           int32_t tail_order, void* stream, double* n_out,
-                                          double* dn_dmu_out) {
+                                          double* dn_dmu_out) try {
   gf::set_global_error("");
   if (!h_dev || !p_dev || !sigma_dev || !sigma_inf_dev || !n_out) {
     gf::set_global_error("gf_occupation_static: NULL input or n_out");
@@ -242,4 +242,6 @@ extern "C" gf_status gf_occupation_static(const void* h_dev, const void* p_dev, 
   *n_out = res[0];
   if (dn_dmu_out) *dn_dmu_out = res[1];
   return GF_OK;
+} catch (...) {
+  return gf::caught_global();
 }

@@ -81,3 +81,39 @@ def test_no_cpu_fallback_without_device(lib):
     h = ctypes.c_void_p()
     assert lib.gf_create(ctypes.byref(h), ctypes.byref(d)) == gf.GF_ECUDA
     assert not h.value
+
+
+def _arr(ctype, vals):
+    return (ctype * len(vals))(*vals)
+
+
+@pytest.mark.parametrize("case,message", [
+    ("nb_zero", "N_b(k)"), ("k_system_range", "k_system out of range"),
+    ("k_system_order", "non-decreasing"), ("m_zero", "every m"), ("beta_zero", "beta"),
+    ("empty_system", "no k-points"), ("weight_nan", "k_weight")])
+def test_create_rejects_inconsistent_tables(lib, case, message):
+    """Per-k and per-system tables are checked before any CUDA call; the half-built context is
+    freed and *out stays NULL."""
+    keep = []
+    if case == "nb_zero":
+        kw = dict(nb=_arr(ctypes.c_int32, [8, 8, 0, 8]))
+    elif case == "k_system_range":
+        kw = dict(k_system=_arr(ctypes.c_int32, [0, 0, 1, 1]))
+    elif case == "k_system_order":
+        kw = dict(n_systems=2, k_system=_arr(ctypes.c_int32, [0, 1, 0, 1]),
+                  m_system=_arr(ctypes.c_int32, [5, 5]), beta=_arr(ctypes.c_double, [40.0, 40.0]))
+    elif case == "m_zero":
+        kw = dict(m_system=_arr(ctypes.c_int32, [0]))
+    elif case == "beta_zero":
+        kw = dict(beta=_arr(ctypes.c_double, [0.0]))
+    elif case == "empty_system":
+        kw = dict(n_systems=2, k_system=_arr(ctypes.c_int32, [0, 0, 0, 0]),
+                  m_system=_arr(ctypes.c_int32, [5, 5]), beta=_arr(ctypes.c_double, [40.0, 40.0]))
+    else:
+        kw = dict(k_weight=_arr(ctypes.c_double, [0.25, float("nan"), 0.25, 0.25]))
+    keep.append(kw)
+    d, _ = _desc(**kw)
+    h = ctypes.c_void_p()
+    assert lib.gf_create(ctypes.byref(h), ctypes.byref(d)) == gf.GF_EINVAL
+    assert not h.value
+    assert message in lib.gf_last_error(None).decode()
