@@ -117,3 +117,50 @@ def test_create_rejects_inconsistent_tables(lib, case, message):
     assert lib.gf_create(ctypes.byref(h), ctypes.byref(d)) == gf.GF_EINVAL
     assert not h.value
     assert message in lib.gf_last_error(None).decode()
+
+
+def declared_prototypes():
+    """{name: (return type, [parameter types])} of every prototype in include/*.h."""
+    protos = {}
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", " ", h.read_text(), flags=re.S)
+        for ret, name, params in re.findall(
+                r"^\s*(gf_status|const char \*)\s*(gf_\w+)\s*\(([^;]*?)\)\s*;", text, re.M):
+            types = []
+            for p in " ".join(params.split()).split(","):
+                p = p.strip()
+                if p in ("", "void"):
+                    continue
+                types.append(re.sub(r"\s*\b\w+$", "", p) if not p.endswith("*") else p)
+            protos[name] = (ret, types)
+    return protos
+
+
+def _kind_of_c(t):
+    if "*" in t:
+        return "pointer"
+    return {"int32_t": "int32", "int": "int32", "double": "double"}[t.replace("const ", "").strip()]
+
+
+def _kind_of_ctypes(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "pointer"
+    if t is ctypes.c_int32:
+        return "int32"
+    if t is ctypes.c_double:
+        return "double"
+    return repr(t)
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes argtypes/restype of the binding has the header's arity and the same kind
+    (pointer, int32, double) at each position, so no pointer is truncated to an int."""
+    lib = gf.load()
+    protos = declared_prototypes()
+    assert set(protos) == set(gf.EXPORTS)
+    for name, (ret, params) in sorted(protos.items()):
+        fn = getattr(lib, name)
+        got = [_kind_of_ctypes(t) for t in fn.argtypes]
+        want = [_kind_of_c(t) for t in params]
+        assert got == want, f"{name}: binding {got}, header {want}"
+        assert fn.restype is (ctypes.c_char_p if ret.startswith("const char") else ctypes.c_int), name
