@@ -165,24 +165,21 @@ gf_status autotune(gf_ctx* c, int key, const std::vector<LaunchCfg>& cands, gf::
   for (const LaunchCfg& g : cands) maxgrid = std::max(maxgrid, g.grid);
   const int n_sample = std::min(n_items, 2 * maxgrid);
   p.items = items;
-  cudaEvent_t e0, e1;
-  GF_CU(cudaEventCreate(&e0));
-  GF_CU(cudaEventCreate(&e1));
   std::vector<float> ms(cands.size(), 0.f);
+  ScopedEvents ev;
+  GF_CU(ev.create());
   for (size_t cand = 0; cand < cands.size(); ++cand) {
     for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the module
       GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
-      GF_CU(cudaEventRecord(e0, c->stream));
+      GF_CU(cudaEventRecord(ev.start, c->stream));
       gf_status st = launch_cfg(c, cands[cand], p, n_sample);
       if (st) return st;
-      GF_CU(cudaEventRecord(e1, c->stream));
-      GF_CU(cudaEventSynchronize(e1));
-      GF_CU(cudaEventElapsedTime(&ms[cand], e0, e1));
+      GF_CU(cudaEventRecord(ev.stop, c->stream));
+      GF_CU(cudaEventSynchronize(ev.stop));
+      GF_CU(cudaEventElapsedTime(&ms[cand], ev.start, ev.stop));
       c->last_launches += 1;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   int best = 0;
   for (size_t cand = 1; cand < cands.size(); ++cand)
     if (ms[cand] < ms[best]) best = (int)cand;
@@ -359,6 +356,7 @@ gf_status run_points(gf_ctx* c, int mode) {
       }
       p.items = items_dev;
       GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
+      reserve_events(c, c->ev_used + 2);
       while ((int)c->ev.size() < c->ev_used + 2) {
         cudaEvent_t e;
         GF_CU(cudaEventCreate(&e));
@@ -475,7 +473,15 @@ gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       c->capturing = true;
-      st = enqueue_occupation(c);
+      try {
+        st = enqueue_occupation(c);
+      } catch (...) {
+        // end the capture and give the caller's stream back before the status is reported
+        c->capturing = false;
+        if (cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && graph) cudaGraphDestroy(graph);
+        c->stream = user;
+        throw;
+      }
       c->capturing = false;
       cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
       if (st == GF_OK && e2 != cudaSuccess) e = e2;
@@ -501,12 +507,11 @@ gf_status occupation_impl(gf_ctx* c, const double* mu, double* n_out, double* dn
   }
   GF_CU(cudaEventRecord(c->ev_user, c->stream));
   GF_CU(cudaStreamWaitEvent(c->cap_stream, c->ev_user, 0));
-  if (c->ev.size() < 2) {
-    cudaEvent_t e0, e1;
-    GF_CU(cudaEventCreate(&e0));
-    GF_CU(cudaEventCreate(&e1));
-    c->ev.push_back(e0);
-    c->ev.push_back(e1);
+  reserve_events(c, 2);
+  while (c->ev.size() < 2) {
+    cudaEvent_t e;
+    GF_CU(cudaEventCreate(&e));
+    c->ev.push_back(e);
   }
   GF_CU(cudaEventRecord(c->ev[0], c->cap_stream));
   GF_CU(cudaGraphLaunch(c->occ_exec, c->cap_stream));

@@ -58,6 +58,7 @@ gf_status pole_run(gf_ctx* c, int mode, bool gloc_kernel = true, int warm = 0, i
     GF_CU(ensure(c->pole_ws, sizeof(double2) * (size_t)grid * p.ws_stride));
     p.ws = c->pole_ws.as<double2>();
   }
+  reserve_events(c, c->ev_used + 2);
   while ((int)c->ev.size() < c->ev_used + 2) {
     cudaEvent_t e;
     GF_CU(cudaEventCreate(&e));

@@ -56,6 +56,22 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// A start/stop pair of timing events owned by one scope: destroyed on every return path.
+struct ScopedEvents {
+  cudaEvent_t start = nullptr, stop = nullptr;
+  cudaError_t create() {
+    const cudaError_t e = cudaEventCreate(&start);
+    return e != cudaSuccess ? e : cudaEventCreate(&stop);
+  }
+  ScopedEvents() = default;
+  ScopedEvents(const ScopedEvents&) = delete;
+  ScopedEvents& operator=(const ScopedEvents&) = delete;
+  ~ScopedEvents() {
+    if (start) cudaEventDestroy(start);
+    if (stop) cudaEventDestroy(stop);
+  }
+};
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int d) {
@@ -150,6 +166,12 @@ struct gf_ctx {
 };
 
 namespace gf_host {
+
+// Room for n timing events in c->ev, taken before an event is created so that the push_back
+// which stores it cannot throw and leak it.
+inline void reserve_events(gf_ctx* c, int n) {
+  if (c->ev.capacity() < (size_t)n) c->ev.reserve(std::max<size_t>(2 * (size_t)n, 16));
+}
 
 inline gf_status fail(gf_ctx* c, gf_status s, const std::string& msg) {
   if (c) c->err = msg;
