@@ -25,6 +25,16 @@ MUTATIONS = {
                                "for (int c = 0; c < m; c++) s += Ak[a * m + c] * Mt[c * m + b];"),
     "lu_update_sign": ("for (int c = j + 1; c < n; c++) a[i * n + c] -= l * a[j * n + c];",
                        "for (int c = j + 1; c < n; c++) a[i * n + c] += l * a[j * n + c];"),
+    "matsubara_factor_halved": ("cplx v = (acc[i * n + j] + conj(acc[j * n + i])) / beta;",
+                                "cplx v = (acc[i * n + j] + conj(acc[j * n + i])) / (2.0 * beta);"),
+    "rho_not_hermitian_part": ("cplx v = (acc[i * n + j] + conj(acc[j * n + i])) / beta;",
+                               "cplx v = (acc[i * n + j] + conj(acc[i * n + j])) / beta;"),
+    "second_tail_sign": ("if (tail_order >= 2) tail += M2[i * n + j] / (iw * iw);",
+                         "if (tail_order >= 2) tail -= M2[i * n + j] / (iw * iw);"),
+    "dndmu_missing_closed_tail": ("if (tail_order >= 2) dn += 0.25 * beta * n;", ""),
+    "gloc_unweighted": ("for (size_t q = 0; q < mm; q++) acc[q] += wk[k] * Q[q];",
+                        "for (size_t q = 0; q < mm; q++) acc[q] += Q[q];"),
+    "occupation_unweighted": ("partN[3 * t + 0] += wk[k] * tr;", "partN[3 * t + 0] += tr;"),
 }
 
 
