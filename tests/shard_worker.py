@@ -37,12 +37,13 @@ def oracle_slice_evaluator(o, s, k0, k1):
     return evaluate
 
 
-def run(rank, world_size, port, out_path):
+def run(rank, world_size, port, out_path, parts=None):
+    """parts: explicit k-slices per rank (e.g. one left empty), else the cost-balanced ones."""
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world_size, timeout=datetime.timedelta(seconds=60))
     try:
         s = sharded_case()
-        k0, k1 = shard.partition_k(s.nb, world_size)[rank]
+        k0, k1 = (parts or shard.partition_k(s.nb, world_size))[rank]
         lat = shard.ShardedLattice(oracle_slice_evaluator(oracle.get(), s, k0, k1))
         mu, evals = lat.find_mu(s.n_target, mu0=0.0, tol=1e-11)
         g, n, dn = lat.evaluate(mu, gloc=True)

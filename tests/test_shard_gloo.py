@@ -33,13 +33,15 @@ def _free_port():
         return sk.getsockname()[1]
 
 
-@pytest.mark.parametrize("world_size", [2])
-def test_two_rank_lattice_sum_and_mu_search_match_single_process(tmp_path, world_size):
+@pytest.mark.parametrize("world_size,parts", [(2, None), (3, None), (2, [(0, 24), (24, 24)])],
+                         ids=["two_ranks", "three_ranks", "one_rank_empty"])
+def test_sharded_lattice_sum_and_mu_search_match_single_process(tmp_path, world_size, parts):
     out = tmp_path / "rank0.npz"
-    tmp.start_processes(shard_worker.run, args=(world_size, _free_port(), str(out)),
+    tmp.start_processes(shard_worker.run, args=(world_size, _free_port(), str(out), parts),
                         nprocs=world_size, join=True, start_method="spawn")
     r = np.load(out)
-    assert r["k1"] > r["k0"] > -1 and r["k1"] < 24  # rank 0 holds a proper part of the k-points
+    if parts is None:
+        assert r["k1"] > r["k0"] > -1 and r["k1"] < 24  # rank 0 holds a proper part of the k-points
     s = shard_worker.sharded_case()
     o = oracle.get()
     mu = float(r["mu"][0])
