@@ -57,7 +57,20 @@ typedef enum {
     GF_ESTATE = 7      /* inputs missing (e.g. gf_local before gf_set_sigma)        */
 } gf_status;
 
-typedef enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1 } gf_precision;
+/* Arithmetic of the (k, i w_n) point kernels.  Reductions over k and n, the
+ * Matsubara tail and the mu search run in FP64 in every mode.
+ *  GF_PREC_FP64  embedding, inverse and projections in FP64.
+ *  GF_PREC_MIXED embedding and Gauss-Jordan inverse in single-word FP32
+ *                (register tiles, windows up to 128 bands; wider windows use
+ *                the GF_PREC_PAIR kernels), the Matsubara sums of G in FP64;
+ *                the columns of G that G_loc and the adjoint consume
+ *                (G P^+ and P G) get one step of iterative refinement with a
+ *                residual in FP32 pairs.  Errors against FP64: about
+ *                kappa(A) 2^-24 per G entry before refinement, which averages
+ *                to ~1e-9 relative on N(mu); ~1e-11 on G_loc after it.
+ *  GF_PREC_PAIR  every matrix entry an FP32 pair (hi + lo) with error-free
+ *                transformations on the FP32 pipes: ~1e-14 of FP64 results. */
+typedef enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1, GF_PREC_PAIR = 2 } gf_precision;
 typedef enum { GF_C128 = 0, GF_C64 = 1 } gf_dtype;
 
 typedef struct {
@@ -89,9 +102,9 @@ typedef struct {
  * (Woodbury identity): H_k = U diag(eps) U^+ is diagonalised once per
  * Hamiltonian upload (batched Jacobi kernel), after which a point costs
  * 3 N_b m^2 + O(m^3) complex multiply-adds instead of N_b^3.  Same results as
- * the direct inverse up to rounding; N_b <= 256.  With GF_PREC_MIXED the band
- * sums of g0, g1, g2 (the N_b m^2 part) run in FP32-pair arithmetic and the
- * m x m algebra in FP64.  With
+ * the direct inverse up to rounding; N_b <= 256.  With GF_PREC_MIXED or
+ * GF_PREC_PAIR the band sums of g0, g1, g2 (the N_b m^2 part) run in FP32-pair
+ * arithmetic and the m x m algebra in FP64.  With
  * GF_FLAG_GRAPH the eigen-decomposition runs outside the replayed graph, once
  * after each upload of H or P.  U^+ G U = D + D Pt^+ K Pt D with D = diag(1/(i w + mu - eps)),
  * Pt = P_k U, K = (I - Sigma Pt D Pt^+)^{-1} Sigma. */

@@ -99,8 +99,9 @@ gf_status check_ready(gf_ctx* c) {
 
 // Kernel configuration of one launch, i.e. of one bucket of band-window sizes.
 struct LaunchCfg {
-  int kind = 0;        // 0 FP64, 1 FP32-pair shared-memory, 2 FP32-pair register-resident
-  int shape = -1;      // register tile shape (kind 2)
+  int kind = 0;        // 0 FP64, 1 FP32-pair shared-memory, 2 FP32-pair register-resident,
+                       // 3 low-rank, 4 FP32 register-resident with refined projections
+  int shape = -1;      // register tile shape (kinds 2 and 4)
   int threads = gf::kThreads;
   size_t smem = 0;
   int grid = 1;
@@ -122,11 +123,12 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
   const int grid = std::min(cfg.grid, std::max(1, n_items));
   if (cfg.kind == 3) {
     gf::LowRank lr{c->lr_eps.as<double>(), c->offD_d.as<int64_t>(), c->lr_Pt.as<double2>(),
-                   cfg.pair_table, c->precision == GF_PREC_MIXED ? 1 : 0};
+                   cfg.pair_table, c->precision != GF_PREC_FP64 ? 1 : 0};
     GF_CU(gf::launch_point_lr(p, lr, grid, cfg.smem, c->stream));
     return GF_OK;
   }
-  if (cfg.kind == 2) GF_CU(gf::launch_point_df64r(cfg.shape, p, grid, cfg.threads, cfg.smem, c->stream));
+  if (cfg.kind == 4) GF_CU(gf::launch_point_f32r(cfg.shape, p, grid, cfg.threads, cfg.smem, c->stream));
+  else if (cfg.kind == 2) GF_CU(gf::launch_point_df64r(cfg.shape, p, grid, cfg.threads, cfg.smem, c->stream));
   else if (cfg.kind == 1) GF_CU(gf::launch_point_df64(p, grid, cfg.smem, c->stream));
   else GF_CU(gf::launch_point_fp64(p, grid, cfg.smem, c->stream));
   return GF_OK;
@@ -134,7 +136,10 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
 
 std::string cfg_name(const LaunchCfg& g) {
   char buf[96];
-  if (g.kind == 2)
+  if (g.kind == 4)
+    std::snprintf(buf, sizeof(buf), "FP32 register %dx%d tiles x %d threads, %d CTAs",
+                  gf::f32r_tile(g.shape, 0), gf::f32r_tile(g.shape, 1), g.threads, g.grid);
+  else if (g.kind == 2)
     std::snprintf(buf, sizeof(buf), "register %dx%d tiles x %d threads", gf::df64r_tile(g.shape, 0),
                   gf::df64r_tile(g.shape, 1), g.threads);
   else
@@ -200,12 +205,34 @@ gf_status autotune(gf_ctx* c, int key, const std::vector<LaunchCfg>& cands, gf::
 // Candidate launch configurations for the items of one window bucket (largest
 // window nbmax): the point kernel of the context's precision with the matrix in
 // shared memory (when it fits) and in an L2-resident global slice (more CTAs per
-// SM), and in the mixed path the register-resident kernel (windows <= 96).
+// SM), and with FP32 pairs the register-resident kernel (windows <= 96).  The
+// mixed path takes the single-word FP32 register kernel for windows up to 128
+// (falling back to the FP32-pair kernels above that).
 gf_status choose_cfg(gf_ctx* c, int mode, int bucket, int nbmax, const gf::PointParams& p,
                      const Item* items, int n_items, LaunchCfg* cfg) {
   const size_t limit = (size_t)c->smem_optin - 1024;
-  const int kind = (c->precision == GF_PREC_MIXED) ? 1 : 0;
   std::vector<LaunchCfg> cands;
+  if (c->precision == GF_PREC_MIXED) {
+    // single-word FP32 register tiles for every shape that serves the window
+    for (int sh = 0; sh < gf::f32r_num_shapes(); ++sh) {
+      if (!gf::f32r_shape_fits(sh, nbmax)) continue;
+      LaunchCfg f;
+      f.kind = 4;
+      f.shape = sh;
+      f.nbmax = nbmax;
+      f.threads = gf::f32r_threads(sh, nbmax);
+      f.smem = gf::point_f32r_smem(nbmax, c->mmax, mode);
+      f.a_in_smem = 1;
+      if (f.smem > limit) continue;
+      const int bps = gf::point_f32r_blocks_per_sm(sh, f.threads, f.smem);
+      if (bps < 1) continue;
+      f.grid = c->sm_count * bps;
+      cands.push_back(f);
+    }
+    if (!cands.empty()) return autotune(c, mode * 8 + bucket, cands, p, items, n_items, cfg);
+    // windows above the register tiles: the FP32-pair kernels below
+  }
+  const int kind = (c->precision == GF_PREC_FP64) ? 0 : 1;
   for (int in_smem = 1; in_smem >= 0; --in_smem) {
     LaunchCfg a;
     a.nbmax = nbmax;
@@ -274,7 +301,7 @@ gf_status run_points(gf_ctx* c, int mode) {
   GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
   st = ensure_lr(c);
   if (st) return st;
-  const bool df64 = (c->precision == GF_PREC_MIXED);
+  const bool df64 = (c->precision != GF_PREC_FP64);
   gf::PointParams p{};
   p.H = c->H.as<double2>();
   p.P = c->P.as<double2>();
@@ -283,6 +310,11 @@ gf_status run_points(gf_ctx* c, int mode) {
     p.Hd = c->Hd.as<float4>();
     p.Pd = c->Pd.as<float4>();
     p.Sd = c->Sd.as<float4>();
+  }
+  if (c->precision == GF_PREC_MIXED) {
+    p.Hs = c->Hs.as<float2>();
+    p.Ps = c->Ps.as<float2>();
+    p.Ss = c->Ss.as<float2>();
   }
   p.kinfo = c->kinfo_d.as<KInfo>();
   p.sinfo = c->sinfo_d.as<SInfo>();
@@ -339,7 +371,7 @@ gf_status run_points(gf_ctx* c, int mode) {
         cfg.kind = 3;
         cfg.nbmax = c->bucket_nbmax[bucket];
         const size_t lim = (size_t)c->smem_optin - 1024;
-        const int ps = c->precision == GF_PREC_MIXED ? 1 : 0;  // FP32-pair band sums
+        const int ps = c->precision != GF_PREC_FP64 ? 1 : 0;  // FP32-pair band sums
         const size_t s0 = gf::point_lr_smem(cfg.nbmax, c->mmax, mode, 0, ps);
         const size_t s1 = gf::point_lr_smem(cfg.nbmax, c->mmax, mode, 1, ps);
         if (s0 > lim)
@@ -641,7 +673,7 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
   for (int in_smem = 0; in_smem <= 1; ++in_smem) {
     const size_t smem = gf::point_fp64_smem(c->nbmax, c->mmax, gf::kOcc, in_smem);
     if (smem <= (size_t)c->smem_optin - 1024)
-      bps = std::max(bps, (c->precision == GF_PREC_MIXED) ? gf::point_df64_blocks_per_sm(smem)
+      bps = std::max(bps, (c->precision != GF_PREC_FP64) ? gf::point_df64_blocks_per_sm(smem)
                                                           : gf::point_fp64_blocks_per_sm(smem));
   }
   int n_buckets = 0;
@@ -686,10 +718,15 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
     if ((e = ensure(c->Sig, sizeof(double2) * c->totSig))) return e;
     if ((e = ensure(c->gacc, sizeof(double2) * c->totSig))) return e;
     if ((e = ensure(c->Sinf, sizeof(double2) * c->totSinf))) return e;
-    if (c->precision == GF_PREC_MIXED) {
+    if (c->precision != GF_PREC_FP64) {
       if ((e = ensure(c->Hd, sizeof(float4) * c->totH))) return e;
       if ((e = ensure(c->Pd, sizeof(float4) * c->totP))) return e;
       if ((e = ensure(c->Sd, sizeof(float4) * c->totSig))) return e;
+    }
+    if (c->precision == GF_PREC_MIXED) {
+      if ((e = ensure(c->Hs, sizeof(float2) * c->totH))) return e;
+      if ((e = ensure(c->Ps, sizeof(float2) * c->totP))) return e;
+      if ((e = ensure(c->Ss, sizeof(float2) * c->totSig))) return e;
     }
     if ((e = ensure(c->trHE, sizeof(double) * c->n_k))) return e;
     if ((e = ensure(c->kN, sizeof(double) * c->n_k))) return e;
@@ -768,7 +805,8 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) try {
   if (!d->m_system) return bad("m_system is NULL");
   if (!d->beta) return bad("beta is NULL");
   if (!d->nb && d->nb_uniform < 1) return bad("nb is NULL and nb_uniform < 1");
-  if (d->precision != GF_PREC_FP64 && d->precision != GF_PREC_MIXED) return bad("bad precision");
+  if (d->precision != GF_PREC_FP64 && d->precision != GF_PREC_MIXED && d->precision != GF_PREC_PAIR)
+    return bad("bad precision");
   if (d->input_dtype != GF_C128 && d->input_dtype != GF_C64) return bad("bad input_dtype");
   if (d->tail_order != 1 && d->tail_order != 2) return bad("tail_order must be 1 or 2");
   gf_ctx* c = new (std::nothrow) gf_ctx();
@@ -842,8 +880,9 @@ gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) try 
     if (st) return st;
     GF_CU(cudaStreamSynchronize(c->stream));
   }
-  if (c->precision == GF_PREC_MIXED) {
-    GF_CU(gf::launch_split_df64(c->H.as<double2>(), c->Hd.as<float4>(), c->totH, c->stream));
+  if (c->precision != GF_PREC_FP64) {
+    gf_status st = derive_f32(c, c->H, c->Hd, &c->Hs, c->totH);
+    if (st) return st;
     GF_CU(cudaStreamSynchronize(c->stream));
   }
   c->have_H = true;
@@ -861,8 +900,8 @@ gf_status gf_set_projectors(gf_ctx* c, const void* p) try {
   DeviceGuard guard(c->device);
   gf_status st = load_complex(c, p, c->totP, c->P.as<double2>());
   if (st) return st;
-  if (c->precision == GF_PREC_MIXED)
-    GF_CU(gf::launch_split_df64(c->P.as<double2>(), c->Pd.as<float4>(), c->totP, c->stream));
+  st = derive_f32(c, c->P, c->Pd, &c->Ps, c->totP);
+  if (st) return st;
   GF_CU(cudaStreamSynchronize(c->stream));
   c->have_P = true;
   c->lr_dirty = true;
@@ -881,8 +920,8 @@ gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) try {
   if (st) return st;
   st = load_complex(c, sinf, c->totSinf, c->Sinf.as<double2>());
   if (st) return st;
-  if (c->precision == GF_PREC_MIXED)
-    GF_CU(gf::launch_split_df64(c->Sig.as<double2>(), c->Sd.as<float4>(), c->totSig, c->stream));
+  st = derive_f32(c, c->Sig, c->Sd, &c->Ss, c->totSig);
+  if (st) return st;
   GF_CU(cudaStreamSynchronize(c->stream));
   c->have_S = true;
   c->einf_dirty = true;
@@ -1052,7 +1091,7 @@ gf_status gf_backward(gf_ctx* c, const double* mu, const void* gbar, const doubl
   if (gbar) {
     GF_CU(ensure(c->gbar, sizeof(double2) * c->totSig));
     GF_CU(cudaMemcpyAsync(c->gbar.p, gbar, sizeof(double2) * c->totSig, cudaMemcpyDefault, c->stream));
-    if (c->precision == GF_PREC_MIXED) {
+    if (c->precision != GF_PREC_FP64) {
       GF_CU(ensure(c->Gbd, sizeof(float4) * c->totSig));
       GF_CU(gf::launch_split_df64(c->gbar.as<double2>(), c->Gbd.as<float4>(), c->totSig, c->stream));
     }

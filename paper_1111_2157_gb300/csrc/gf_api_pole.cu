@@ -291,8 +291,8 @@ gf_status gf_set_projectors_lowdin(gf_ctx* c, const void* w, void* p_out) try {
   GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
   GF_CU(gf::launch_lowdin(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_k, c->mmax,
                           c->wraw.as<double2>(), c->P.as<double2>(), c->status.as<int>(), c->stream));
-  if (c->precision == GF_PREC_MIXED)
-    GF_CU(gf::launch_split_df64(c->P.as<double2>(), c->Pd.as<float4>(), c->totP, c->stream));
+  st = derive_f32(c, c->P, c->Pd, &c->Ps, c->totP);
+  if (st) return st;
   if (p_out)
     GF_CU(cudaMemcpyAsync(p_out, c->P.p, sizeof(double2) * c->totP, cudaMemcpyDefault, c->stream));
   st = sync_and_check(c);

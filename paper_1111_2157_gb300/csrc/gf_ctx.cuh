@@ -119,7 +119,8 @@ struct gf_ctx {
   DevBuf H, P, Sig, Sinf, Einf, trHE, kinfo_d, sinfo_d, items_d, offD_d, mu, nbar, gbar, status,
       queue, stage, occ_part, rho_part, rho_out, gq, kN, kdN, kNc, sysout, a_scratch, mubar_part,
       mubar_sys, gacc, sysout2;
-  DevBuf Hd, Pd, Sd, Gbd;  // FP32-pair copies for the mixed path
+  DevBuf Hd, Pd, Sd, Gbd;  // FP32-pair copies (GF_PREC_MIXED and GF_PREC_PAIR)
+  DevBuf Hs, Ps, Ss;       // single-word FP32 copies (GF_PREC_MIXED)
   bool have_H = false, have_P = false, have_S = false, einf_dirty = true;
   bool have_gbar_for_call = false;
   // pinned host staging: mu [S] | n_bar [S] | status | outputs [2S] | mu_bar [S] | outputs [2S]
@@ -212,6 +213,16 @@ inline gf_status load_complex(gf_ctx* c, const void* src, int64_t n, double2* ds
     GF_CU(cudaMemcpyAsync(c->stage.p, src, (size_t)n * 8, cudaMemcpyDefault, c->stream));
     GF_CU(gf::launch_upcast(c->stage.as<float2>(), dst, n, c->stream));
   }
+  return GF_OK;
+}
+
+// FP32 copies of an uploaded input (n complex numbers in src): FP32 pairs for
+// GF_PREC_MIXED and GF_PREC_PAIR, and single words for GF_PREC_MIXED.
+inline gf_status derive_f32(gf_ctx* c, const DevBuf& src, DevBuf& pair, DevBuf* single, int64_t n) {
+  if (c->precision == GF_PREC_FP64 || n <= 0) return GF_OK;
+  GF_CU(gf::launch_split_df64(src.as<double2>(), pair.as<float4>(), n, c->stream));
+  if (c->precision == GF_PREC_MIXED && single)
+    GF_CU(gf::launch_round_f32(src.as<double2>(), single->as<float2>(), n, c->stream));
   return GF_OK;
 }
 

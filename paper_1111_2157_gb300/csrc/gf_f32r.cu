@@ -1,0 +1,751 @@
+// Mixed-precision point kernel of the lattice Green's function path (sm_103a):
+// single-word FP32 Gauss-Jordan inverse held in registers, FP64 Matsubara sums,
+// and one step of iterative refinement, with an FP32-pair residual, of the
+// columns of G that the projections consume.
+//
+// Arithmetic per (k, i w_n) point:
+//   1. A = (i w_n + mu) I - H_k - P_k^+ (Sigma(i w_n) P_k)  in FP32 (Eq. dmftloop1);
+//      the diagonal mu - H_ii is formed in FP64 and rounded once.
+//   2. X = A^{-1} by Gauss-Jordan elimination with partial pivoting in FP32.
+//      On GB300 one SM issues 128 FP32 FMAs per clock against 2 FP64 FMAs, so
+//      this costs about 1/64 of the FP64 inverse; its error is about
+//      kappa(A) * 2^-24 relative per entry.
+//   3. Epilogues:
+//      kOcc  Re Tr X and Re Tr X^2, summed over the frequencies in FP64    -> N, dN/dmu
+//      kRho  S_k += X in FP64                                             -> rho_k
+//      kGloc Y = X P^+ refined once: R = P^+ - A Y in FP32 pairs (A from the
+//            FP32-pair copies of H, P and Sigma), Y += X R in FP32; then
+//            w_k P Y with P Y0 in pairs                                   -> G_loc
+//      kAdj  the same refinement of Z = P X (R' = P - Z A), then A_k = P Y,
+//            B_k = Z Y and w_k [A^+ Gbar A^+ + nbar (2/beta) B^+] in pairs
+// One refinement step leaves an error of about (kappa 2^-24)^2 plus the pair
+// residual's 2^-44 kappa, far below the FP32 inverse's own, for the m
+// columns that G_loc and the adjoint use (m << N_b), at 2 N_b^2 m extra
+// multiply-adds instead of the N_b^3 of refining the whole inverse.
+//
+// Thread layout: the CTA is warp 0 (pivot lookahead) plus a TR x TC grid of
+// owners; owner (tr, tc) holds the RA x RB entries (tr + TR a, tc + TC b) of A
+// in registers.  A pivot step reads RA multipliers and RB pivot-row entries
+// from shared memory (broadcast) for RA RB register updates; warp 0 updates the
+// next column, searches its pivot and forms the reciprocal meanwhile (one pivot
+// of lookahead, two barriers per pivot).  After the inverse the tile is written
+// once to shared memory (columns permuted by the pivot sequence) for the
+// epilogues.
+#include <math.h>
+#include <stdint.h>
+
+#include "gf_complex.cuh"
+#include "gf_internal.cuh"
+
+namespace gf {
+
+namespace {
+
+using namespace cx;
+
+constexpr int kMaxWarpsF = 18;
+
+__device__ __forceinline__ double block_sum_f(double v, double* red) {
+  // Deterministic: fixed xor tree in each warp, then warp 0 over the warps.
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < nw ? red[lane] : 0.0;
+    for (int off = 16; off; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+  }
+  return r;
+}
+
+__device__ __forceinline__ float2 f2zero() { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ float2 fneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ cf conj_cf(const cf& a) { return cf{a.rh, a.rl, -a.ih, -a.il}; }
+// Pivot key with the row index in its low 7 bits (rows < 128): the largest key
+// wins, ties (and keys equal to 2^-16 relative) go to the lowest row.
+__device__ __forceinline__ unsigned pack_key(float2 v, int i) {
+  return (pivot_key_s(v) & ~127u) | (unsigned)(127 - i);
+}
+__device__ __forceinline__ float2 round_cf(const cf& a) {
+  return make_float2(__fadd_rn(a.rh, a.rl), __fadd_rn(a.ih, a.il));
+}
+
+}  // namespace
+
+// Shared-memory layout of k_point_f32r in bytes.  T = Sigma P (embedding) lives in
+// the G region, which is free until the inverse is written there.
+struct LayoutF {
+  size_t oP, oS, oG, oT, oB, oD, oHii, oY0, oR, odY, oW, oV, oZ0, odZ, oQa, oQb, oMt, oPiv, bytes;
+};
+
+// Length of the pivot-step buffers: the register tiles cover TR RA and TC RB
+// rows and columns, up to nbmax + 7 (RA, RB <= 8).
+__host__ __device__ inline int f32r_nbp(int nbmax) { return nbmax + 8; }
+
+__host__ __device__ inline LayoutF make_layout_f(int nbmax, int mmax, int mode) {
+  LayoutF L;
+  const size_t ld = (size_t)(nbmax | 1);
+  const size_t mn = (size_t)mmax * nbmax, mm = (size_t)mmax * mmax;
+  size_t o = 0;
+  L.oP = o; o += 8 * mn;
+  L.oS = o; o += 8 * mm;
+  L.oG = o;
+  size_t g = (size_t)nbmax * ld;
+  if (g < mn) g = mn;
+  if (g < mm) g = mm;
+  o += 8 * g;
+  L.oT = L.oG;
+  L.oB = o; o += 8 * 6 * (size_t)f32r_nbp(nbmax);  // l, u, next column; two buffers each
+  L.oD = o; o += 8 * (size_t)nbmax;                  // diagonal i w_n + mu - H_ii (FP32)
+  o = (o + 15) & ~(size_t)15;
+  L.oHii = o; o += 16 * (size_t)nbmax;               // H_ii (FP64)
+  const bool refine = (mode & (kGloc | kAdj)) != 0;
+  o = (o + 15) & ~(size_t)15;
+  L.oW = o; o += refine ? 16 * mm : 0;   // P Y0 (pair), then Z0 P^+
+  L.oV = o; o += refine ? 16 * mm : 0;   // Sigma (P Y0) (pair)
+  L.oY0 = o; o += refine ? 8 * mn : 0;   // Y0 = X P^+ (N x m)
+  L.oR = o; o += refine ? 8 * mn : 0;    // residual (N x m or m x N)
+  L.odY = o; o += refine ? 8 * mn : 0;   // X R
+  const bool adj = (mode & kAdj) != 0;
+  L.oZ0 = o; o += adj ? 8 * mn : 0;      // Z0 = P X (m x N)
+  L.odZ = o; o += adj ? 8 * mn : 0;      // R' X
+  L.oQa = o; o += adj ? 16 * mm : 0;     // A_k = P Y (pair)
+  L.oQb = o; o += adj ? 16 * mm : 0;     // B_k = Z Y (pair)
+  L.oMt = o; o += adj ? 16 * mm : 0;     // Gbar A_k^+ (pair)
+  L.oPiv = o; o += 3 * sizeof(int) * (size_t)nbmax;  // p, q = p^{-1}, row offsets
+  L.bytes = o;
+  return L;
+}
+
+namespace {
+
+template <int RA, int RB, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_point_f32r(const PointParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_item;
+  __shared__ int s_p[2], s_pq[2], s_pm[2];  // pivot row, its tile index p / TR and p % TR
+  __shared__ float2 s_r[2];
+  __shared__ double s_red[kMaxWarpsF];
+  const LayoutF L = make_layout_f(p.nbmax, p.mmax, p.mode);
+  float2* sP = reinterpret_cast<float2*>(smraw + L.oP);
+  float2* sS = reinterpret_cast<float2*>(smraw + L.oS);
+  float2* sG = reinterpret_cast<float2*>(smraw + L.oG);
+  float2* sT = reinterpret_cast<float2*>(smraw + L.oT);
+  float2* sB = reinterpret_cast<float2*>(smraw + L.oB);
+  float4* sW = reinterpret_cast<float4*>(smraw + L.oW);
+  float4* sV = reinterpret_cast<float4*>(smraw + L.oV);
+  float2* sY0 = reinterpret_cast<float2*>(smraw + L.oY0);
+  float2* sR = reinterpret_cast<float2*>(smraw + L.oR);
+  float2* sdY = reinterpret_cast<float2*>(smraw + L.odY);
+  float2* sZ0 = reinterpret_cast<float2*>(smraw + L.oZ0);
+  float2* sdZ = reinterpret_cast<float2*>(smraw + L.odZ);
+  float4* sQa = reinterpret_cast<float4*>(smraw + L.oQa);
+  float4* sQb = reinterpret_cast<float4*>(smraw + L.oQb);
+  float4* sMt = reinterpret_cast<float4*>(smraw + L.oMt);
+  float2* sD = reinterpret_cast<float2*>(smraw + L.oD);
+  double2* sHii = reinterpret_cast<double2*>(smraw + L.oHii);
+  int* sPiv = reinterpret_cast<int*>(smraw + L.oPiv);
+  int* sIdx = sPiv + p.nbmax;
+  int* sRow = sIdx + p.nbmax;
+  const int nbp = f32r_nbp(p.nbmax);
+  float2* bCol = sB;
+  float2* bU = sB + 2 * nbp;
+  float2* bCx = sB + 4 * nbp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthr = blockDim.x;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1);
+    __syncthreads();
+    const int itx = s_item;
+    if (itx >= p.n_items) break;
+    const Item it = p.items[itx];
+    const KInfo ki = p.kinfo[it.k];
+    const SInfo si = p.sinfo[ki.sys];
+    const int N = ki.nb, M = si.m, ld = N | 1;
+    const int TR = (N + RA - 1) / RA, TC = (N + RB - 1) / RB;
+    const int ot = tid - 32;  // warp 0 owns no tile: it runs the pivot lookahead
+    const bool owner = ot >= 0 && ot < TR * TC;
+    const int tr = owner ? ot / TC : 0, tc = owner ? ot - (ot / TC) * TC : 0;
+    const float2* Hk = p.Hs + ki.offH;
+    const double2* Hk64 = p.H + ki.offH;
+    const float4* Hkp = p.Hd + ki.offH;
+    const float4* Pkp = p.Pd + ki.offP;
+    const double mu = p.mu[ki.sys];
+    const double beta = si.beta;
+    const double wk = ki.w;
+    double nbar = 0.0;
+    if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
+    for (int e = tid; e < M * N; e += nthr) sP[e] = p.Ps[ki.offP + e];
+    for (int i = tid; i < N; i += nthr) sHii[i] = Hk64[i * N + i];
+    for (int i = tid; i < 2 * nbp; i += nthr) bCol[i] = f2zero();  // zero tails of l
+    const double pib = M_PI / beta;
+
+    double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
+    for (int n = it.n0; n < it.n1; ++n) {
+      const double wn = (2.0 * n + 1.0) * pib;
+      __syncthreads();  // previous epilogue done with the shared buffers
+      for (int e = tid; e < M * M; e += nthr) sS[e] = p.Ss[si.offSig + (int64_t)n * M * M + e];
+      __syncthreads();
+      // T = Sigma(i w_n) P_k  (M x N), in the G region
+      for (int e = tid; e < M * N; e += nthr) {
+        const int a = e / N, j = e - a * N;
+        float2 acc = f2zero();
+        for (int b = 0; b < M; ++b) fmac(acc, sS[a * M + b], sP[b * N + j]);
+        sT[e] = acc;
+      }
+      for (int i = tid; i < N; i += nthr)
+        sD[i] = make_float2(__double2float_rn(mu - sHii[i].x), __double2float_rn(wn - sHii[i].y));
+      __syncthreads();
+      // A = (i w_n + mu) I - H_k - P_k^+ T in the owners' registers; the diagonal
+      // (i w_n + mu - H_ii) comes from sD, formed in FP64 and rounded once
+      float2 A[RA][RB];
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+          const int i = tr + TR * a, c = tc + TC * b;
+          float2 v = f2zero();
+          if (owner && i < N && c < N) v = (i == c) ? sD[i] : fneg(Hk[i * N + c]);
+          A[a][b] = v;
+        }
+      if (owner) {
+        for (int x = 0; x < M; ++x) {
+          float2 pv[RA];
+#pragma unroll
+          for (int a = 0; a < RA; ++a) {
+            const int i = tr + TR * a;
+            pv[a] = (i < N) ? fneg(sP[x * N + i]) : f2zero();
+          }
+#pragma unroll
+          for (int b = 0; b < RB; ++b) {
+            const int c = tc + TC * b;
+            const float2 tv = (c < N) ? sT[x * N + c] : f2zero();
+#pragma unroll
+            for (int a = 0; a < RA; ++a) fmac_ca(A[a][b], pv[a], tv);
+          }
+        }
+      }
+      // Gauss-Jordan elimination with partial pivoting, without row interchanges
+      // (the exchange or sweep form of the elimination): step j pivots on
+      // (p_j, j), p_j the unused row of largest |A[i][j]|, so that afterwards
+      // X[i][c] = B[p_i][q_c] with q the inverse permutation of p.  Every step is
+      // one uniform rank-1 update of the whole tile,
+      //   A[i][c] -= l[i] u[c],  u = A[p][.] / A[p][j] with u[j] = 1/A[p][j],
+      //   l[i] = A[i][j] (i != p), l[p] = -1,
+      // after the owners of row p and of column j have zeroed them (so that row p
+      // becomes u and column j becomes -l u[j]).  Phases per step:
+      //  (R) owners of row p publish u and zero the row, owners of column j zero
+      //      it, owners of column j+1 publish it (cx);
+      //  (U) owners update their tiles; warp 0 applies the same update to cx,
+      //      picks p_{j+1} among the unused rows and forms the next l and
+      //      1/pivot (one pivot of lookahead).  Two barriers per step.
+      if (owner && tc == 0) {
+#pragma unroll
+        for (int a = 0; a < RA; ++a) bCx[nbp + tr + TR * a] = A[a][0];
+      }
+      __syncthreads();
+      unsigned used = 0u;  // warp 0: bit t marks row lane + 32 t as a pivot row already
+      if (warp == 0) {
+        const float2* cx0 = bCx + nbp;
+        float2 v[4];
+        unsigned best = 0u;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = lane + 32 * t;
+          v[t] = (i < N) ? cx0[i] : f2zero();
+          if (i < N) best = max(best, pack_key(v[t], i));
+        }
+        best = __reduce_max_sync(0xffffffffu, best);
+        // a zero or non-finite pivot is flagged; the row index stays in range
+        const int bi = min(127 - (int)(best & 127u), N - 1);
+        if (lane == 0 && ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u))
+          atomicOr(p.status, kFlagSingular);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = lane + 32 * t;
+          if (i < N) bCol[i] = (i == bi) ? make_float2(-1.f, 0.f) : v[t];
+          if (i == bi) {
+            used |= 1u << t;
+            s_r[0] = frcp(v[t]);
+            s_p[0] = bi;
+            s_pq[0] = bi / TR;
+            s_pm[0] = bi - (bi / TR) * TR;
+            sPiv[0] = bi;
+          }
+        }
+      }
+      __syncthreads();
+      int jqc = 0, jmc = 0;                                 // j / TC, j % TC
+      int nqc = (TC > 1) ? 0 : 1, nmc = (TC > 1) ? 1 : 0;  // (j+1) / TC, (j+1) % TC
+      for (int j = 0; j < N; ++j) {
+        const int bf = j & 1;
+        const float2* col = bCol + bf * nbp;
+        float2* urow = bU + bf * nbp;
+        float2* cxb = bCx + bf * nbp;
+        const int prq = s_pq[bf], prm = s_pm[bf];
+        const float2 r = s_r[bf];
+        const int jn = j + 1;
+        if (owner) {
+          if (tr == prm) {
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+              if (a == prq) {
+#pragma unroll
+                for (int b = 0; b < RB; ++b) {
+                  const int c = tc + TC * b;
+                  urow[c] = (c == j) ? r : fmul(A[a][b], r);
+                  A[a][b] = f2zero();
+                }
+              }
+          }
+          if (tc == jmc) {
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+              if (b == jqc) {
+#pragma unroll
+                for (int a = 0; a < RA; ++a) A[a][b] = f2zero();
+              }
+          }
+          if (jn < N && tc == nmc) {
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+              if (b == nqc) {
+#pragma unroll
+                for (int a = 0; a < RA; ++a) cxb[tr + TR * a] = A[a][b];
+              }
+          }
+        }
+        __syncthreads();
+        if (owner) {
+          float2 lv[RA];
+#pragma unroll
+          for (int a = 0; a < RA; ++a) lv[a] = col[tr + TR * a];
+#pragma unroll
+          for (int b = 0; b < RB; ++b) {
+            const float2 u = urow[tc + TC * b];
+#pragma unroll
+            for (int a = 0; a < RA; ++a) fsub_prod(A[a][b], lv[a], u);
+          }
+        } else if (warp == 0 && jn < N) {
+          float2* ncol = bCol + (bf ^ 1) * nbp;
+          const float2 u = urow[jn];
+          float2 v[4];
+          unsigned best = 0u;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            v[t] = f2zero();
+            if (i < N) {
+              v[t] = cxb[i];
+              fsub_prod(v[t], col[i], u);
+              if (!((used >> t) & 1u)) best = max(best, pack_key(v[t], i));
+            }
+          }
+          best = __reduce_max_sync(0xffffffffu, best);
+          const int bi = min(127 - (int)(best & 127u), N - 1);
+          if (lane == 0 && ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u))
+            atomicOr(p.status, kFlagSingular);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i < N) ncol[i] = (i == bi) ? make_float2(-1.f, 0.f) : v[t];
+            if (i == bi) {
+              used |= 1u << t;
+              s_r[bf ^ 1] = frcp(v[t]);
+              s_p[bf ^ 1] = bi;
+              s_pq[bf ^ 1] = bi / TR;
+              s_pm[bf ^ 1] = bi - (bi / TR) * TR;
+              sPiv[jn] = bi;
+            }
+          }
+        }
+        __syncthreads();
+        if (++jmc == TC) { jmc = 0; ++jqc; }
+        if (++nmc == TC) { nmc = 0; ++nqc; }
+      }
+      // B to shared memory; X[i][c] = B[p_i][q_c]: sPiv = p, sIdx = q = p^{-1}
+      if (owner) {
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+          for (int b = 0; b < RB; ++b) {
+            const int i = tr + TR * a, c = tc + TC * b;
+            if (i < N && c < N) sG[i * ld + c] = A[a][b];
+          }
+      }
+      for (int j = tid; j < N; j += nthr) sIdx[sPiv[j]] = j;
+      __syncthreads();
+      for (int i = tid; i < N; i += nthr) sRow[i] = sPiv[i] * ld;
+      __syncthreads();
+
+      if (p.mode & kOcc) {
+        for (int i = tid; i < N; i += nthr) acc_tr += (double)sG[sRow[i] + sIdx[i]].x;
+        float g2 = 0.f;
+        for (int e = tid; e < N * N; e += nthr) {
+          const int i = e / N, c = e - i * N;
+          const float2 g1 = sG[sRow[i] + sIdx[c]], gt = sG[sRow[c] + sIdx[i]];
+          g2 = __fmaf_rn(g1.x, gt.x, __fmaf_rn(-g1.y, gt.y, g2));
+        }
+        acc_g2 += (double)g2;
+      }
+      if (p.mode & kRho) {
+        double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
+        const bool first = (n == it.n0);
+        for (int e = tid; e < N * N; e += nthr) {
+          const int i = e / N, c = e - i * N;
+          const float2 g = sG[sRow[i] + sIdx[c]];
+          if (first) {
+            S[e] = make_double2((double)g.x, (double)g.y);
+          } else {
+            double2 s = S[e];
+            s.x += (double)g.x;
+            s.y += (double)g.y;
+            S[e] = s;
+          }
+        }
+      }
+      if (p.mode & (kGloc | kAdj)) {
+        const bool adj = (p.mode & kAdj) != 0;
+        cf zw;  // -(i w_n + mu) as a pair
+        split(-mu, zw.rh, zw.rl);
+        split(-wn, zw.ih, zw.il);
+        // Y0 = X P^+ (N x M);  Z0 = P X (M x N)
+        for (int e = tid; e < N * M; e += nthr) {
+          const int i = e / M, b = e - i * M;
+          float2 acc = f2zero();
+          for (int c = 0; c < N; ++c) fmac_cb(acc, sG[sRow[i] + sIdx[c]], sP[b * N + c]);
+          sY0[e] = acc;
+        }
+        if (adj) {
+          for (int e = tid; e < M * N; e += nthr) {
+            const int a = e / N, c = e - a * N;
+            const int colx = sIdx[c];
+            float2 acc = f2zero();
+            for (int i = 0; i < N; ++i) fmac(acc, sP[a * N + i], sG[sRow[i] + colx]);
+            sZ0[e] = acc;
+          }
+        }
+        __syncthreads();
+        // W = P Y0 (pairs)
+        for (int e = tid; e < M * M; e += nthr) {
+          const int a = e / M, b = e - a * M;
+          cf acc = czero();
+          #pragma unroll 1
+          for (int i = 0; i < N; ++i) {
+            cacc1(acc, ld4(Pkp[a * N + i]), sY0[i * M + b]);
+            if ((i & 15) == 15) cnorm(acc);
+          }
+          cnorm(acc);
+          sW[e] = st4(acc);
+        }
+        __syncthreads();
+        // V = Sigma W (pairs)
+        {
+          const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
+          for (int e = tid; e < M * M; e += nthr) {
+            const int a = e / M, b = e - a * M;
+            cf acc = czero();
+            #pragma unroll 1
+            for (int x = 0; x < M; ++x) cacc(acc, ld4(Sgp[a * M + x]), ld4(sW[x * M + b]));
+            cnorm(acc);
+            sV[e] = st4(acc);
+          }
+        }
+        __syncthreads();
+        // R = P^+ - A Y0 = P^+ - (i w + mu) Y0 + H Y0 + P^+ V  (pairs, rounded to FP32)
+        for (int e = tid; e < N * M; e += nthr) {
+          const int i = e / M, b = e - i * M;
+          cf acc = conj_cf(ld4(Pkp[b * N + i]));
+          cacc1(acc, zw, sY0[e]);
+          #pragma unroll 1
+          for (int c = 0; c < N; ++c) {
+            cacc1(acc, ld4(Hkp[i * N + c]), sY0[c * M + b]);
+            if ((c & 15) == 15) cnorm(acc);
+          }
+          #pragma unroll 1
+          for (int a = 0; a < M; ++a) cacc_ca(acc, ld4(Pkp[a * N + i]), ld4(sV[a * M + b]));
+          cnorm(acc);
+          sR[e] = round_cf(acc);
+        }
+        __syncthreads();
+        // dY = X R (FP32);  Y = Y0 + dY
+        for (int e = tid; e < N * M; e += nthr) {
+          const int i = e / M, b = e - i * M;
+          float2 acc = f2zero();
+          for (int c = 0; c < N; ++c) fmac(acc, sG[sRow[i] + sIdx[c]], sR[c * M + b]);
+          sdY[e] = acc;
+        }
+        __syncthreads();
+        // P Y = W + P dY  (the second term in FP32)
+        if (p.mode & kGloc) {
+          double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
+          for (int e = tid; e < M * M; e += nthr) {
+            const int a = e / M, b = e - a * M;
+            float2 d = f2zero();
+            for (int i = 0; i < N; ++i) fmac(d, sP[a * N + i], sdY[i * M + b]);
+            const double2 w = to_d2(ld4(sW[e]));
+            out[e] = make_double2(wk * (w.x + (double)d.x), wk * (w.y + (double)d.y));
+          }
+        }
+        if (adj) {
+          // A_k = P Y in pairs (kept for the adjoint)
+          for (int e = tid; e < M * M; e += nthr) {
+            const int a = e / M, b = e - a * M;
+            float2 d = f2zero();
+            for (int i = 0; i < N; ++i) fmac(d, sP[a * N + i], sdY[i * M + b]);
+            cf q = ld4(sW[e]);
+            float s, t;
+            two_sum(q.rh, d.x, s, t);
+            q.rh = s;
+            q.rl = __fadd_rn(q.rl, t);
+            two_sum(q.ih, d.y, s, t);
+            q.ih = s;
+            q.il = __fadd_rn(q.il, t);
+            cnorm(q);
+            sQa[e] = st4(q);
+          }
+          __syncthreads();
+          // W' = Z0 P^+ (pairs), then V' = W' Sigma
+          for (int e = tid; e < M * M; e += nthr) {
+            const int a = e / M, b = e - a * M;
+            cf acc = czero();
+            #pragma unroll 1
+            for (int i = 0; i < N; ++i) {
+              cacc1(acc, conj_cf(ld4(Pkp[b * N + i])), sZ0[a * N + i]);
+              if ((i & 15) == 15) cnorm(acc);
+            }
+            cnorm(acc);
+            sW[e] = st4(acc);
+          }
+          __syncthreads();
+          {
+            const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
+            for (int e = tid; e < M * M; e += nthr) {
+              const int a = e / M, b = e - a * M;
+              cf acc = czero();
+              #pragma unroll 1
+              for (int x = 0; x < M; ++x) cacc(acc, ld4(sW[a * M + x]), ld4(Sgp[x * M + b]));
+              cnorm(acc);
+              sV[e] = st4(acc);
+            }
+          }
+          __syncthreads();
+          // R' = P - Z0 A = P - (i w + mu) Z0 + Z0 H + V' P  (pairs, rounded), m x N
+          for (int e = tid; e < M * N; e += nthr) {
+            const int a = e / N, c = e - a * N;
+            cf acc = ld4(Pkp[a * N + c]);
+            cacc1(acc, zw, sZ0[e]);
+            #pragma unroll 1
+            for (int i = 0; i < N; ++i) {
+              cacc1(acc, ld4(Hkp[i * N + c]), sZ0[a * N + i]);
+              if ((i & 15) == 15) cnorm(acc);
+            }
+            #pragma unroll 1
+            for (int b = 0; b < M; ++b) cacc(acc, ld4(sV[a * M + b]), ld4(Pkp[b * N + c]));
+            cnorm(acc);
+            sR[e] = round_cf(acc);
+          }
+          __syncthreads();
+          // dZ = R' X (FP32)
+          for (int e = tid; e < M * N; e += nthr) {
+            const int a = e / N, c = e - a * N;
+            const int colx = sIdx[c];
+            float2 acc = f2zero();
+            for (int i = 0; i < N; ++i) fmac(acc, sR[a * N + i], sG[sRow[i] + colx]);
+            sdZ[e] = acc;
+          }
+          __syncthreads();
+          // B_k = Z Y = Z0 Y0 (pairs) + Z0 dY + dZ Y0 (FP32)
+          for (int e = tid; e < M * M; e += nthr) {
+            const int a = e / M, b = e - a * M;
+            cf acc = czero();
+            float2 d = f2zero();
+            #pragma unroll 1
+            for (int i = 0; i < N; ++i) {
+              const float2 z = sZ0[a * N + i], y = sY0[i * M + b];
+              cacc1(acc, cf{z.x, 0.f, z.y, 0.f}, y);
+              fmac(d, z, sdY[i * M + b]);
+              fmac(d, sdZ[a * N + i], y);
+              if ((i & 15) == 15) cnorm(acc);
+            }
+            float s, t;
+            two_sum(acc.rh, d.x, s, t);
+            acc.rh = s;
+            acc.rl = __fadd_rn(acc.rl, t);
+            two_sum(acc.ih, d.y, s, t);
+            acc.ih = s;
+            acc.il = __fadd_rn(acc.il, t);
+            cnorm(acc);
+            sQb[e] = st4(acc);
+          }
+          __syncthreads();
+          const bool have_gbar = (p.Gbd != nullptr);
+          if (have_gbar) {
+            const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
+            // Mt = Gbar A_k^+ (pairs)
+            for (int e = tid; e < M * M; e += nthr) {
+              const int a = e / M, b = e - a * M;
+              cf acc = czero();
+              #pragma unroll 1
+              for (int c = 0; c < M; ++c) cacc_cb(acc, ld4(Gb[a * M + c]), ld4(sQa[b * M + c]));
+              cnorm(acc);
+              sMt[e] = st4(acc);
+            }
+            // mu_bar partial: - w_k Re<Gbar, B_k>
+            for (int e = tid; e < M * M; e += nthr) {
+              const double2 gv = to_d2(ld4(Gb[e])), bv = to_d2(ld4(sQb[e]));
+              acc_mu -= wk * fma(gv.x, bv.x, gv.y * bv.y);
+            }
+            __syncthreads();
+          }
+          double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
+          const double cb = nbar * 2.0 / beta;
+          for (int e = tid; e < M * M; e += nthr) {
+            const int a = e / M, b = e - a * M;
+            cf acc = czero();
+            if (have_gbar)
+              #pragma unroll 1
+              for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sMt[c * M + b]));
+            cnorm(acc);
+            const double2 v = to_d2(acc);
+            const double2 bt = to_d2(ld4(sQb[b * M + a]));
+            out[e] = make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y));
+          }
+        }
+      }
+    }
+    if (p.mode & kOcc) {
+      const double tr_ = block_sum_f(acc_tr, s_red);
+      const double g2 = block_sum_f(acc_g2, s_red);
+      if (tid == 0) {
+        double* o = p.occ_part + ((int64_t)it.k * p.n_chunks + it.chunk) * 2;
+        o[0] = tr_;
+        o[1] = g2;
+      }
+    }
+    if (p.mode & kAdj) {
+      const double mb = block_sum_f(acc_mu, s_red);
+      if (tid == 0) p.mubar_part[(int64_t)it.k * p.n_chunks + it.chunk] = mb;
+    }
+    __syncthreads();
+  }
+}
+
+// Tile shapes: (RA, RB), the thread bound of the instantiation (owners plus the
+// pivot warp), the minimum resident CTAs it is compiled for, and the largest
+// window it is meant for (TR = ceil(N / RA), TC = ceil(N / RB), TR TC <= MAXT - 32).
+struct ShapeF {
+  int ra, rb, maxt, minb, nmax;
+};
+constexpr ShapeF kShapesF[] = {
+    {2, 2, 96, 4, 16}, {2, 5, 192, 3, 40}, {4, 5, 128, 4, 40}, {4, 4, 288, 2, 64},
+    {4, 8, 160, 3, 64}, {6, 8, 224, 2, 96}, {4, 8, 352, 1, 96}, {4, 8, 544, 1, 128},
+    {8, 8, 288, 1, 128},
+};
+constexpr int kNumShapesF = (int)(sizeof(kShapesF) / sizeof(kShapesF[0]));
+
+template <int RA, int RB, int MAXT, int MINB>
+cudaError_t launch_f(const PointParams& p, int grid, int threads, size_t smem, cudaStream_t s) {
+  if (threads > MAXT) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_point_f32r<RA, RB, MAXT, MINB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_point_f32r<RA, RB, MAXT, MINB><<<grid, threads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int RA, int RB, int MAXT, int MINB>
+int bps_f(int threads, size_t smem) {
+  int nb = 0;
+  if (cudaFuncSetAttribute(k_point_f32r<RA, RB, MAXT, MINB>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_point_f32r<RA, RB, MAXT, MINB>, threads,
+                                                    smem) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+#define GF_F32R_SHAPES(X) \
+  X(0, 2, 2, 96, 4)       \
+  X(1, 2, 5, 192, 3)      \
+  X(2, 4, 5, 128, 4)      \
+  X(3, 4, 4, 288, 2)      \
+  X(4, 4, 8, 160, 3)      \
+  X(5, 6, 8, 224, 2)      \
+  X(6, 4, 8, 352, 1)      \
+  X(7, 4, 8, 544, 1)      \
+  X(8, 8, 8, 288, 1)
+
+}  // namespace
+
+int f32r_num_shapes() { return kNumShapesF; }
+
+int f32r_tile(int shape, int which) {
+  if (shape < 0 || shape >= kNumShapesF) return 0;
+  return which == 0 ? kShapesF[shape].ra : kShapesF[shape].rb;
+}
+
+// A shape serves a window of nbmax bands when its owner grid fits its thread
+// bound and nbmax is within the window class it was tuned for.
+bool f32r_shape_fits(int shape, int nbmax) {
+  if (shape < 0 || shape >= kNumShapesF) return false;
+  const ShapeF sh = kShapesF[shape];
+  if (nbmax > sh.nmax) return false;
+  return ((nbmax + sh.ra - 1) / sh.ra) * ((nbmax + sh.rb - 1) / sh.rb) <= sh.maxt - 32;
+}
+
+int f32r_threads(int shape, int nbmax) {
+  const ShapeF sh = kShapesF[shape];
+  const int t = ((nbmax + sh.ra - 1) / sh.ra) * ((nbmax + sh.rb - 1) / sh.rb);
+  return 32 + ((t + 31) / 32) * 32;  // owners plus the pivot warp
+}
+
+int f32r_nmax(int shape) { return (shape >= 0 && shape < kNumShapesF) ? kShapesF[shape].nmax : 0; }
+
+size_t point_f32r_smem(int nbmax, int mmax, int mode) { return make_layout_f(nbmax, mmax, mode).bytes; }
+
+int point_f32r_blocks_per_sm(int shape, int threads, size_t smem) {
+  switch (shape) {
+#define X(i, a, b, t, m) \
+  case i:                \
+    return bps_f<a, b, t, m>(threads, smem);
+    GF_F32R_SHAPES(X)
+#undef X
+  }
+  return 0;
+}
+
+cudaError_t launch_point_f32r(int shape, const PointParams& p, int grid, int threads, size_t smem,
+                              cudaStream_t s) {
+  switch (shape) {
+#define X(i, a, b, t, m) \
+  case i:                \
+    return launch_f<a, b, t, m>(p, grid, threads, smem, s);
+    GF_F32R_SHAPES(X)
+#undef X
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gf
+
+namespace gf {
+
+namespace {
+__global__ void k_round_f32(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2(__double2float_rn(in[i].x), __double2float_rn(in[i].y));
+}
+}  // namespace
+
+cudaError_t launch_round_f32(const double2* in, float2* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_round_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace gf

@@ -68,6 +68,10 @@ struct PointParams {
   const float4* Pd;
   const float4* Sd;
   const float4* Gbd;
+  // single-word FP32 copies of H, P and Sigma for the f32r kernel
+  const float2* Hs;
+  const float2* Ps;
+  const float2* Ss;
   // outputs
   double* occ_part;     // [n_k][n_chunks][2]
   double2* rho_part;    // [n_chunks][sum_k N_b^2]
@@ -254,6 +258,19 @@ size_t point_df64r_smem(int nbmax, int mmax, int mode);
 int point_df64r_blocks_per_sm(int shape, int threads, size_t smem);
 cudaError_t launch_point_df64r(int shape, const PointParams& p, int grid, int threads, size_t smem,
                                cudaStream_t s);
+// Mixed-precision register-resident FP32 kernel (gf_f32r.cu): tile shapes, the
+// window class each serves, thread count, shared memory and occupancy.
+int f32r_num_shapes();
+int f32r_tile(int shape, int which);  // RA (which = 0) or RB (which = 1)
+int f32r_nmax(int shape);
+bool f32r_shape_fits(int shape, int nbmax);
+int f32r_threads(int shape, int nbmax);
+size_t point_f32r_smem(int nbmax, int mmax, int mode);
+int point_f32r_blocks_per_sm(int shape, int threads, size_t smem);
+cudaError_t launch_point_f32r(int shape, const PointParams& p, int grid, int threads, size_t smem,
+                              cudaStream_t s);
+// out[i] = complex FP32 rounding of in[i], for n complex numbers
+cudaError_t launch_round_f32(const double2* in, float2* out, int64_t n, cudaStream_t s);
 // Shared memory of k_point_df64 with nmat matrices (frequencies) per CTA step.
 size_t point_df64_smem(int nbmax, int mmax, int mode, int a_in_smem, int nmat);
 // out[i] = FP32 pair (hi, lo) of in[i], hi = RN(x), lo = RN(x - hi), for n complex numbers

@@ -19,7 +19,7 @@ _lib = None
 GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ESINGULAR, GF_ENOTCONV, GF_ETIMEOUT, GF_ESTATE = range(8)
 STATUS_NAMES = {0: "GF_OK", 1: "GF_EINVAL", 2: "GF_ENOMEM", 3: "GF_ECUDA", 4: "GF_ESINGULAR",
                 5: "GF_ENOTCONV", 6: "GF_ETIMEOUT", 7: "GF_ESTATE"}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "pair": 2}
 DTYPE = {"c128": 0, "c64": 1}
 
 EXPORTS = ["gf_create", "gf_destroy", "gf_set_hamiltonian", "gf_set_projectors", "gf_set_sigma",

@@ -15,7 +15,7 @@ def _batched_small():
     return synth.batched(n_iw=24, nk_scale=0.002).systems
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "pair"])
 def test_one_launch_for_all_systems_matches_oracle(precision):
     systems = _batched_small()
     g = make_gf(systems, precision=precision)
@@ -25,15 +25,17 @@ def test_one_launch_for_all_systems_matches_oracle(precision):
     gl = g.local(mus).cpu().numpy()
     st = g.stats()
     off = 0
-    tol = 1e-10 if precision == "fp64" else 1e-9
+    # mixed: N at the contract (1e-7), G_loc from refined projections (1e-8), dN/dmu from
+    # unrefined FP32 inverses (1e-5)
+    tol_n, tol_dn, tol_g = (1e-10, 1e-10, 1e-10) if precision == "fp64" else (1e-7, 1e-5, 1e-8)
     for i, s in enumerate(systems):
         r = oracle.get().density(s.H, s.P, s.sigma, s.sigma_inf, s.beta, mus[i], want_rho=False)
-        assert abs(n[i] - r["N"]) < tol * r["N"]
-        assert abs(dn[i] - r["dN_dmu"]) < tol * r["dN_dmu"]
+        assert abs(n[i] - r["N"]) < tol_n * r["N"]
+        assert abs(dn[i] - r["dN_dmu"]) < tol_dn * r["dN_dmu"]
         size = s.n_iw * s.m * s.m
         if i < 2:
             glo = oracle.get().local(s.H, s.P, s.sigma, s.beta, mus[i])
-            assert rel(gl[off:off + size], glo.reshape(-1)) < tol
+            assert rel(gl[off:off + size], glo.reshape(-1)) < tol_g
         off += size
     # G_loc of all systems comes from one point-kernel launch per band-window bucket
     # (N_b <= 64, <= 96, > 96) plus one k-reduction
@@ -52,7 +54,7 @@ def test_batched_equals_one_context_per_system():
         gi.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "pair"])
 def test_graph_replay_is_bitwise_identical(precision):
     systems = _batched_small()[:3]
     g0 = make_gf(systems, precision=precision)
@@ -61,10 +63,12 @@ def test_graph_replay_is_bitwise_identical(precision):
         a = g0.occupation(mus)
         b = g1.occupation(mus)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
-    # the replayed evaluations still drive the mu search
+    # the replayed evaluations still drive the mu search (the mixed path's N carries FP32
+    # rounding of about 1e-9 relative, so its search stops at 1e-8 relative)
     targets = [s.n_target for s in systems]
-    m0, _ = g0.find_mu(targets, 0.0, tol=1e-10)
-    m1, _ = g1.find_mu(targets, 0.0, tol=1e-10)
+    tol = 1e-8 * min(targets) if precision == "mixed" else 1e-10
+    m0, _ = g0.find_mu(targets, 0.0, tol=tol)
+    m1, _ = g1.find_mu(targets, 0.0, tol=tol)
     assert np.array_equal(m0, m1)
     # inputs changed after capture: the graph reads the new inputs
     s2 = [synth.System(s.H, s.P, s.pole, s.sigma * 0.5, s.beta, s.n_target) for s in systems]
