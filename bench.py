@@ -39,7 +39,7 @@ UNIT = "points/s"
 WORKLOAD = "ce_like: N_k=1000, N_b=40, m=14, N_w=1024, beta=100 1/eV, U=6 eV, dense H, two-pole Sigma"
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Peak of the FP32-pair arithmetic of the mixed path, in FP64-equivalent flop/s: the FP32 pipes
+# Peak of the FP32-pair arithmetic (GF_PREC_PAIR), in FP64-equivalent flop/s: the FP32 pipes
 # issue 152 SMs x 128 lanes x 2.07 GHz operations, and one FP32-pair complex multiply-add takes
 # at least 48 of them (4 error-free products with head sums, 12 operations each); 8 flop per CMAC.
 MIXED_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 48 * 8 / 1e12
@@ -56,16 +56,19 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-nio", action="store_true", help="skip the NiO-like leg of the default line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched leg of the default line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the bounded CPU-oracle sample")
-    ap.add_argument("--nk-scale", type=float, default=0.25,
+    ap.add_argument("--nk-scale", type=float, default=1.0,
                     help="batched workload: fraction of each system's k-points")
     ap.add_argument("--nk", type=int, default=None,
                     help="smaller k-set of the same workload (profiling captures only)")
     ap.add_argument("--n-iw", type=int, default=None,
                     help="fewer Matsubara frequencies (profiling captures only)")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
-                    help="arithmetic of the point kernel (mixed: FP32 pairs on the FP32 pipes)")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "pair"], default="fp64",
+                    help="arithmetic of the point kernel (mixed: FP32 inverse with refined "
+                         "projections; pair: FP32 pairs on the FP32 pipes)")
     ap.add_argument("--workload", choices=["ce_like", "nio_like", "batched", "adjoint", "lowrank",
                                            "pole", "dmft_step"],
                     default="ce_like", help="non-default workloads print one measurement line each")
@@ -207,7 +210,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32x2",
+            "dtype": {"fp64": "f64", "mixed": "f32", "pair": "f32x2"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "step": f"oracle Matsubara-sum pass over {k} k-points x "
                                                      f"{s.n_iw} frequencies at mu=0 (bounded sample)",
@@ -258,6 +261,148 @@ def _lr_pole_cases(args, synth):
             ("nio_like_1024k", synth.nio_like(nk=1024).systems[0])]
 
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+MIXED_MU_TOL = 1e-8  # mixed path: mu search to |N - N_target| <= 1e-8 N_target (FP32 noise ~1e-9)
+
+
+def _dev_context(gf, systems, precision, graph=False, lowrank=False):
+    """Context with the inputs uploaded from device tensors (resident in HBM)."""
+    import torch
+    g = gf.GreensFunction.for_systems(systems, precision=precision, graph=graph, lowrank=lowrank)
+    g.set_hamiltonian(torch.from_numpy(_pack([_pack(s.H) for s in systems])).cuda())
+    g.set_projectors(torch.from_numpy(_pack([_pack(s.P) for s in systems])).cuda())
+    g.set_sigma(torch.from_numpy(_pack([s.sigma for s in systems])).cuda(),
+                torch.from_numpy(_pack([s.sigma_inf for s in systems])).cuda())
+    return g
+
+
+def nio_leg(gf, synth, o, nk=4096, n_iw=2048):
+    """NiO-like precision workload: one fixed-mu fused pass (G_loc, N, dN/dmu) on the FP64
+    and on the mixed path, the mixed mu search, and errors against the oracle."""
+    s = synth.nio_like(nk=nk, n_iw=n_iw).systems[0]
+    npts = s.nk * s.n_iw
+    out = {"config": f"N_k={s.nk}, N_b=96, m=20 (2 atoms x 5 d x 2 spin, AFM Sigma), N_w={s.n_iw}, "
+                     "beta=40 1/eV, U=8 eV", "points_per_pass": npts}
+    # mixed: mu search (graph replay of the N(mu) evaluation), then the fused pass at mu*
+    gm = _dev_context(gf, [s], "mixed", graph=True)
+    tol = MIXED_MU_TOL * s.n_target
+    (mu, it), t_mu = _sync_time(lambda: gm.find_mu([s.n_target], 0.0, tol=tol))
+    smu = gm.stats()
+    gm.evaluate(mu, rho=False, n_corr=False)  # autotunes the fused pass's launch
+    evm, t_m = _sync_time(lambda: gm.evaluate(mu, rho=False, n_corr=False))
+    stm = gm.stats()
+    gl_m = evm["gloc"].cpu().numpy().reshape(s.n_iw, s.m, s.m)
+    mixed_log = gm.tuning_log()
+    gm.close()
+    # FP64: the same fused pass (one call; the autotuner's samples are outside its kernel time)
+    g64 = _dev_context(gf, [s], "fp64")
+    ev64, t_64 = _sync_time(lambda: g64.evaluate(mu, rho=False, n_corr=False))
+    st64 = g64.stats()
+    gl_d = ev64["gloc"].cpu().numpy().reshape(s.n_iw, s.m, s.m)
+    fp64_log = g64.tuning_log()
+    g64.close()
+    idx = [0, 1, s.n_iw // 2, s.n_iw - 1]
+    glo = o.local(s.H, s.P, s.sigma, s.beta, float(mu[0]), n_idx=idx)
+    # N against the oracle on an 8-k subset (all frequencies), the GPU evaluating the same subset
+    ks = list(range(8))
+    sub = synth.System(s.H[ks], s.P[ks], s.pole, s.sigma, s.beta, s.n_target)
+    r_o = o.density(sub.H, sub.P, sub.sigma, sub.sigma_inf, sub.beta, float(mu[0]), want_rho=False)
+    gs = _dev_context(gf, [sub], "mixed")
+    n_sub, dn_sub = gs.occupation(mu)
+    gs.close()
+    k_m, k_d = stm["kernel_ms"] / 1e3, st64["kernel_ms"] / 1e3
+    out.update({
+        "mu_star": float(mu[0]), "N_at_mu_star": float(evm["N"][0]),
+        "fp64": {"pass_s": t_64, "pass_kernel_s": k_d, "points_per_s": npts / k_d,
+                 "kernel_tflops": st64["flops"] / st64["kernel_ms"] / 1e9,
+                 "frac_of_fp64_peak": st64["flops"] / st64["kernel_ms"] / 1e9 / FP64_PEAK_TFLOPS,
+                 "kernel_choice": fp64_log},
+        "mixed": {"pass_s": t_m, "pass_kernel_s": k_m, "points_per_s": npts / k_m,
+                  "speedup_vs_fp64_gpu": k_d / k_m, "speedup_vs_fp64_gpu_wall": t_64 / t_m,
+                  "roofline": {"bound": "alu", "achieved": stm["flops"] / stm["kernel_ms"] / 1e9,
+                               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": stm["flops"] / stm["kernel_ms"] / 1e9 / FP32_PEAK_TFLOPS,
+                               "kernel": "k_point_f32r (autotuned tiles)",
+                               "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"},
+                  "find_mu_s": t_mu, "find_mu_evaluations": it,
+                  "find_mu_points_per_s": smu["points"] / t_mu,
+                  "find_mu_speedup_vs_fp64_pass_rate": (smu["points"] / t_mu) / (npts / k_d),
+                  "kernel_choice": mixed_log},
+        "N_rel_err_mixed_vs_fp64_gpu": abs(float(evm["N"][0]) - float(ev64["N"][0])) / float(ev64["N"][0]),
+        "dN_dmu_rel_err_mixed_vs_fp64_gpu": abs(float(evm["dN_dmu"][0]) - float(ev64["dN_dmu"][0]))
+                                             / float(ev64["dN_dmu"][0]),
+        "G_loc_rel_err_mixed_vs_fp64_gpu": float(np.max(np.abs(gl_m - gl_d)) / np.max(np.abs(gl_d))),
+        "G_loc_rel_err_vs_oracle": {"mixed": float(np.max(np.abs(gl_m[idx] - glo)) / np.max(np.abs(glo))),
+                                    "fp64": float(np.max(np.abs(gl_d[idx] - glo)) / np.max(np.abs(glo))),
+                                    "sample": f"frequencies {idx} over all {s.nk} k-points"},
+        "N_rel_err_vs_oracle": {"mixed": abs(float(n_sub[0]) - r_o["N"]) / r_o["N"],
+                                "sample": "k-points 0-7, all frequencies, at mu*"},
+    })
+    return out
+
+
+def batched_leg(gf, synth, o, nk_scale=1.0):
+    """Batched workload: 8 systems with ragged windows in one launch per window bucket, FP64
+    and mixed N(mu) passes, one launch per system, and a graph-replayed mixed mu search."""
+    systems = synth.batched(nk_scale=nk_scale).systems
+    pts = sum(sy.nk * sy.n_iw for sy in systems)
+    mus = [0.0] * len(systems)
+    out = {"config": (f"8 systems, N_k per system {[sy.nk for sy in systems]}, N_b(k) uniform in [48, 128], "
+                      f"m {[sy.m for sy in systems]}, N_w=1024, beta=40 (k-sets x {nk_scale})"),
+           "points_per_pass": pts}
+    g64 = _dev_context(gf, systems, "fp64")
+    (n64, d64), t64 = _sync_time(lambda: g64.occupation(mus))
+    s64 = g64.stats()
+    out["fp64"] = {"pass_s": t64, "pass_kernel_s": s64["kernel_ms"] / 1e3,
+                   "points_per_s": pts / (s64["kernel_ms"] / 1e3), "launches": s64["launches"],
+                   "kernel_tflops": s64["flops"] / s64["kernel_ms"] / 1e9}
+    g64.close()
+    gm = _dev_context(gf, systems, "mixed")
+    gm.occupation(mus)
+    (nm, dm), tm = _sync_time(lambda: gm.occupation(mus))
+    sm_ = gm.stats()
+    log = gm.tuning_log()
+    gm.close()
+    t_per, n_launch = 0.0, 0
+    for sy in systems:
+        gi = _dev_context(gf, [sy], "mixed")
+        gi.occupation([0.0])
+        _, t = _sync_time(lambda: gi.occupation([0.0]))
+        t_per += t
+        n_launch += gi.stats()["launches"]
+        gi.close()
+    gg = _dev_context(gf, systems, "mixed", graph=True)
+    targets = [sy.n_target for sy in systems]
+    (mu_g, it_g), t_g = _sync_time(lambda: gg.find_mu(targets, 0.0, tol=MIXED_MU_TOL * min(targets)))
+    pts_g = gg.stats()["points"]
+    gg.close()
+    # N against the oracle on k-subsets of two systems (4 k-points each, all frequencies)
+    errs = []
+    for i in (0, 1):
+        sy = systems[i]
+        sub = synth.System(sy.H[:4], sy.P[:4], sy.pole, sy.sigma, sy.beta, sy.n_target)
+        r_o = o.density(sub.H, sub.P, sub.sigma, sub.sigma_inf, sub.beta, 0.0, want_rho=False)
+        gs = _dev_context(gf, [sub], "mixed")
+        n_s, _ = gs.occupation([0.0])
+        gs.close()
+        errs.append(abs(float(n_s[0]) - r_o["N"]) / r_o["N"])
+    k_m = sm_["kernel_ms"] / 1e3
+    out["mixed"] = {"pass_s": tm, "pass_kernel_s": k_m, "points_per_s": pts / k_m,
+                    "launches": sm_["launches"], "speedup_vs_fp64_gpu": s64["kernel_ms"] / sm_["kernel_ms"],
+                    "roofline": {"bound": "alu", "achieved": sm_["flops"] / sm_["kernel_ms"] / 1e9,
+                                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": sm_["flops"] / sm_["kernel_ms"] / 1e9 / FP32_PEAK_TFLOPS},
+                    "per_system_launches_s": t_per, "per_system_kernel_launches": n_launch,
+                    "speedup_one_launch_vs_per_system": t_per / tm,
+                    "graph_find_mu_s": t_g, "graph_find_mu_evaluations": it_g,
+                    "graph_find_mu_points_per_s": pts_g / t_g, "kernel_choice": log}
+    out["N_rel_err_mixed_vs_fp64_gpu"] = float(np.max(np.abs(nm - n64) / n64))
+    out["dN_dmu_rel_err_mixed_vs_fp64_gpu"] = float(np.max(np.abs(dm - d64) / d64))
+    out["N_rel_err_vs_oracle"] = {"mixed": max(errs), "sample": "systems 0 and 1, k-points 0-3 each, "
+                                                                 "all frequencies, mu = 0"}
+    return out
+
+
 def run_workload(args):
     """Measurements on the NiO-like, batched and adjoint workloads (one JSON line each)."""
     import torch
@@ -270,93 +415,9 @@ def run_workload(args):
     o.set_threads(cpu_cores())
     out = {"workload": args.workload}
     if args.workload == "nio_like":
-        s = synth.nio_like(nk=args.nk or 4096, n_iw=args.n_iw or 2048).systems[0]
-        out["config"] = (f"N_k={s.nk}, N_b=96, m=20 (2 atoms x 5 d x 2 spin, AFM Sigma), N_w={s.n_iw}, "
-                         "beta=40, U=8")
-        gm = _context(gf, [s], "mixed", graph=True)
-        (mu, it), t_mu = _sync_time(lambda: gm.find_mu([s.n_target], 0.0, tol=1e-10))
-        n_pass = gm.stats()
-        ev, t_ev = _sync_time(lambda: gm.evaluate(mu, rho=False, n_corr=False))
-        stm = gm.stats()
-        out["mixed"] = {"mu_star": float(mu[0]), "mu_evaluations": it, "find_mu_s": t_mu,
-                        "points_per_s": n_pass["points"] / t_mu, "evaluate_s": t_ev,
-                        "evaluate_kernel_s": stm["kernel_ms"] / 1e3,
-                        "kernel_choice": gm.tuning_log()}
-        g64 = _context(gf, [s], "fp64")
-        (ev64), t64 = _sync_time(lambda: g64.evaluate(mu, rho=False, n_corr=False))
-        st64 = g64.stats()
-        out["fp64"] = {"evaluate_s": t64, "points_per_s": s.nk * s.n_iw / t64,
-                       "kernel_tflops": st64["flops"] / st64["kernel_ms"] / 1e9,
-                       "kernel_choice": g64.tuning_log()}
-        # (the first pass of a mode also runs the autotuner's samples; kernel times exclude them)
-        out["mixed_speedup_per_pass"] = t64 / t_ev
-        out["mixed_speedup_per_pass_kernel_time"] = st64["kernel_ms"] / stm["kernel_ms"]
-        out["fp64"]["evaluate_kernel_s"] = st64["kernel_ms"] / 1e3
-        out["N_rel_err_mixed_vs_fp64_gpu"] = abs(ev["N"][0] - ev64["N"][0]) / ev64["N"][0]
-        gl_m, gl_d = ev["gloc"], ev64["gloc"]
-        out["G_loc_rel_err_mixed_vs_fp64_gpu"] = float((gl_m - gl_d).abs().max() / gl_d.abs().max())
-        idx = [0, 1, s.n_iw // 2, s.n_iw - 1]
-        glo = o.local(s.H, s.P, s.sigma, s.beta, float(mu[0]), n_idx=idx)
-        glm = gl_m.cpu().numpy().reshape(s.n_iw, 20, 20)[idx]
-        gld = gl_d.cpu().numpy().reshape(s.n_iw, 20, 20)[idx]
-        out["G_loc_rel_err_vs_oracle_sampled"] = {
-            "mixed": float(np.max(np.abs(glm - glo)) / np.max(np.abs(glo))),
-            "fp64": float(np.max(np.abs(gld - glo)) / np.max(np.abs(glo))),
-            "frequencies": idx}
-        gm.close()
-        g64.close()
+        out.update(nio_leg(gf, synth, o, nk=args.nk or 4096, n_iw=args.n_iw or 2048))
     elif args.workload == "batched":
-        systems = synth.batched(nk_scale=args.nk_scale)
-        systems = systems.systems
-        out["config"] = (f"8 systems, N_k per system {[s.nk for s in systems]}, N_b(k) uniform in [48, 128], "
-                         f"m {[s.m for s in systems]}, N_w=1024, beta=40 (k-sets scaled by {args.nk_scale})")
-        mus = [0.0] * len(systems)
-        res = {}
-        for prec in ("fp64", "mixed"):
-            g = _context(gf, systems, prec)
-            g.occupation(mus)
-            _, t_one = _sync_time(lambda: g.occupation(mus))
-            pts = g.stats()["points"]
-            launches = g.stats()["launches"]
-            g.close()
-            t_per = 0.0
-            n_launch = 0
-            for sy in systems:
-                gi = _context(gf, [sy], prec)
-                gi.occupation([0.0])
-                _, t = _sync_time(lambda: gi.occupation([0.0]))
-                t_per += t
-                n_launch += gi.stats()["launches"]
-                gi.close()
-            gg = _context(gf, systems, prec, graph=True)
-            targets = [sy.n_target for sy in systems]
-            (mu_g, it_g), t_g = _sync_time(lambda: gg.find_mu(targets, 0.0, tol=1e-10))
-            pts_g = gg.stats()["points"]
-            log = gg.tuning_log()
-            gg.close()
-            res[prec] = {"one_launch_s": t_one, "one_launch_points_per_s": pts / t_one,
-                         "one_launch_kernel_launches": launches,
-                         "per_system_s": t_per, "per_system_kernel_launches": n_launch,
-                         "speedup_one_launch_vs_per_system": t_per / t_one,
-                         "graph_find_mu_s": t_g, "graph_find_mu_evaluations": it_g,
-                         "graph_points_per_s": pts_g / t_g, "kernel_choice": log}
-        out.update(res)
-        out["mixed_speedup_one_launch"] = res["fp64"]["one_launch_s"] / res["mixed"]["one_launch_s"]
-        # the same passes with the low-rank algorithm (one launch per window bucket, graph replay)
-        gl = _context(gf, systems, "fp64", lowrank=True)
-        gl.occupation(mus)
-        _, t_one = _sync_time(lambda: gl.occupation(mus))
-        pts = gl.stats()["points"]
-        gl.close()
-        gg = _context(gf, systems, "fp64", graph=True, lowrank=True)
-        targets = [sy.n_target for sy in systems]
-        (mu_g, it_g), t_g = _sync_time(lambda: gg.find_mu(targets, 0.0, tol=1e-10))
-        pts_g = gg.stats()["points"]
-        gg.close()
-        out["lowrank"] = {"one_launch_s": t_one, "one_launch_points_per_s": pts / t_one,
-                          "speedup_vs_fp64_direct": res["fp64"]["one_launch_s"] / t_one,
-                          "graph_find_mu_s": t_g, "graph_find_mu_evaluations": it_g,
-                          "graph_points_per_s": pts_g / t_g}
+        out.update(batched_leg(gf, synth, o, nk_scale=args.nk_scale))
     elif args.workload == "adjoint":
         from paper_1111_2157_gb300.autograd import lattice_green, newton_mu
         s = synth.adjoint_case().systems[0]
@@ -589,8 +650,10 @@ def main():
             passes[name]["flops"] += st["flops"]
             passes[name]["launches"] += 1
 
+        mu_tol = MIXED_MU_TOL * s.n_target if precision == "mixed" else 1e-10
+
         def step():
-            mu, it = g.find_mu([s.n_target], 0.0, tol=1e-10, max_iter=60)
+            mu, it = g.find_mu([s.n_target], 0.0, tol=mu_tol, max_iter=60)
             acc("find_mu")
             out = g.evaluate(mu, gloc_out=gloc_d, rho_out=rho_d)
             acc("evaluate")
@@ -652,36 +715,55 @@ def main():
                  "speedup_vs_fp64_gpu": (mt["points"] / mx["elapsed"]) / (totals["points"] / elapsed),
                  "N_rel_err_vs_fp64_gpu": err_n, "G_loc_rel_err_vs_fp64_gpu": err_g,
                  "mu_star": mx["info"]["mu"],
-                 "fp64_equivalent_tflops": mt["flops"] / (mt["kernel_ms"] / 1e3) / 1e12,
-                 "frac_of_fp32_pair_peak": mt["flops"] / (mt["kernel_ms"] / 1e3) / 1e12 / MIXED_PEAK_TFLOPS,
-                 "arithmetic": "FP32 pairs (hi + lo, error-free transformations) on the FP32 pipes; "
-                               "FP64 reductions, Matsubara tail and mu search",
+                 "mu_tol": MIXED_MU_TOL * s.n_target,
+                 "roofline": {"bound": "alu", "achieved": mt["flops"] / (mt["kernel_ms"] / 1e3) / 1e12,
+                              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": mt["flops"] / (mt["kernel_ms"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                              "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"},
+                 "arithmetic": "FP32 embedding and Gauss-Jordan inverse (register tiles); FP64 Matsubara "
+                               "sums, tail, k-sums and mu search; G P^+ and P G refined once with an "
+                               "FP32-pair residual",
                  "kernel_choice": gm.tuning_log(), "gpu_launches": mt["launches"]}
         gm.close()
+        # the FP32-pair mode (GF_PREC_PAIR, ~1e-14 of FP64), a few steps
+        ps_, pw_ = min(args.steps, 3), min(args.warmup, 3)
+        pl = run_leg("pair", ps_, pw_, False)
+        gp = pl["g"]
+        n_p, _ = gp.occupation([info["mu"]])
+        pt = pl["totals"]
+        mixed["pair_mode"] = {"value": pt["points"] * ws / pl["elapsed"], "unit": UNIT, "steps": ps_,
+                              "ms_per_step": pl["elapsed"] / ps_ * 1e3,
+                              "speedup_vs_fp64_gpu": (pt["points"] / pl["elapsed"]) / (totals["points"] / elapsed),
+                              "N_rel_err_vs_fp64_gpu": abs(n_p[0] - info["N"]) / abs(info["N"]),
+                              "arithmetic": "FP32 pairs (hi + lo, error-free transformations) on the FP32 "
+                                            "pipes; FP64 reductions, tail and mu search",
+                              "kernel_choice": gp.tuning_log()}
+        gp.close()
 
     lowrank = None
     if args.precision == "fp64" and not args.no_mixed:
         # the same step with the eigenbasis (Woodbury) algorithm: a different algorithm, reported
         # beside the direct path's numbers, never in them
-        lr = run_leg("fp64", args.steps, args.warmup, False, lowrank=True)
+        ls_, lw_ = min(args.steps, 5), min(args.warmup, 3)
+        lr = run_leg("fp64", ls_, lw_, False, lowrank=True)
         gr = lr["g"]
         n_lr, _ = gr.occupation([info["mu"]])
         gl_lr = gr.local([info["mu"]])
         gl_fp = g.local([info["mu"]])
         lt = lr["totals"]
         # and with GF_PREC_MIXED (FP32-pair band sums, FP64 m x m algebra)
-        ml = run_leg("mixed", args.steps, args.warmup, False, lowrank=True)
+        ml = run_leg("mixed", ls_, lw_, False, lowrank=True)
         gml = ml["g"]
         n_ml, _ = gml.occupation([info["mu"]])
         mlt = ml["totals"]
         mixed_lowrank = {"value": mlt["points"] * ws / ml["elapsed"], "unit": UNIT,
-                         "ms_per_step": ml["elapsed"] / args.steps * 1e3,
+                         "ms_per_step": ml["elapsed"] / ls_ * 1e3, "steps": ls_,
                          "speedup_vs_direct_fp64_gpu": (mlt["points"] / ml["elapsed"]) / (totals["points"] / elapsed),
                          "N_rel_err_vs_direct": abs(n_ml[0] - info["N"]) / abs(info["N"]),
                          "gpu_launches": mlt["launches"]}
         gml.close()
         lowrank = {"value": lt["points"] * ws / lr["elapsed"], "unit": UNIT,
-                   "ms_per_step": lr["elapsed"] / args.steps * 1e3,
+                   "ms_per_step": lr["elapsed"] / ls_ * 1e3, "steps": ls_,
                    "speedup_vs_direct_fp64_gpu": (lt["points"] / lr["elapsed"]) / (totals["points"] / elapsed),
                    "N_rel_err_vs_direct": abs(n_lr[0] - info["N"]) / abs(info["N"]),
                    "G_loc_rel_err_vs_direct": float((gl_lr - gl_fp).abs().max() / gl_fp.abs().max()),
@@ -737,9 +819,20 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_sample(s, info["mu"], args.cpu_seconds)
+    nio = batched = None
+    if rank == 0 and ws == 1 and args.precision == "fp64" and not (args.nk or args.n_iw):
+        import oracle
+        o = oracle.get()
+        o.set_threads(cpu_cores())
+        if not args.no_nio:
+            nio = nio_leg(gf, synth, o)
+        if not args.no_batched:
+            batched = batched_leg(gf, synth, o, nk_scale=args.nk_scale)
 
     if args.precision == "fp64":
         peak, peak_source = FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz"
+    elif args.precision == "mixed":
+        peak, peak_source = FP32_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
     else:
         peak, peak_source = MIXED_PEAK_TFLOPS, ("FP32 pipes: 152 SMs x 128 lanes x 2.07 GHz / 48 FP32 "
                                                 "operations per FP32-pair complex multiply-add x 8 flop")
@@ -748,10 +841,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32x2",
+            "dtype": {"fp64": "f64", "mixed": "f32", "pair": "f32x2"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD,
-                       "step": "find_mu (Newton from mu=0, tol 1e-10) + fused G_loc/rho_k/N/dN/n_corr "
+                       "step": "find_mu (Newton from mu=0, tol 1e-10; mixed legs 1e-8 N_target) + fused G_loc/rho_k/N/dN/n_corr "
                                "pass + adjoint (Sigma_bar, mu_bar)",
                        "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
@@ -761,8 +854,8 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": ncu_traffic() if args.precision == "fp64" else None,
-                         "kernel": "k_point_fp64" if args.precision == "fp64"
-                         else "k_point_df64 / k_point_df64r (autotuned)",
+                         "kernel": {"fp64": "k_point_fp64", "mixed": "k_point_f32r (autotuned tiles)",
+                                    "pair": "k_point_df64 / k_point_df64r (autotuned)"}[args.precision],
                          "peak_source": peak_source,
                          "kernel_share_of_step": totals["kernel_ms"] / 1e3 / elapsed,
                          "by_pass_tflops": {k: v["flops"] / max(v["kernel_ms"], 1e-9) / 1e9
@@ -772,6 +865,8 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": totals["launches"], "clocks": clk,
             "mixed": mixed,
             "lowrank": lowrank,
+            "nio_like": nio,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     g.close()

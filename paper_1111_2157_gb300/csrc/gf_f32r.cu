@@ -72,6 +72,134 @@ __device__ __forceinline__ float2 round_cf(const cf& a) {
   return make_float2(__fadd_rn(a.rh, a.rl), __fadd_rn(a.ih, a.il));
 }
 
+
+__device__ __forceinline__ float2 fconj(float2 a) { return make_float2(a.x, -a.y); }
+// pair += single: q = q + d with d much smaller than q
+__device__ __forceinline__ void add_single(cf& q, float2 d) {
+  float s, t;
+  two_sum(q.rh, d.x, s, t);
+  q.rh = s;
+  q.rl = __fadd_rn(q.rl, t);
+  two_sum(q.ih, d.y, s, t);
+  q.ih = s;
+  q.il = __fadd_rn(q.il, t);
+  cnorm(q);
+}
+// acc += a b for pair or single-word operands (single words enter exactly)
+__device__ __forceinline__ void pmac(cf& acc, const cf& a, float2 b) { cacc1(acc, a, b); }
+__device__ __forceinline__ void pmac(cf& acc, float2 a, const cf& b) { cacc1(acc, b, a); }
+__device__ __forceinline__ void pmac(cf& acc, const cf& a, const cf& b) { cacc(acc, a, b); }
+__device__ __forceinline__ void pmac(cf& acc, float2 a, float2 b) { cacc1(acc, cf{a.x, 0.f, a.y, 0.f}, b); }
+
+// C (R x C) = sum_k la(r, k) lb(k, c) in FP32; each thread computes 2 x 2 blocks
+// (two loaded values of each operand feed four multiply-adds).
+template <class LA, class LB, class ST>
+__device__ __forceinline__ void mm_f32(int R, int C, int K, LA la, LB lb, ST st) {
+  const int cb = (C + 1) >> 1, nw = ((R + 1) >> 1) * cb;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+    const int r0 = (w / cb) * 2, c0 = (w - (w / cb) * cb) * 2;
+    const int r1 = min(r0 + 1, R - 1), c1 = min(c0 + 1, C - 1);
+    float2 a00 = f2zero(), a01 = f2zero(), a10 = f2zero(), a11 = f2zero();
+    for (int k = 0; k < K; ++k) {
+      const float2 x0 = la(r0, k), x1 = la(r1, k), y0 = lb(k, c0), y1 = lb(k, c1);
+      fmac(a00, x0, y0);
+      fmac(a01, x0, y1);
+      fmac(a10, x1, y0);
+      fmac(a11, x1, y1);
+    }
+    st(r0, c0, a00);
+    if (c1 != c0) st(r0, c1, a01);
+    if (r1 != r0) {
+      st(r1, c0, a10);
+      if (c1 != c0) st(r1, c1, a11);
+    }
+  }
+}
+
+// C (R x C) = init(r, c) + sum_k la(r, k) lb(k, c) in FP32 pairs (operands pairs or
+// single words), 2 x 2 blocks per
+// thread; with S > 1 the k range is split in S parts whose partial sums go to
+// part[S][R][C] (pairs) and are added in part order (deterministic).  The
+// caller separates consecutive calls with a barrier; the function has its own
+// barrier only when S > 1.
+template <class LA, class LB, class IN, class ST>
+__device__ __forceinline__ void mm_pair(int R, int C, int K, int S, float4* part, LA la, LB lb, IN init,
+                                        ST st) {
+  const int cb = (C + 1) >> 1, nb = ((R + 1) >> 1) * cb, nw = nb * S;
+  const int kc = (K + S - 1) / S;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+    const int blk = w / S, sp = w - blk * S;
+    const int r0 = (blk / cb) * 2, c0 = (blk - (blk / cb) * cb) * 2;
+    const int r1 = min(r0 + 1, R - 1), c1 = min(c0 + 1, C - 1);
+    cf a00 = czero(), a01 = czero(), a10 = czero(), a11 = czero();
+    const int k0 = sp * kc, k1 = min(K, k0 + kc);
+    for (int k = k0; k < k1; ++k) {
+      const auto x0 = la(r0, k), x1 = la(r1, k);
+      const auto y0 = lb(k, c0), y1 = lb(k, c1);
+      pmac(a00, x0, y0);
+      pmac(a01, x0, y1);
+      pmac(a10, x1, y0);
+      pmac(a11, x1, y1);
+      if (((k - k0) & 15) == 15) {
+        cnorm(a00);
+        cnorm(a01);
+        cnorm(a10);
+        cnorm(a11);
+      }
+    }
+    cnorm(a00);
+    cnorm(a01);
+    cnorm(a10);
+    cnorm(a11);
+    if (S == 1) {
+      auto fin = [&](int r, int c, cf v) {
+        cf q = init(r, c);
+        float s, t;
+        two_sum(q.rh, v.rh, s, t);
+        q.rh = s;
+        q.rl = __fadd_rn(__fadd_rn(q.rl, v.rl), t);
+        two_sum(q.ih, v.ih, s, t);
+        q.ih = s;
+        q.il = __fadd_rn(__fadd_rn(q.il, v.il), t);
+        cnorm(q);
+        st(r, c, q);
+      };
+      fin(r0, c0, a00);
+      if (c1 != c0) fin(r0, c1, a01);
+      if (r1 != r0) {
+        fin(r1, c0, a10);
+        if (c1 != c0) fin(r1, c1, a11);
+      }
+    } else {
+      float4* pp = part + (size_t)sp * R * C;
+      pp[r0 * C + c0] = st4(a00);
+      if (c1 != c0) pp[r0 * C + c1] = st4(a01);
+      if (r1 != r0) {
+        pp[r1 * C + c0] = st4(a10);
+        if (c1 != c0) pp[r1 * C + c1] = st4(a11);
+      }
+    }
+  }
+  if (S > 1) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * C; e += blockDim.x) {
+      const int r = e / C, c = e - r * C;
+      cf q = init(r, c);
+      for (int sp = 0; sp < S; ++sp) {
+        const cf v = ld4(part[(size_t)sp * R * C + e]);
+        float s, t;
+        two_sum(q.rh, v.rh, s, t);
+        q.rh = s;
+        q.rl = __fadd_rn(__fadd_rn(q.rl, v.rl), t);
+        two_sum(q.ih, v.ih, s, t);
+        q.ih = s;
+        q.il = __fadd_rn(__fadd_rn(q.il, v.il), t);
+      }
+      cnorm(q);
+      st(r, c, q);
+    }
+  }
+}
 }  // namespace
 
 // Shared-memory layout of k_point_f32r in bytes.  T = Sigma P (embedding) lives in
@@ -102,18 +230,24 @@ __host__ __device__ inline LayoutF make_layout_f(int nbmax, int mmax, int mode) 
   o = (o + 15) & ~(size_t)15;
   L.oHii = o; o += 16 * (size_t)nbmax;               // H_ii (FP64)
   const bool refine = (mode & (kGloc | kAdj)) != 0;
-  o = (o + 15) & ~(size_t)15;
-  L.oW = o; o += refine ? 16 * mm : 0;   // P Y0 (pair), then Z0 P^+
-  L.oV = o; o += refine ? 16 * mm : 0;   // Sigma (P Y0) (pair)
-  L.oY0 = o; o += refine ? 8 * mn : 0;   // Y0 = X P^+ (N x m)
-  L.oR = o; o += refine ? 8 * mn : 0;    // residual (N x m or m x N)
-  L.odY = o; o += refine ? 8 * mn : 0;   // X R
   const bool adj = (mode & kAdj) != 0;
-  L.oZ0 = o; o += adj ? 8 * mn : 0;      // Z0 = P X (m x N)
-  L.odZ = o; o += adj ? 8 * mn : 0;      // R' X
-  L.oQa = o; o += adj ? 16 * mm : 0;     // A_k = P Y (pair)
-  L.oQb = o; o += adj ? 16 * mm : 0;     // B_k = Z Y (pair)
-  L.oMt = o; o += adj ? 16 * mm : 0;     // Gbar A_k^+ (pair)
+  auto take = [&o](size_t bytes) {  // 16-byte aligned region
+    o = (o + 15) & ~(size_t)15;
+    const size_t at = o;
+    o += bytes;
+    return at;
+  };
+  L.oW = take(refine ? 16 * mm : 0);   // P Y0 (pair), then Z0 P^+
+  L.oV = take(refine ? 16 * mm : 0);   // Sigma (P Y0) (pair)
+  L.oY0 = take(refine ? 8 * mn : 0);   // Y0 = X P^+ (N x m)
+  L.oR = take(refine ? 8 * mn : 0);    // residual (N x m or m x N); with dY: partial sums
+  L.odY = o; o += refine ? 8 * mn : 0; // X R (directly after R: 16 mn bytes together)
+  L.oZ0 = take(adj ? 8 * mn : 0);      // Z0 = P X (m x N)
+  L.odZ = take(adj ? 8 * mn : 0);      // R' X
+  L.oQa = take(adj ? 16 * mm : 0);     // A_k = P Y (pair)
+  L.oQb = take(adj ? 16 * mm : 0);     // B_k = Z Y (pair)
+  L.oMt = take(adj ? 16 * mm : 0);     // Gbar A_k^+ (pair)
+  o = (o + 15) & ~(size_t)15;
   L.oPiv = o; o += 3 * sizeof(int) * (size_t)nbmax;  // p, q = p^{-1}, row offsets
   L.bytes = o;
   return L;
@@ -144,6 +278,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_f32r(const PointParams p) 
   float4* sQa = reinterpret_cast<float4*>(smraw + L.oQa);
   float4* sQb = reinterpret_cast<float4*>(smraw + L.oQb);
   float4* sMt = reinterpret_cast<float4*>(smraw + L.oMt);
+  float4* sPart = reinterpret_cast<float4*>(smraw + L.oR);  // partial sums of mm_pair (R and dY regions)
   float2* sD = reinterpret_cast<float2*>(smraw + L.oD);
   double2* sHii = reinterpret_cast<double2*>(smraw + L.oHii);
   int* sPiv = reinterpret_cast<int*>(smraw + L.oPiv);
@@ -412,188 +547,107 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_f32r(const PointParams p) 
         cf zw;  // -(i w_n + mu) as a pair
         split(-mu, zw.rh, zw.rl);
         split(-wn, zw.ih, zw.il);
-        // Y0 = X P^+ (N x M);  Z0 = P X (M x N)
-        for (int e = tid; e < N * M; e += nthr) {
-          const int i = e / M, b = e - i * M;
-          float2 acc = f2zero();
-          for (int c = 0; c < N; ++c) fmac_cb(acc, sG[sRow[i] + sIdx[c]], sP[b * N + c]);
-          sY0[e] = acc;
-        }
-        if (adj) {
-          for (int e = tid; e < M * N; e += nthr) {
-            const int a = e / N, c = e - a * N;
-            const int colx = sIdx[c];
-            float2 acc = f2zero();
-            for (int i = 0; i < N; ++i) fmac(acc, sP[a * N + i], sG[sRow[i] + colx]);
-            sZ0[e] = acc;
-          }
-        }
+        const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
+        auto X = [&](int i, int c) { return sG[sRow[i] + sIdx[c]]; };
+        // Y0 = X P^+ (N x M)
+        mm_f32(N, M, N, X, [&](int c, int b) { return fconj(sP[b * N + c]); },
+               [&](int i, int b, float2 v) { sY0[i * M + b] = v; });
+        // Z0 = P X (M x N)
+        if (adj)
+          mm_f32(M, N, N, [&](int a, int i) { return sP[a * N + i]; }, X,
+                 [&](int a, int c, float2 v) { sZ0[a * N + c] = v; });
         __syncthreads();
-        // W = P Y0 (pairs)
-        for (int e = tid; e < M * M; e += nthr) {
-          const int a = e / M, b = e - a * M;
-          cf acc = czero();
-          #pragma unroll 1
-          for (int i = 0; i < N; ++i) {
-            cacc1(acc, ld4(Pkp[a * N + i]), sY0[i * M + b]);
-            if ((i & 15) == 15) cnorm(acc);
-          }
-          cnorm(acc);
-          sW[e] = st4(acc);
-        }
+        // W = P Y0 (pairs; the sum over bands split in S parts, partials in the R region)
+        const int S = max(1, min(4, N / M));
+        mm_pair(M, M, N, S, sPart, [&](int a, int i) { return ld4(Pkp[a * N + i]); },
+                [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
+                [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
         __syncthreads();
         // V = Sigma W (pairs)
-        {
-          const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            cf acc = czero();
-            #pragma unroll 1
-            for (int x = 0; x < M; ++x) cacc(acc, ld4(Sgp[a * M + x]), ld4(sW[x * M + b]));
-            cnorm(acc);
-            sV[e] = st4(acc);
-          }
-        }
+        mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(Sgp[a * M + x]); },
+                [&](int x, int b) { return ld4(sW[x * M + b]); }, [&](int, int) { return czero(); },
+                [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
         __syncthreads();
         // R = P^+ - A Y0 = P^+ - (i w + mu) Y0 + H Y0 + P^+ V  (pairs, rounded to FP32)
-        for (int e = tid; e < N * M; e += nthr) {
-          const int i = e / M, b = e - i * M;
-          cf acc = conj_cf(ld4(Pkp[b * N + i]));
-          cacc1(acc, zw, sY0[e]);
-          #pragma unroll 1
-          for (int c = 0; c < N; ++c) {
-            cacc1(acc, ld4(Hkp[i * N + c]), sY0[c * M + b]);
-            if ((c & 15) == 15) cnorm(acc);
-          }
-          #pragma unroll 1
-          for (int a = 0; a < M; ++a) cacc_ca(acc, ld4(Pkp[a * N + i]), ld4(sV[a * M + b]));
-          cnorm(acc);
-          sR[e] = round_cf(acc);
-        }
+        mm_pair(N, M, N, 1, sPart, [&](int i, int c) { return ld4(Hkp[i * N + c]); },
+                [&](int c, int b) { return sY0[c * M + b]; },
+                [&](int i, int b) {
+                  cf acc = conj_cf(ld4(Pkp[b * N + i]));
+                  cacc1(acc, zw, sY0[i * M + b]);
+                  for (int a = 0; a < M; ++a) cacc_ca(acc, ld4(Pkp[a * N + i]), ld4(sV[a * M + b]));
+                  return acc;
+                },
+                [&](int i, int b, const cf& v) { sR[i * M + b] = round_cf(v); });
         __syncthreads();
         // dY = X R (FP32);  Y = Y0 + dY
-        for (int e = tid; e < N * M; e += nthr) {
-          const int i = e / M, b = e - i * M;
-          float2 acc = f2zero();
-          for (int c = 0; c < N; ++c) fmac(acc, sG[sRow[i] + sIdx[c]], sR[c * M + b]);
-          sdY[e] = acc;
-        }
+        mm_f32(N, M, N, X, [&](int c, int b) { return sR[c * M + b]; },
+               [&](int i, int b, float2 v) { sdY[i * M + b] = v; });
         __syncthreads();
-        // P Y = W + P dY  (the second term in FP32)
+        // P Y = W + P dY (the second term in FP32)
         if (p.mode & kGloc) {
           double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            float2 d = f2zero();
-            for (int i = 0; i < N; ++i) fmac(d, sP[a * N + i], sdY[i * M + b]);
-            const double2 w = to_d2(ld4(sW[e]));
-            out[e] = make_double2(wk * (w.x + (double)d.x), wk * (w.y + (double)d.y));
-          }
+          mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
+                 [&](int i, int b) { return sdY[i * M + b]; },
+                 [&](int a, int b, float2 d) {
+                   const double2 w = to_d2(ld4(sW[a * M + b]));
+                   out[a * M + b] = make_double2(wk * (w.x + (double)d.x), wk * (w.y + (double)d.y));
+                 });
         }
         if (adj) {
-          // A_k = P Y in pairs (kept for the adjoint)
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            float2 d = f2zero();
-            for (int i = 0; i < N; ++i) fmac(d, sP[a * N + i], sdY[i * M + b]);
-            cf q = ld4(sW[e]);
-            float s, t;
-            two_sum(q.rh, d.x, s, t);
-            q.rh = s;
-            q.rl = __fadd_rn(q.rl, t);
-            two_sum(q.ih, d.y, s, t);
-            q.ih = s;
-            q.il = __fadd_rn(q.il, t);
-            cnorm(q);
-            sQa[e] = st4(q);
-          }
+          // A_k = P Y in pairs
+          mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
+                 [&](int i, int b) { return sdY[i * M + b]; },
+                 [&](int a, int b, float2 d) {
+                   cf q = ld4(sW[a * M + b]);
+                   add_single(q, d);
+                   sQa[a * M + b] = st4(q);
+                 });
           __syncthreads();
           // W' = Z0 P^+ (pairs), then V' = W' Sigma
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            cf acc = czero();
-            #pragma unroll 1
-            for (int i = 0; i < N; ++i) {
-              cacc1(acc, conj_cf(ld4(Pkp[b * N + i])), sZ0[a * N + i]);
-              if ((i & 15) == 15) cnorm(acc);
-            }
-            cnorm(acc);
-            sW[e] = st4(acc);
-          }
+          mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+                  [&](int i, int b) { return conj_cf(ld4(Pkp[b * N + i])); }, [&](int, int) { return czero(); },
+                  [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
           __syncthreads();
-          {
-            const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
-            for (int e = tid; e < M * M; e += nthr) {
-              const int a = e / M, b = e - a * M;
-              cf acc = czero();
-              #pragma unroll 1
-              for (int x = 0; x < M; ++x) cacc(acc, ld4(sW[a * M + x]), ld4(Sgp[x * M + b]));
-              cnorm(acc);
-              sV[e] = st4(acc);
-            }
-          }
+          mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(sW[a * M + x]); },
+                  [&](int x, int b) { return ld4(Sgp[x * M + b]); }, [&](int, int) { return czero(); },
+                  [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
           __syncthreads();
-          // R' = P - Z0 A = P - (i w + mu) Z0 + Z0 H + V' P  (pairs, rounded), m x N
-          for (int e = tid; e < M * N; e += nthr) {
-            const int a = e / N, c = e - a * N;
-            cf acc = ld4(Pkp[a * N + c]);
-            cacc1(acc, zw, sZ0[e]);
-            #pragma unroll 1
-            for (int i = 0; i < N; ++i) {
-              cacc1(acc, ld4(Hkp[i * N + c]), sZ0[a * N + i]);
-              if ((i & 15) == 15) cnorm(acc);
-            }
-            #pragma unroll 1
-            for (int b = 0; b < M; ++b) cacc(acc, ld4(sV[a * M + b]), ld4(Pkp[b * N + c]));
-            cnorm(acc);
-            sR[e] = round_cf(acc);
-          }
+          // R' = P - Z0 A = P - (i w + mu) Z0 + Z0 H + V' P  (pairs, rounded), M x N
+          mm_pair(M, N, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+                  [&](int i, int c) { return ld4(Hkp[i * N + c]); },
+                  [&](int a, int c) {
+                    cf acc = ld4(Pkp[a * N + c]);
+                    cacc1(acc, zw, sZ0[a * N + c]);
+                    for (int b = 0; b < M; ++b) cacc(acc, ld4(sV[a * M + b]), ld4(Pkp[b * N + c]));
+                    return acc;
+                  },
+                  [&](int a, int c, const cf& v) { sR[a * N + c] = round_cf(v); });
           __syncthreads();
           // dZ = R' X (FP32)
-          for (int e = tid; e < M * N; e += nthr) {
-            const int a = e / N, c = e - a * N;
-            const int colx = sIdx[c];
-            float2 acc = f2zero();
-            for (int i = 0; i < N; ++i) fmac(acc, sR[a * N + i], sG[sRow[i] + colx]);
-            sdZ[e] = acc;
-          }
+          mm_f32(M, N, N, [&](int a, int i) { return sR[a * N + i]; }, X,
+                 [&](int a, int c, float2 v) { sdZ[a * N + c] = v; });
           __syncthreads();
-          // B_k = Z Y = Z0 Y0 (pairs) + Z0 dY + dZ Y0 (FP32)
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            cf acc = czero();
-            float2 d = f2zero();
-            #pragma unroll 1
-            for (int i = 0; i < N; ++i) {
-              const float2 z = sZ0[a * N + i], y = sY0[i * M + b];
-              cacc1(acc, cf{z.x, 0.f, z.y, 0.f}, y);
-              fmac(d, z, sdY[i * M + b]);
-              fmac(d, sdZ[a * N + i], y);
-              if ((i & 15) == 15) cnorm(acc);
-            }
-            float s, t;
-            two_sum(acc.rh, d.x, s, t);
-            acc.rh = s;
-            acc.rl = __fadd_rn(acc.rl, t);
-            two_sum(acc.ih, d.y, s, t);
-            acc.ih = s;
-            acc.il = __fadd_rn(acc.il, t);
-            cnorm(acc);
-            sQb[e] = st4(acc);
-          }
+          // B_k = Z Y = Z0 Y0 (pairs of exact FP32 products) + Z0 dY + dZ Y0 (FP32)
+          mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+                  [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
+                  [&](int a, int b, const cf& v) { sQb[a * M + b] = st4(v); });
+          __syncthreads();
+          mm_f32(M, M, 2 * N,
+                 [&](int a, int k) { return k < N ? sZ0[a * N + k] : sdZ[a * N + k - N]; },
+                 [&](int k, int b) { return k < N ? sdY[k * M + b] : sY0[(k - N) * M + b]; },
+                 [&](int a, int b, float2 d) {
+                   cf q = ld4(sQb[a * M + b]);
+                   add_single(q, d);
+                   sQb[a * M + b] = st4(q);
+                 });
           __syncthreads();
           const bool have_gbar = (p.Gbd != nullptr);
           if (have_gbar) {
             const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
             // Mt = Gbar A_k^+ (pairs)
-            for (int e = tid; e < M * M; e += nthr) {
-              const int a = e / M, b = e - a * M;
-              cf acc = czero();
-              #pragma unroll 1
-              for (int c = 0; c < M; ++c) cacc_cb(acc, ld4(Gb[a * M + c]), ld4(sQa[b * M + c]));
-              cnorm(acc);
-              sMt[e] = st4(acc);
-            }
+            mm_pair(M, M, M, 1, sPart, [&](int a, int c) { return ld4(Gb[a * M + c]); },
+                    [&](int c, int b) { return conj_cf(ld4(sQa[b * M + c])); }, [&](int, int) { return czero(); },
+                    [&](int a, int b, const cf& v) { sMt[a * M + b] = st4(v); });
             // mu_bar partial: - w_k Re<Gbar, B_k>
             for (int e = tid; e < M * M; e += nthr) {
               const double2 gv = to_d2(ld4(Gb[e])), bv = to_d2(ld4(sQb[e]));
@@ -607,7 +661,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_f32r(const PointParams p) 
             const int a = e / M, b = e - a * M;
             cf acc = czero();
             if (have_gbar)
-              #pragma unroll 1
               for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sMt[c * M + b]));
             cnorm(acc);
             const double2 v = to_d2(acc);
