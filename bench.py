@@ -223,9 +223,9 @@ def run_reference(args):
 
 
 def run_peaks():
-    """Build paper_1111_2157_gb300/peaks.cu with nvcc and run it (prints one line per pipe)."""
+    """Build peaks.cu (beside this script) with nvcc and run it (prints one line per pipe)."""
     from paper_1111_2157_gb300 import build as gfbuild
-    src = ROOT / "paper_1111_2157_gb300" / "peaks.cu"
+    src = ROOT / "peaks.cu"
     exe = gfbuild.BUILD / "peaks"
     gfbuild.BUILD.mkdir(exist_ok=True)
     subprocess.run([gfbuild.nvcc(), *gfbuild.ARCH, "-O3", "-o", str(exe), str(src)], check=True)
