@@ -265,10 +265,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA: 152 SMs x 128 lane
 MIXED_MU_TOL = 1e-8  # mixed path: mu search to |N - N_target| <= 1e-8 N_target (FP32 noise ~1e-9)
 
 
-def _dev_context(gf, systems, precision, graph=False, lowrank=False):
-    """Context with the inputs uploaded from device tensors (resident in HBM)."""
+def _dev_context(gf, systems, precision, graph=False, lowrank=False, input_dtype="c128"):
+    """Context with the inputs uploaded from device tensors (resident in HBM); with
+    input_dtype="per_system" each system is uploaded in its own dtype (complex64 systems
+    as complex64)."""
     import torch
-    g = gf.GreensFunction.for_systems(systems, precision=precision, graph=graph, lowrank=lowrank)
+    g = gf.GreensFunction.for_systems(systems, precision=precision, graph=graph, lowrank=lowrank,
+                                      input_dtype=input_dtype)
     g.set_hamiltonian(torch.from_numpy(_pack([_pack(s.H) for s in systems])).cuda())
     g.set_projectors(torch.from_numpy(_pack([_pack(s.P) for s in systems])).cuda())
     g.set_sigma(torch.from_numpy(_pack([s.sigma for s in systems])).cuda(),
@@ -341,23 +344,37 @@ def nio_leg(gf, synth, o, nk=4096, n_iw=2048):
     return out
 
 
+def _as_uploaded(synth, s):
+    """A complex64 system as the library receives it (inputs rounded to complex64)."""
+    if s.dtype != "c64":
+        return s
+    r = lambda a: np.asarray(a).astype(np.complex64).astype(np.complex128)  # noqa: E731
+    H = [r(h) for h in s.H] if isinstance(s.H, list) else r(s.H)
+    P = [r(p) for p in s.P] if isinstance(s.P, list) else r(s.P)
+    return synth.System(H, P, synth.PoleSigma(r(s.pole.sigma_inf), s.pole.p, s.pole.V), r(s.sigma),
+                        s.beta, s.n_target, dtype="c64")
+
+
 def batched_leg(gf, synth, o, nk_scale=1.0):
-    """Batched workload: 8 systems with ragged windows in one launch per window bucket, FP64
-    and mixed N(mu) passes, one launch per system, and a graph-replayed mixed mu search."""
+    """Batched workload: 8 systems with ragged windows, half of them complex64 and half
+    complex128, in one context and one launch per window bucket: FP64 and mixed N(mu) passes,
+    one launch per system, and a graph-replayed mixed mu search."""
     systems = synth.batched(nk_scale=nk_scale).systems
+    pd = "per_system"
     pts = sum(sy.nk * sy.n_iw for sy in systems)
     mus = [0.0] * len(systems)
     out = {"config": (f"8 systems, N_k per system {[sy.nk for sy in systems]}, N_b(k) uniform in [48, 128], "
-                      f"m {[sy.m for sy in systems]}, N_w=1024, beta=40 (k-sets x {nk_scale})"),
+                      f"m {[sy.m for sy in systems]}, N_w=1024, beta=40 (k-sets x {nk_scale}); inputs "
+                      f"{[sy.dtype for sy in systems]} in one context"),
            "points_per_pass": pts}
-    g64 = _dev_context(gf, systems, "fp64")
+    g64 = _dev_context(gf, systems, "fp64", input_dtype=pd)
     (n64, d64), t64 = _sync_time(lambda: g64.occupation(mus))
     s64 = g64.stats()
     out["fp64"] = {"pass_s": t64, "pass_kernel_s": s64["kernel_ms"] / 1e3,
                    "points_per_s": pts / (s64["kernel_ms"] / 1e3), "launches": s64["launches"],
                    "kernel_tflops": s64["flops"] / s64["kernel_ms"] / 1e9}
     g64.close()
-    gm = _dev_context(gf, systems, "mixed")
+    gm = _dev_context(gf, systems, "mixed", input_dtype=pd)
     gm.occupation(mus)
     (nm, dm), tm = _sync_time(lambda: gm.occupation(mus))
     sm_ = gm.stats()
@@ -365,13 +382,13 @@ def batched_leg(gf, synth, o, nk_scale=1.0):
     gm.close()
     t_per, n_launch = 0.0, 0
     for sy in systems:
-        gi = _dev_context(gf, [sy], "mixed")
+        gi = _dev_context(gf, [sy], "mixed", input_dtype=pd)
         gi.occupation([0.0])
         _, t = _sync_time(lambda: gi.occupation([0.0]))
         t_per += t
         n_launch += gi.stats()["launches"]
         gi.close()
-    gg = _dev_context(gf, systems, "mixed", graph=True)
+    gg = _dev_context(gf, systems, "mixed", graph=True, input_dtype=pd)
     targets = [sy.n_target for sy in systems]
     (mu_g, it_g), t_g = _sync_time(lambda: gg.find_mu(targets, 0.0, tol=MIXED_MU_TOL * min(targets)))
     pts_g = gg.stats()["points"]
@@ -380,9 +397,10 @@ def batched_leg(gf, synth, o, nk_scale=1.0):
     errs = []
     for i in (0, 1):
         sy = systems[i]
-        sub = synth.System(sy.H[:4], sy.P[:4], sy.pole, sy.sigma, sy.beta, sy.n_target)
-        r_o = o.density(sub.H, sub.P, sub.sigma, sub.sigma_inf, sub.beta, 0.0, want_rho=False)
-        gs = _dev_context(gf, [sub], "mixed")
+        sub = synth.System(sy.H[:4], sy.P[:4], sy.pole, sy.sigma, sy.beta, sy.n_target, dtype=sy.dtype)
+        up = _as_uploaded(synth, sub)
+        r_o = o.density(up.H, up.P, up.sigma, up.sigma_inf, up.beta, 0.0, want_rho=False)
+        gs = _dev_context(gf, [sub], "mixed", input_dtype=pd)
         n_s, _ = gs.occupation([0.0])
         gs.close()
         errs.append(abs(float(n_s[0]) - r_o["N"]) / r_o["N"])
@@ -398,8 +416,8 @@ def batched_leg(gf, synth, o, nk_scale=1.0):
                     "graph_find_mu_points_per_s": pts_g / t_g, "kernel_choice": log}
     out["N_rel_err_mixed_vs_fp64_gpu"] = float(np.max(np.abs(nm - n64) / n64))
     out["dN_dmu_rel_err_mixed_vs_fp64_gpu"] = float(np.max(np.abs(dm - d64) / d64))
-    out["N_rel_err_vs_oracle"] = {"mixed": max(errs), "sample": "systems 0 and 1, k-points 0-3 each, "
-                                                                 "all frequencies, mu = 0"}
+    out["N_rel_err_vs_oracle"] = {"mixed": max(errs), "sample": "systems 0 (complex128) and 1 (complex64), "
+                                                                 "k-points 0-3 each, all frequencies, mu = 0"}
     return out
 
 

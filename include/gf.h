@@ -23,6 +23,11 @@
  *  - Complex numbers are interleaved (re, im).  Arrays are row-major.
  *  - Energies in eV, beta in 1/eV.
  *  - k-points are grouped by system: k_system[] must be non-decreasing.
+ *  - Inputs of several systems are packed system after system.  With
+ *    gf_desc.system_dtype each system's block is stored in that system's dtype
+ *    (complex128: 16 bytes, complex64: 8 bytes per number), so one context
+ *    holds complex128 and complex64 systems; complex64 numbers are widened
+ *    exactly on the device.
  *  - Pointer arguments named *_ptr may point to host memory (pageable or
  *    pinned) or to device memory of the context's device; the library tells
  *    them apart through unified addressing.  Input arrays are copied into
@@ -89,6 +94,8 @@ typedef struct {
     int32_t device;           /* CUDA device ordinal                                             */
     void *stream;             /* cudaStream_t to order all work on, or NULL (legacy default)     */
     int32_t flags;            /* GF_FLAG_* bits                                                  */
+    const int32_t *system_dtype; /* host [n_systems]: gf_dtype of each system's blocks in the    */
+                              /* arrays given to gf_set_*, or NULL: input_dtype for every system */
 } gf_desc;
 
 /* gf_desc.flags: replay the N(mu) evaluation (gf_occupation, each step of
@@ -203,10 +210,9 @@ gf_status gf_backward(gf_ctx *ctx, const double *mu, const void *gloc_bar_ptr, c
  * about 32 bytes per (k, frequency chunk) item plus 56 bytes per k-point
  * (n_k = 1000 with 1024 frequencies needs about 0.5 MiB); larger problems,
  * and windows whose matrix does not fit in shared memory, return GF_EINVAL.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call shares the one array and overwrites it, so calls whose work overlaps on
- * the GPU (other streams, other host threads) race: serialise them.
+ * Each call looks up the array's address on the current device.  Every call
+ * shares the one array and overwrites it, so calls whose work overlaps on the
+ * GPU (other streams, other host threads) race: serialise them.
  * Errors (message in gf_last_error(NULL)): GF_EINVAL, GF_ESINGULAR, GF_ECUDA. */
 gf_status gf_occupation_static(const void *h_dev, const void *p_dev, const void *sigma_dev,
                                const void *sigma_inf_dev, int32_t n_k, int32_t nb, int32_t m,

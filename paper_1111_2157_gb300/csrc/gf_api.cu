@@ -638,6 +638,26 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
   c->totH = offH;
   c->totP = offP;
   c->totNb = offD;
+  c->sys_dtype.resize(c->n_sys);
+  c->sysH.resize(c->n_sys + 1);
+  c->sysD.resize(c->n_sys + 1);
+  c->sysP.resize(c->n_sys + 1);
+  c->sysSig.resize(c->n_sys + 1);
+  c->sysSinf.resize(c->n_sys + 1);
+  for (int s = 0; s < c->n_sys; ++s) {
+    const SInfo& si = c->sinfo[s];
+    c->sys_dtype[s] = d->system_dtype ? d->system_dtype[s] : d->input_dtype;
+    c->sysH[s] = c->kinfo[si.k0].offH;
+    c->sysD[s] = c->offD[si.k0];
+    c->sysP[s] = c->kinfo[si.k0].offP;
+    c->sysSig[s] = si.offSig;
+    c->sysSinf[s] = si.offSinf;
+  }
+  c->sysH[c->n_sys] = c->totH;
+  c->sysD[c->n_sys] = c->totNb;
+  c->sysP[c->n_sys] = c->totP;
+  c->sysSig[c->n_sys] = c->totSig;
+  c->sysSinf[c->n_sys] = c->totSinf;
   for (int k = 0; k < c->n_k; ++k) {
     const int bk = gf_bucket(c->nb[k]);
     c->bucket_nbmax[bk] = std::max(c->bucket_nbmax[bk], c->nb[k]);
@@ -808,6 +828,9 @@ gf_status gf_create(gf_ctx** out, const gf_desc* d) try {
   if (d->precision != GF_PREC_FP64 && d->precision != GF_PREC_MIXED && d->precision != GF_PREC_PAIR)
     return bad("bad precision");
   if (d->input_dtype != GF_C128 && d->input_dtype != GF_C64) return bad("bad input_dtype");
+  if (d->system_dtype)
+    for (int s = 0; s < d->n_systems; ++s)
+      if (d->system_dtype[s] != GF_C128 && d->system_dtype[s] != GF_C64) return bad("bad system_dtype");
   if (d->tail_order != 1 && d->tail_order != 2) return bad("tail_order must be 1 or 2");
   gf_ctx* c = new (std::nothrow) gf_ctx();
   if (!c) {
@@ -866,7 +889,7 @@ gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) try 
     gf_status st = GF_OK;
     cudaError_t e = ensure(diag, sizeof(double2) * c->totNb);
     if (e != cudaSuccess) return fail(c, GF_ENOMEM, "allocation of the diagonal staging failed");
-    st = load_complex(c, h, c->totNb, diag.as<double2>());
+    st = load_complex(c, h, c->sysD, diag.as<double2>());
     if (st == GF_OK) {
       e = gf::launch_diag_to_dense(c->kinfo_d.as<KInfo>(), diag.as<double2>(), c->offD_d.as<int64_t>(),
                                    c->n_k, c->H.as<double2>(), c->stream);
@@ -876,7 +899,7 @@ gf_status gf_set_hamiltonian(gf_ctx* c, const void* h, int32_t is_diagonal) try 
     release(diag);
     if (st) return st;
   } else {
-    gf_status st = load_complex(c, h, c->totH, c->H.as<double2>());
+    gf_status st = load_complex(c, h, c->sysH, c->H.as<double2>());
     if (st) return st;
     GF_CU(cudaStreamSynchronize(c->stream));
   }
@@ -898,7 +921,7 @@ gf_status gf_set_projectors(gf_ctx* c, const void* p) try {
   if (!c) return GF_EINVAL;
   if (!p) return fail(c, GF_EINVAL, "p_ptr is NULL");
   DeviceGuard guard(c->device);
-  gf_status st = load_complex(c, p, c->totP, c->P.as<double2>());
+  gf_status st = load_complex(c, p, c->sysP, c->P.as<double2>());
   if (st) return st;
   st = derive_f32(c, c->P, c->Pd, &c->Ps, c->totP);
   if (st) return st;
@@ -916,9 +939,9 @@ gf_status gf_set_sigma(gf_ctx* c, const void* sig, const void* sinf) try {
   if (!c) return GF_EINVAL;
   if (!sig || !sinf) return fail(c, GF_EINVAL, "sigma_iw_ptr or sigma_inf_ptr is NULL");
   DeviceGuard guard(c->device);
-  gf_status st = load_complex(c, sig, c->totSig, c->Sig.as<double2>());
+  gf_status st = load_complex(c, sig, c->sysSig, c->Sig.as<double2>());
   if (st) return st;
-  st = load_complex(c, sinf, c->totSinf, c->Sinf.as<double2>());
+  st = load_complex(c, sinf, c->sysSinf, c->Sinf.as<double2>());
   if (st) return st;
   st = derive_f32(c, c->Sig, c->Sd, &c->Ss, c->totSig);
   if (st) return st;

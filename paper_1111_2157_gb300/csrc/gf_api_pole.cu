@@ -173,10 +173,13 @@ gf_status gf_set_sigma_poles(gf_ctx* c, const int32_t* n_poles, const double* po
   if (offp > 0) {
     GF_CU(cudaMemcpyAsync(c->poles.p, hp.data(), sizeof(double) * offp, cudaMemcpyHostToDevice,
                           c->stream));
-    gf_status st = load_complex(c, v, offV, c->Vp.as<double2>());
+    std::vector<int64_t> sysV(c->n_sys + 1);
+    for (int s = 0; s < c->n_sys; ++s) sysV[s] = pinfo[s].offV;
+    sysV[c->n_sys] = offV;
+    gf_status st = load_complex(c, v, sysV, c->Vp.as<double2>());
     if (st) return st;
   }
-  gf_status st = load_complex(c, sinf, c->totSinf, c->Sinf_p.as<double2>());
+  gf_status st = load_complex(c, sinf, c->sysSinf, c->Sinf_p.as<double2>());
   if (st) return st;
   GF_CU(cudaMemcpyAsync(c->pinfo_d.p, pinfo.data(), sizeof(gf::PInfo) * c->n_sys,
                         cudaMemcpyHostToDevice, c->stream));
@@ -286,7 +289,7 @@ gf_status gf_set_projectors_lowdin(gf_ctx* c, const void* w, void* p_out) try {
   if (c->mmax > 32) return fail(c, GF_EINVAL, "the projector orthonormalisation takes m <= 32");
   DeviceGuard guard(c->device);
   GF_CU(ensure(c->wraw, sizeof(double2) * c->totP));
-  gf_status st = load_complex(c, w, c->totP, c->wraw.as<double2>());
+  gf_status st = load_complex(c, w, c->sysP, c->wraw.as<double2>());
   if (st) return st;
   GF_CU(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
   GF_CU(gf::launch_lowdin(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_k, c->mmax,

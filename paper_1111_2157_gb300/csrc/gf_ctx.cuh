@@ -101,6 +101,11 @@ inline int gf_bucket(int nb) {
 
 struct gf_ctx {
   int n_sys = 0, n_k = 0, n_iw = 0, precision = 0, in_dtype = 0, tail_order = 2, device = 0;
+  // input dtype of each system's blocks (gf_desc.system_dtype, else in_dtype for all), and the
+  // first complex element of each system in the packed H, diagonal-H, P, Sigma and Sigma_inf
+  // arrays ([n_sys + 1], last = total)
+  std::vector<int> sys_dtype;
+  std::vector<int64_t> sysH, sysD, sysP, sysSig, sysSinf;
   cudaStream_t stream = nullptr;
   std::vector<int> nb, ksys, msys;
   std::vector<double> beta, wk;
@@ -202,16 +207,39 @@ inline gf_status caught(const gf_ctx* c) noexcept {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                     \
   } while (0)
 
-// Copy n complex numbers of the input dtype from a host or device pointer into
-// a complex128 device array.
-inline gf_status load_complex(gf_ctx* c, const void* src, int64_t n, double2* dst) {
+// Copy n complex numbers of one dtype from a host or device pointer into a complex128
+// device array (complex64 upcast on the device).
+inline gf_status load_complex_dtype(gf_ctx* c, const void* src, int64_t n, int dtype, double2* dst) {
   if (n <= 0) return GF_OK;
-  if (c->in_dtype == GF_C128) {
+  if (dtype == GF_C128) {
     GF_CU(cudaMemcpyAsync(dst, src, (size_t)n * 16, cudaMemcpyDefault, c->stream));
   } else {
     GF_CU(ensure(c->stage, (size_t)n * 8));
     GF_CU(cudaMemcpyAsync(c->stage.p, src, (size_t)n * 8, cudaMemcpyDefault, c->stream));
     GF_CU(gf::launch_upcast(c->stage.as<float2>(), dst, n, c->stream));
+  }
+  return GF_OK;
+}
+
+// Copy a packed per-system input (system s holds complex elements [sysoff[s], sysoff[s+1]) of
+// the destination, stored in the source in the dtype of system s, the systems' blocks one
+// after the other) into a complex128 device array.  Consecutive systems of one dtype move
+// in one copy.
+inline gf_status load_complex(gf_ctx* c, const void* src, const std::vector<int64_t>& sysoff,
+                              double2* dst) {
+  const unsigned char* in = static_cast<const unsigned char*>(src);
+  size_t byte = 0;
+  for (int s0 = 0; s0 < c->n_sys;) {
+    int s1 = s0 + 1;
+    while (s1 < c->n_sys && c->sys_dtype[s1] == c->sys_dtype[s0]) ++s1;
+    const int64_t e0 = sysoff[s0], n = sysoff[s1] - e0;
+    const int dt = c->sys_dtype[s0];
+    gf_status st = load_complex_dtype(c, in + byte, n, dt, dst + e0);
+    if (st) return st;
+    byte += (size_t)n * (dt == GF_C128 ? 16 : 8);
+    // the staging buffer of a complex64 run is reused by the next run: wait for the upcast
+    if (dt == GF_C64 && s1 < c->n_sys) GF_CU(cudaStreamSynchronize(c->stream));
+    s0 = s1;
   }
   return GF_OK;
 }

@@ -450,7 +450,8 @@ __global__ void k_gq_reduce(const KInfo* __restrict__ kinfo, const SInfo* __rest
   acc[si.offSig + t] = v;
 }
 
-// E_inf,k = P_k^+ Sigma_inf P_k and trHE_k = Re Tr(H_k + E_inf,k).  One CTA per k.
+// E_inf,k = P_k^+ Sigma_inf P_k and trHE_k = Re Tr(H_k + E_inf,k) (by trhe_partial).  One CTA
+// per k.
 __global__ void __launch_bounds__(kThreads) k_einf(const KInfo* __restrict__ kinfo,
                                                    const SInfo* __restrict__ sinfo,
                                                    const double2* __restrict__ H,
@@ -465,7 +466,6 @@ __global__ void __launch_bounds__(kThreads) k_einf(const KInfo* __restrict__ kin
   const int N = ki.nb, M = si.m;
   const double2* Pk = P + ki.offP;
   const double2* S = Sinf + si.offSinf;
-  double tr = 0.0;
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
     double2 v = make_double2(0.0, 0.0);
@@ -475,9 +475,8 @@ __global__ void __launch_bounds__(kThreads) k_einf(const KInfo* __restrict__ kin
       cmac_ca(v, Pk[a * N + i], t);
     }
     Einf[ki.offH + e] = v;
-    if (i == j) tr += v.x + H[ki.offH + e].x;
   }
-  const double t = block_sum(tr, red);
+  const double t = block_sum(trhe_partial(H + ki.offH, Pk, S, N, M, threadIdx.x, kThreads), red);
   if (threadIdx.x == 0) trHE[k] = t;
 }
 

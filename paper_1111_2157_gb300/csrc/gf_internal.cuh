@@ -131,6 +131,28 @@ struct PoleParams {
 
 __host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
 
+// Thread t's share (of nthr threads) of Re Tr H_k + Re Tr(Sigma_inf P_k P_k^+), the trace
+// of the first-moment matrix H_k + P_k^+ Sigma_inf P_k that the tail needs; summing the
+// shares over the threads gives the trace.  (P P^+)_ba = sum_i P_bi conj(P_ai).  Shared by
+// the context path (k_einf) and the allocation-free path so that both compute it alike.
+__device__ inline double trhe_partial(const double2* __restrict__ Hk, const double2* __restrict__ Pk,
+                                      const double2* __restrict__ S, int nb, int m, int t, int nthr) {
+  double v = 0.0;
+  for (int i = t; i < nb; i += nthr) v += Hk[(int64_t)i * nb + i].x;
+  for (int e = t; e < m * m; e += nthr) {
+    const int a = e / m, b = e - a * m;
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      const double2 x = Pk[b * nb + i], y = Pk[a * nb + i];
+      re = fma(x.x, y.x, fma(x.y, y.y, re));
+      im = fma(x.y, y.x, fma(-x.x, y.y, im));
+    }
+    const double2 sv = S[a * m + b];
+    v = fma(sv.x, re, fma(-sv.y, im, v));
+  }
+  return v;
+}
+
 // Eigenbasis data of the low-rank path: H_k = U diag(eps) U^+, Pt = P_k U.
 struct LowRank {
   const double* eps;     // [sum_k N_b] at offD[k]

@@ -12,7 +12,6 @@
 // the outputs; the same point kernel as gf_occupation does the work.
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 
 #include "gf.h"
 #include "gf_internal.cuh"
@@ -20,12 +19,8 @@
 namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)4 << 20;  // 4 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
-
-std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -50,8 +45,8 @@ StaticLayout static_layout(int n_k, int n_items) {
   return L;
 }
 
-// Tables of one uniform system and trHE_k = Re Tr H_k + Re Tr(Sigma_inf P_k P_k^+).
-// One CTA per k.
+// Tables of one uniform system and trHE_k = Re Tr H_k + Re Tr(Sigma_inf P_k P_k^+) (the same
+// trhe_partial as the context path).  One CTA per k.
 __global__ void __launch_bounds__(256) k_static_setup(
     const double2* __restrict__ H, const double2* __restrict__ P, const double2* __restrict__ Sinf,
     int n_k, int nb, int m, int n_chunks, int chunk_w, int n_iw, double beta, double tailc, double mu,
@@ -89,22 +84,8 @@ __global__ void __launch_bounds__(256) k_static_setup(
     it.chunk = ch;
     items[(int64_t)k * n_chunks + ch] = it;
   }
-  const double2* Hk = H + (int64_t)k * nb * nb;
-  const double2* Pk = P + (int64_t)k * m * nb;
-  double v = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += Hk[(int64_t)i * nb + i].x;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int a = e / m, b = e - a * m;
-    // (P P^+)_ba = sum_i P_bi conj(P_ai); Re(Sinf_ab (P P^+)_ba)
-    double re = 0.0, im = 0.0;
-    for (int i = 0; i < nb; ++i) {
-      const double2 x = Pk[b * nb + i], y = Pk[a * nb + i];
-      re = fma(x.x, y.x, fma(x.y, y.y, re));
-      im = fma(x.y, y.x, fma(-x.x, y.y, im));
-    }
-    const double2 s = Sinf[a * m + b];
-    v = fma(s.x, re, fma(-s.y, im, v));
-  }
+  double v = gf::trhe_partial(H + (int64_t)k * nb * nb, P + (int64_t)k * m * nb, Sinf, nb, m,
+                              threadIdx.x, blockDim.x);
   for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
@@ -115,24 +96,18 @@ __global__ void __launch_bounds__(256) k_static_setup(
   }
 }
 
-// Device address of g_scratch for the current device, looked up once per device.
+// Device address of g_scratch on the current device.  Looked up on every call (about a
+// microsecond): a cached address would go stale after cudaDeviceReset or when another
+// context becomes current on the device, and the module is then loaded afresh.
 gf_status scratch_for_current_device(unsigned char** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    gf::set_global_error("gf_occupation_static: no current CUDA device");
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e != cudaSuccess || !ptr) {
+    gf::set_global_error(e != cudaSuccess ? cudaGetErrorString(e)
+                                          : "gf_occupation_static: no device address for the scratch");
     return GF_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
-    if (e != cudaSuccess || !ptr) {
-      gf::set_global_error(cudaGetErrorString(e));
-      return GF_ECUDA;
-    }
-    g_scratch_addr[dev] = ptr;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *out = static_cast<unsigned char*>(ptr);
   return GF_OK;
 }
 

@@ -45,7 +45,7 @@ class GFDesc(ctypes.Structure):
                 ("beta", ctypes.POINTER(ctypes.c_double)), ("k_weight", ctypes.POINTER(ctypes.c_double)),
                 ("precision", ctypes.c_int32), ("input_dtype", ctypes.c_int32),
                 ("tail_order", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("system_dtype", ctypes.POINTER(ctypes.c_int32))]
 GF_FLAG_GRAPH = 1
 GF_FLAG_LOWRANK = 2
 
@@ -160,11 +160,52 @@ class _Arg:
             self.ptr = self.obj.ctypes.data
 
 
+def _flat(x):
+    import torch
+    if isinstance(x, torch.Tensor):
+        return x.reshape(-1)
+    return np.asarray(x).reshape(-1)
+
+
+class _SysArg:
+    """Packed per-system input with a dtype per system: system s's block (counts[s] complex
+    numbers) converted to dtypes[s] ("c128"/"c64"), the blocks concatenated as raw bytes.
+    x is one packed array of sum(counts) numbers or a list of per-system arrays."""
+
+    def __init__(self, x, counts, dtypes):
+        import torch
+        if isinstance(x, (list, tuple)):
+            parts = [_flat(p) for p in x]
+        else:
+            flat, parts, off = _flat(x), [], 0
+            for n in counts:
+                parts.append(flat[off:off + n])
+                off += n
+        if any(len(p) != n for p, n in zip(parts, counts)) or len(parts) != len(counts):
+            raise ValueError("per-system input sizes do not match the context")
+        cd = {"c128": "complex128", "c64": "complex64"}
+        if any(isinstance(p, torch.Tensor) for p in parts):
+            dev = next(p.device for p in parts if isinstance(p, torch.Tensor))
+            bufs = []
+            for p, d in zip(parts, dtypes):
+                t = p if isinstance(p, torch.Tensor) else torch.from_numpy(np.asarray(p))
+                t = t.to(device=dev, dtype=getattr(torch, cd[d])).contiguous()
+                bufs.append(torch.view_as_real(t).reshape(-1).view(torch.uint8))
+            self.obj = torch.cat(bufs)
+            self.ptr = self.obj.data_ptr()
+        else:
+            self.obj = np.concatenate([np.ascontiguousarray(p, dtype=cd[d]).view(np.uint8)
+                                       for p, d in zip(parts, dtypes)])
+            self.ptr = self.obj.ctypes.data
+
+
 class GreensFunction:
     """One libgf context: inputs live on the device, every call runs the CUDA path.
 
     nb: int (uniform) or per-k sequence; m and beta: per system (scalars for one
-    system); k_system: per-k system index (non-decreasing) for several systems.
+    system); k_system: per-k system index (non-decreasing) for several systems;
+    input_dtype: "c128", "c64", or a list with one of them per system (the inputs of the
+    gf_set_* calls are then packed with each system's block in its own dtype).
     """
 
     def __init__(self, nb, m, n_iw, beta, k_system=None, n_k=None, k_weight=None, precision="fp64",
@@ -172,6 +213,10 @@ class GreensFunction:
         import torch
         self.lib = load()
         self.device = int(device)
+        self.sys_dtypes = None
+        if isinstance(input_dtype, (list, tuple)):
+            self.sys_dtypes = [str(t) for t in input_dtype]
+            input_dtype = self.sys_dtypes[0]
         self.input_dtype = input_dtype
         m = np.atleast_1d(np.asarray(m, dtype=np.int32))
         beta = np.atleast_1d(np.asarray(beta, dtype=np.float64))
@@ -191,7 +236,11 @@ class GreensFunction:
         kw = None if k_weight is None else np.ascontiguousarray(k_weight, dtype=np.float64)
         if stream is None:
             stream = torch.cuda.current_stream(self.device).cuda_stream if torch.cuda.is_available() else 0
-        self._keep = [nb_arr, ks, m, beta, kw]
+        sd = (np.ascontiguousarray([DTYPE[t] for t in self.sys_dtypes], dtype=np.int32)
+              if self.sys_dtypes is not None else None)
+        if sd is not None and len(sd) != n_sys:
+            raise ValueError("input_dtype list must have one entry per system")
+        self._keep = [nb_arr, ks, m, beta, kw, sd]
         d = GFDesc()
         d.n_systems, d.n_k = n_sys, n_k
         d.nb = nb_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if nb_arr is not None else None
@@ -207,6 +256,7 @@ class GreensFunction:
         d.device = self.device
         d.stream = int(stream)
         d.flags = (GF_FLAG_GRAPH if graph else 0) | (GF_FLAG_LOWRANK if lowrank else 0)
+        d.system_dtype = sd.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if sd is not None else None
         h = ctypes.c_void_p()
         st = self.lib.gf_create(ctypes.byref(h), ctypes.byref(d))
         if st != GF_OK:
@@ -217,11 +267,21 @@ class GreensFunction:
         self.tot_p = int(np.sum(msys.astype(np.int64) * self.nb))
         self.tot_sig = int(np.sum(self.n_iw * self.m.astype(np.int64) ** 2))
         self.tot_sinf = int(np.sum(self.m.astype(np.int64) ** 2))
+        nb64 = self.nb.astype(np.int64)
+        self._cnt = {
+            "H": [int(np.sum(nb64[self.k_system == s] ** 2)) for s in range(n_sys)],
+            "Hd": [int(np.sum(nb64[self.k_system == s])) for s in range(n_sys)],
+            "P": [int(self.m[s]) * int(np.sum(nb64[self.k_system == s])) for s in range(n_sys)],
+            "Sig": [self.n_iw * int(self.m[s]) ** 2 for s in range(n_sys)],
+            "Sinf": [int(self.m[s]) ** 2 for s in range(n_sys)]}
 
     @classmethod
     def for_systems(cls, systems, precision="fp64", input_dtype="c128", tail_order=2, device=0,
                     graph=False, lowrank=False):
-        """Context for a list of ``synth.System`` (one or several, ragged or not)."""
+        """Context for a list of ``synth.System`` (one or several, ragged or not);
+        input_dtype="per_system" takes each system's own ``dtype``."""
+        if input_dtype == "per_system":
+            input_dtype = [s.dtype for s in systems]
         nb = np.concatenate([s.nb for s in systems])
         ks = np.concatenate([np.full(s.nk, i, np.int32) for i, s in enumerate(systems)])
         n_iw = systems[0].n_iw
@@ -236,6 +296,12 @@ class GreensFunction:
 
     def _cdt(self):
         return "complex128" if self.input_dtype == "c128" else "complex64"
+
+    def _in(self, x, kind):
+        """Marshal an input array of the given kind (H, Hd, P, Sig, Sinf)."""
+        if self.sys_dtypes is not None:
+            return _SysArg(x, self._cnt[kind], self.sys_dtypes)
+        return _Arg(x, self._cdt())
 
     def close(self):
         if getattr(self, "h", None):
@@ -256,15 +322,15 @@ class GreensFunction:
 
     # ---------------------------------------------------------------- inputs
     def set_hamiltonian(self, H, diagonal=False):
-        a = _Arg(H, self._cdt())
+        a = self._in(H, "Hd" if diagonal else "H")
         self._check(self.lib.gf_set_hamiltonian(self.h, a.ptr, 1 if diagonal else 0))
 
     def set_projectors(self, P):
-        a = _Arg(P, self._cdt())
+        a = self._in(P, "P")
         self._check(self.lib.gf_set_projectors(self.h, a.ptr))
 
     def set_sigma(self, sigma, sigma_inf):
-        a, b = _Arg(sigma, self._cdt()), _Arg(sigma_inf, self._cdt())
+        a, b = self._in(sigma, "Sig"), self._in(sigma_inf, "Sinf")
         self._check(self.lib.gf_set_sigma(self.h, a.ptr, b.ptr))
 
     # --------------------------------------------------------------- compute
@@ -338,7 +404,7 @@ class GreensFunction:
     # ------------------------------------- projectors and the DMFT step
     def set_projectors_lowdin(self, W, out=None):
         """Make P_k = (W_k W_k^+)^{-1/2} W_k the projectors; returns P (complex128)."""
-        a = _Arg(W, self._cdt())
+        a = self._in(W, "P")
         out = self._out(self.tot_p, out)
         o = _Arg(out)
         self._check(self.lib.gf_set_projectors_lowdin(self.h, a.ptr, ctypes.c_void_p(o.ptr)))
@@ -369,7 +435,11 @@ class GreensFunction:
         npl = np.ascontiguousarray(np.atleast_1d(n_poles), dtype=np.int32)
         pa = _Arg(np.asarray(poles, dtype=np.float64).reshape(-1) if not _is_tensor(poles) else
                   poles.double().reshape(-1))
-        va, sa = _Arg(V, self._cdt()), _Arg(sigma_inf, self._cdt())
+        if self.sys_dtypes is not None:
+            cnt_v = [int(n) * int(m) for n, m in zip(npl, self.m)]
+            va, sa = _SysArg(V, cnt_v, self.sys_dtypes), self._in(sigma_inf, "Sinf")
+        else:
+            va, sa = _Arg(V, self._cdt()), _Arg(sigma_inf, self._cdt())
         self._check(self.lib.gf_set_sigma_poles(self.h, npl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                                 pa.ptr, va.ptr, sa.ptr))
 

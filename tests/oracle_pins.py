@@ -40,6 +40,19 @@ def sigma0_remainder(xi, beta, n_iw):
     return out
 
 
+def sigma0_remainder_tail1(xi, beta, n_iw):
+    """(2 xi/beta) sum_{n >= N} 1/(w_n^2 + xi^2) = (1/pi) Im psi(N + 1/2 + i beta xi/(2 pi)).
+
+    With only the 1/(i w) moment subtracted, one level at xi = eps - mu and Sigma = 0 gives
+    (1/beta) sum_{n<N} [(G - 1/(i w_n)) + c.c.] + 1/2 = 1/2 - (2 xi/beta) sum_{n<N} 1/(w_n^2 + xi^2),
+    because Re[1/(i w - xi) - 1/(i w)] = -xi/(w^2 + xi^2); the complete sum is
+    n_F(xi) = 1/2 - (2 xi/beta) sum_{n>=0} 1/(w_n^2 + xi^2) (the partial-fraction series of
+    tanh(beta xi/2)), so the truncated value is n_F(xi) plus this remainder.
+    """
+    xi = np.asarray(xi, dtype=float)
+    return np.imag(digamma(n_iw + 0.5 + 1j * beta * xi / (2 * np.pi))) / np.pi
+
+
 def small_system(seed=7, nk=5, nb=7, m=3, n_iw=64, beta=12.0, dense=True):
     return synth.random_system(seed, nk, nb, m, n_iw, beta, dense=dense)
 
@@ -84,6 +97,33 @@ def pin_sigma0_density(o):
     Pt = s.P @ U
     ncorr_ref = np.einsum("kab,kb,kab->", Pt, f, np.conj(Pt)).real / s.nk
     # each part divided by its own tolerance: rho, N, n_corr to 1e-12, dN/dmu to 1e-9 relative
+    err = max(np.max(np.abs(r["rho"] - rho_ref)) / 1e-12, abs(r["N"] - n_ref) / 1e-12,
+              abs(r["n_corr"] - ncorr_ref) / 1e-12, abs(r["dN_dmu"] - dn_ref) / abs(dn_ref) / 1e-9)
+    return err, 1.0
+
+
+def pin_sigma0_density_tail1(o):
+    """tail_order = 1, Sigma = 0: rho_k = U diag(n_F(xi) + R1_N(xi)) U^+ with the remainder of the
+    1/(i w)-only tail in closed form; N, n_corr and dN/dmu from the same closed form."""
+    s = small_system(seed=13, nb=6, m=2, n_iw=48, beta=7.0)
+    mu = 0.23
+    sig = np.zeros_like(s.sigma)
+    sinf = np.zeros_like(s.sigma_inf)
+    r = o.density(s.H, s.P, sig, sinf, s.beta, mu, tail_order=1)
+    eps, U = np.linalg.eigh(s.H)
+
+    def occ(mu_):
+        xi = eps - mu_
+        return fermi(xi, s.beta) + sigma0_remainder_tail1(xi.ravel(), s.beta, s.n_iw).reshape(xi.shape)
+
+    f = occ(mu)
+    rho_ref = np.einsum("kab,kb,kcb->kac", U, f, np.conj(U))
+    n_ref = np.sum(f) / s.nk
+    h = 1e-3
+    dn_ref = (8 * (np.sum(occ(mu + h)) - np.sum(occ(mu - h)))
+              - (np.sum(occ(mu + 2 * h)) - np.sum(occ(mu - 2 * h)))) / (12 * h) / s.nk
+    Pt = s.P @ U
+    ncorr_ref = np.einsum("kab,kb,kab->", Pt, f, np.conj(Pt)).real / s.nk
     err = max(np.max(np.abs(r["rho"] - rho_ref)) / 1e-12, abs(r["N"] - n_ref) / 1e-12,
               abs(r["n_corr"] - ncorr_ref) / 1e-12, abs(r["dN_dmu"] - dn_ref) / abs(dn_ref) / 1e-9)
     return err, 1.0
@@ -285,7 +325,7 @@ def pin_backward_fd(o):
     return worst, 1e-6
 
 
-ALL_PINS = [pin_sigma0_gloc, pin_sigma0_density, pin_pseudo_hamiltonian, pin_two_band_inverse,
+ALL_PINS = [pin_sigma0_gloc, pin_sigma0_density, pin_sigma0_density_tail1, pin_pseudo_hamiltonian, pin_two_band_inverse,
             pin_woodbury_eigenbasis,
             pin_high_frequency_moment, pin_symmetry_and_causality, pin_density_bounds,
             pin_dn_dmu_fd, pin_backward_fd]

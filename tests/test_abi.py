@@ -3,6 +3,7 @@ import ctypes
 import re
 from pathlib import Path
 
+import numpy as np
 import pytest
 
 from paper_1111_2157_gb300 import build as gfbuild
@@ -63,6 +64,24 @@ def test_create_rejects_invalid_descriptor(lib, field, value):
     assert st == gf.GF_EINVAL
     assert not h.value
     assert lib.gf_last_error(None).decode()
+
+
+def test_create_rejects_invalid_system_dtype(lib):
+    sd = (ctypes.c_int32 * 1)(7)
+    d, keep = _desc(system_dtype=sd)
+    h = ctypes.c_void_p()
+    assert lib.gf_create(ctypes.byref(h), ctypes.byref(d)) == gf.GF_EINVAL
+    assert not h.value
+    assert "system_dtype" in lib.gf_last_error(None).decode()
+
+
+def test_per_system_packing_of_inputs():
+    """The binding packs each system's block in its own dtype, blocks one after the other."""
+    a = np.arange(6) + 1j * np.arange(6)
+    x = gf._SysArg(a, [2, 4], ["c128", "c64"])
+    assert x.obj.nbytes == 2 * 16 + 4 * 8
+    assert np.array_equal(x.obj[:32].view(np.complex128), a[:2])
+    assert np.array_equal(x.obj[32:].view(np.complex64), a[2:].astype(np.complex64))
 
 
 def test_create_null_arguments(lib):

@@ -117,3 +117,55 @@ def test_self_energy_mixing_step_reduces_mismatch():
     gl2, _ = lattice_green(g, sigma2, mu, s.sigma_inf)
     loss1 = (gl2 - target).abs().pow(2).sum()
     assert loss1.item() < loss0.item()
+
+
+def test_full_size_gradient_against_the_oracle():
+    """The differentiation workload at full size (N_k = 2048, N_b = 64, m = 14, N_w = 1024,
+    beta = 100), in the launch configuration of the full problem: Sigma_bar and mu_bar of the
+    whole k-set equal the sum of the same VJP over eight k-blocks (each a context whose k-points
+    carry the full set's weight 1/2048), and one block's VJP equals the oracle's (1e-10).  The
+    mixed forward/backward pair matches the FP64 one to the contract's tolerance."""
+    import torch
+    s = synth.adjoint_case().systems[0]
+    assert (s.nk, s.nb[0], s.m, s.n_iw) == (2048, 64, 14, 1024)
+    rng = np.random.default_rng(31)
+    gbar = (rng.standard_normal(s.sigma.shape) + 1j * rng.standard_normal(s.sigma.shape)) * 1e-2
+    mu, nbar = 0.25, 0.6
+    g = make_gf([s])
+    sb_full, mb_full = g.backward([mu], gloc_bar=gbar.reshape(-1), n_bar=[nbar])
+    sb_full = sb_full.cpu().numpy().reshape(s.sigma.shape)
+    g.close()
+    nblk, kb = 8, s.nk // 8
+    w_full = np.full(kb, 1.0 / s.nk)
+    acc_sb, acc_mb = np.zeros_like(sb_full), 0.0
+    block0 = None
+    for b in range(nblk):
+        ks = slice(b * kb, (b + 1) * kb)
+        sub = synth.System(s.H[ks], s.P[ks], s.pole, s.sigma, s.beta, s.n_target, weights=w_full)
+        from paper_1111_2157_gb300.gf import GreensFunction
+        gb = GreensFunction(64, 14, s.n_iw, s.beta, n_k=kb, k_weight=w_full)
+        gb.set_hamiltonian(s.H[ks])
+        gb.set_projectors(s.P[ks])
+        gb.set_sigma(s.sigma, s.sigma_inf)
+        sb_b, mb_b = gb.backward([mu], gloc_bar=gbar.reshape(-1), n_bar=[nbar])
+        sb_b = sb_b.cpu().numpy().reshape(s.sigma.shape)
+        gb.close()
+        acc_sb += sb_b
+        acc_mb += mb_b[0]
+        if b == 0:
+            block0 = (sub, sb_b, mb_b[0])
+    assert rel(sb_full, acc_sb) < 1e-12
+    assert abs(mb_full[0] - acc_mb) <= 1e-12 * abs(mb_full[0])
+    sub, sb_0, mb_0 = block0
+    sb_o, mb_o = oracle.get().backward(sub.H, sub.P, sub.sigma, sub.sigma_inf, sub.beta, mu,
+                                       gloc_bar=gbar, n_bar=nbar, weights=w_full)
+    assert rel(sb_0, sb_o) < 1e-10
+    assert abs(mb_0 - mb_o) <= 1e-10 * abs(mb_o)
+    # sampled entries of the full gradient are finite and carry both terms of the VJP
+    for (w, a, b2) in [(0, 0, 0), (3, 5, 9), (511, 13, 2), (1023, 7, 7)]:
+        assert np.isfinite(sb_full[w, a, b2])
+    gm = make_gf([s], precision="mixed")
+    sb_m, mb_m = gm.backward([mu], gloc_bar=gbar.reshape(-1), n_bar=[nbar])
+    gm.close()
+    assert rel(sb_m.cpu().numpy().reshape(s.sigma.shape), sb_full) < 1e-6
+    assert abs(mb_m[0] - mb_full[0]) <= 1e-6 * abs(mb_full[0])

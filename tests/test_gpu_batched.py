@@ -91,3 +91,46 @@ def test_graph_replay_is_bitwise_identical(precision):
     g1.set_sigma(sig, pack([t.sigma_inf for t in s2]))
     a, b = g0.occupation([0.1, 0.1, 0.1])[0], g1.occupation([0.1, 0.1, 0.1])[0]
     assert np.all(np.abs(a - b) <= tol * np.abs(a))
+
+
+def _rounded(s):
+    """The system as its complex64 inputs carry it (what the library receives for a c64 system)."""
+    if s.dtype != "c64":
+        return s
+    r = lambda a: np.asarray(a).astype(np.complex64).astype(np.complex128)  # noqa: E731
+    H = [r(h) for h in s.H] if isinstance(s.H, list) else r(s.H)
+    P = [r(p) for p in s.P] if isinstance(s.P, list) else r(s.P)
+    pole = synth.PoleSigma(r(s.pole.sigma_inf), s.pole.p, s.pole.V)
+    return synth.System(H, P, pole, r(s.sigma), s.beta, s.n_target, dtype="c64")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_complex128_and_complex64_systems_in_one_context(precision):
+    """Half the batched systems are complex64: one context takes every system in its own dtype
+    (one launch per window bucket), matches the oracle on the complex64-rounded inputs, and, in
+    FP64, equals bit for bit a context given the same rounded values in complex128."""
+    from paper_1111_2157_gb300.gf import GreensFunction
+    systems = _batched_small()[:4]
+    assert {s.dtype for s in systems} == {"c128", "c64"}
+    g = GreensFunction.for_systems(systems, precision=precision, input_dtype="per_system")
+    g.set_hamiltonian(pack([pack(s.H) for s in systems]))
+    g.set_projectors(pack([pack(s.P) for s in systems]))
+    g.set_sigma(pack([s.sigma for s in systems]), pack([s.sigma_inf for s in systems]))
+    mus = [0.1, -0.2, 0.3, 0.0]
+    n, dn = g.occupation(mus)
+    gl = g.local(mus).cpu().numpy()
+    ref = [_rounded(s) for s in systems]
+    tol_n, tol_g = (1e-10, 1e-10) if precision == "fp64" else (1e-7, 1e-8)
+    off = 0
+    for i, s in enumerate(ref):
+        r = oracle.get().density(s.H, s.P, s.sigma, s.sigma_inf, s.beta, mus[i], want_rho=False)
+        assert abs(n[i] - r["N"]) < tol_n * r["N"]
+        size = s.n_iw * s.m * s.m
+        if i < 2:
+            glo = oracle.get().local(s.H, s.P, s.sigma, s.beta, mus[i])
+            assert rel(gl[off:off + size], glo.reshape(-1)) < tol_g
+        off += size
+    if precision == "fp64":
+        g2 = make_gf(ref)
+        n2, dn2 = g2.occupation(mus)
+        assert np.array_equal(n, n2) and np.array_equal(dn, dn2)

@@ -35,6 +35,12 @@ MUTATIONS = {
     "gloc_unweighted": ("for (size_t q = 0; q < mm; q++) acc[q] += wk[k] * Q[q];",
                         "for (size_t q = 0; q < mm; q++) acc[q] += Q[q];"),
     "occupation_unweighted": ("partN[3 * t + 0] += wk[k] * tr;", "partN[3 * t + 0] += tr;"),
+    # the tail_order = 1 branch: the second moment subtracted anyway, or its exact sum added back
+    # without it being subtracted
+    "tail1_keeps_second_moment": ("if (tail_order >= 2) tail += M2[i * n + j] / (iw * iw);",
+                                  "if (tail_order >= 1) tail += M2[i * n + j] / (iw * iw);"),
+    "tail1_adds_second_sum": ("if (tail_order >= 2) v -= 0.25 * beta * M2[i * n + j];",
+                              "if (tail_order >= 1) v -= 0.25 * beta * M2[i * n + j];"),
 }
 
 
