@@ -347,24 +347,27 @@ gf_status run_points(gf_ctx* c, int mode) {
     p.nbar = c->nbar.as<double>();
   }
   const bool kred = (mode & (gf::kGloc | gf::kAdj)) != 0;
-  const int nb_batches = kred ? (int)c->batch_k0.size() - 1 : 1;
+  const int nb_batches = kred ? (int)c->batch_g0.size() - 1 : 1;
+  p.kperm = kred ? c->kperm_d.as<int>() : nullptr;
+  // window of an item's (first) k-point: the k-points of a group share a bucket
+  auto item_nb = [&](const Item& it) { return c->nb[kred ? c->kperm[it.k] : it.k]; };
   int64_t points = 0;
   for (int b = 0; b < nb_batches; ++b) {
     const int i0 = kred ? c->batch_item0[b] : c->all_item0;
-    const int i1 = kred ? c->batch_item0[b + 1] : c->all_item0 + c->n_items_batched;
-    const int kb0 = kred ? c->batch_k0[b] : 0;
-    const int kb1 = kred ? c->batch_k0[b + 1] : c->n_k;
+    const int i1 = kred ? c->batch_item0[b + 1] : c->all_item0 + c->n_items_all;
+    const int gb0 = kred ? c->batch_g0[b] : 0;
+    const int gb1 = kred ? c->batch_g0[b + 1] : 0;
     if (kred) {
-      GF_CU(ensure(c->gq, sizeof(double2) * (size_t)(kb1 - kb0) * c->n_iw * c->mmax * c->mmax));
+      GF_CU(ensure(c->gq, sizeof(double2) * (size_t)(gb1 - gb0) * c->n_iw * c->mmax * c->mmax));
       p.gq = c->gq.as<double2>();
-      p.kb0 = kb0;
+      p.gb0 = gb0;
     }
     // items are sorted by decreasing window: one launch per window bucket, with
     // shared-memory tiles sized to the bucket's largest window
     for (int s0 = i0; s0 < i1;) {
-      const int bucket = gf_bucket(c->nb[c->items[s0].k]);
+      const int bucket = gf_bucket(item_nb(c->items[s0]));
       int s1 = s0;
-      while (s1 < i1 && gf_bucket(c->nb[c->items[s1].k]) == bucket) ++s1;
+      while (s1 < i1 && gf_bucket(item_nb(c->items[s1])) == bucket) ++s1;
       const Item* items_dev = c->items_d.as<Item>() + s0;
       LaunchCfg cfg;
       if (c->lowrank) {
@@ -408,16 +411,19 @@ gf_status run_points(gf_ctx* c, int mode) {
     if (kred) {
       int max_total = 0;
       for (const SInfo& si : c->sinfo) max_total = std::max(max_total, c->n_iw * si.m * si.m);
-      GF_CU(gf::launch_gq_reduce(c->kinfo_d.as<KInfo>(), c->sinfo_d.as<SInfo>(), c->n_sys, max_total,
-                                 c->gq.as<double2>(), kb0, kb1, c->n_iw, c->mmax, b == 0,
-                                 c->gacc.as<double2>(), c->stream));
+      GF_CU(gf::launch_gq_reduce(c->sinfo_d.as<SInfo>(), c->n_sys, max_total, c->sysg_d.as<int>(),
+                                 c->sysg_d.as<int>() + c->n_sys, c->gq.as<double2>(), gb0, gb1, c->n_iw,
+                                 c->mmax, b == 0, c->gacc.as<double2>(), c->stream));
       c->last_launches += 1;
     }
     for (int i = i0; i < i1; ++i) {
       const Item& it = c->items[i];
-      points += it.n1 - it.n0;
-      c->last_flops += (it.n1 - it.n0) * (c->lowrank ? point_flops_lr(c->nb[it.k], c->msys[c->ksys[it.k]], mode)
-                                                     : point_flops(c->nb[it.k], c->msys[c->ksys[it.k]], mode));
+      for (int q = 0; q < it.nk; ++q) {
+        const int k = kred ? c->kperm[it.k + q] : it.k + q;
+        points += it.n1 - it.n0;
+        c->last_flops += (it.n1 - it.n0) * (c->lowrank ? point_flops_lr(c->nb[k], c->msys[c->ksys[k]], mode)
+                                                       : point_flops(c->nb[k], c->msys[c->ksys[k]], mode));
+      }
     }
   }
   c->last_points += points;
@@ -675,8 +681,8 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
   DeviceGuard guard(c->device);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
   cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  // k-batches for the k-reductions: gq holds (k1-k0) * n_iw * mmax^2 complex
-  // numbers, within a quarter of the free device memory and at most 32 GiB
+  // the k-reductions keep one slot of n_iw * mmax^2 complex numbers per k-group in gq,
+  // batched within a quarter of the free device memory and at most 32 GiB
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
     cudaGetLastError();
@@ -685,8 +691,7 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
   size_t budget = std::min<size_t>((size_t)32 << 30, std::max<size_t>(free_b / 4, (size_t)1 << 28));
   if (const char* env = std::getenv("GF_GQ_BUDGET_MB")) budget = (size_t)std::atoll(env) << 20;
   c->gq_budget = budget;
-  const size_t per_k = sizeof(double2) * (size_t)c->n_iw * c->mmax * c->mmax;
-  const int kpb = (int)std::max<size_t>(1, std::min<size_t>(c->n_k, budget / per_k));
+  const size_t per_group = sizeof(double2) * (size_t)c->n_iw * c->mmax * c->mmax;
   // chunk width: about 40 items per resident CTA in each window bucket's launch
   // (resident CTAs: the larger of the two matrix placements of the point kernel)
   int bps = 1;
@@ -702,31 +707,65 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
   const double want = (double)c->n_k * c->n_iw / (40.0 * resident * std::max(1, n_buckets));
   c->chunk_w = (int)std::min<double>(c->n_iw, std::max(4.0, std::ceil(want)));
   c->n_chunks = (c->n_iw + c->chunk_w - 1) / c->chunk_w;
-  c->batch_k0.clear();
+  // Work items.  Modes without a k-reduction: one item per (k, chunk), all in one list
+  // sorted by decreasing window (one launch per window bucket).  Modes with a k-reduction:
+  // the k-points of each system and window bucket, in increasing k, form groups of kg;
+  // one item per (group, chunk) sums its k-points into one slot per (group, frequency),
+  // so the scratch holds n_iw mmax^2 numbers per group instead of per k-point.  kg keeps
+  // about 8 items per resident CTA.
+  // groups share a window bucket; order by the window of their first k-point
+  auto by_window = [&](const Item& a, const Item& b) { return c->nb[c->kperm[a.k]] > c->nb[c->kperm[b.k]]; };
+  c->kg = (int)std::max(1.0, std::min(16.0, std::floor((double)c->n_k * c->n_chunks / (8.0 * resident))));
+  c->kperm.clear();
+  c->group_k0.clear();
+  c->group_nk.clear();
+  c->sys_g0.assign(c->n_sys, 0);
+  c->sys_g1.assign(c->n_sys, 0);
+  for (int s = 0; s < c->n_sys; ++s) {
+    c->sys_g0[s] = (int)c->group_k0.size();
+    for (int b = kNumBuckets - 1; b >= 0; --b) {
+      int in_group = 0;
+      for (int k = c->sinfo[s].k0; k < c->sinfo[s].k1; ++k) {
+        if (gf_bucket(c->nb[k]) != b) continue;
+        if (in_group == 0) {
+          c->group_k0.push_back((int)c->kperm.size());
+          c->group_nk.push_back(0);
+        }
+        c->kperm.push_back(k);
+        ++c->group_nk.back();
+        if (++in_group == c->kg) in_group = 0;
+      }
+    }
+    c->sys_g1[s] = (int)c->group_k0.size();
+  }
+  c->n_groups = (int)c->group_k0.size();
+  const int gpb = (int)std::max<size_t>(1, std::min<size_t>(c->n_groups, budget / per_group));
+  c->items.clear();
+  c->batch_g0.clear();
   c->batch_item0.clear();
-  auto by_window = [&](const Item& a, const Item& b) { return c->nb[a.k] > c->nb[b.k]; };
-  for (int kb = 0; kb < c->n_k; kb += kpb) {
-    const int ke = std::min(c->n_k, kb + kpb);
-    c->batch_k0.push_back(kb);
+  for (int gb = 0; gb < c->n_groups; gb += gpb) {
+    const int ge = std::min(c->n_groups, gb + gpb);
+    c->batch_g0.push_back(gb);
     c->batch_item0.push_back((int)c->items.size());
     std::vector<Item> its;
-    for (int k = kb; k < ke; ++k)
+    for (int g = gb; g < ge; ++g)
       for (int ch = 0; ch < c->n_chunks; ++ch)
-        its.push_back(Item{k, ch * c->chunk_w, std::min(c->n_iw, (ch + 1) * c->chunk_w), ch});
-    // most expensive first (N_b^3), stable in (k, chunk)
+        its.push_back(Item{c->group_k0[g], ch * c->chunk_w, std::min(c->n_iw, (ch + 1) * c->chunk_w), ch,
+                           c->group_nk[g], g});
+    // most expensive first (N_b^3), stable in (group, chunk)
     std::stable_sort(its.begin(), its.end(), by_window);
     c->items.insert(c->items.end(), its.begin(), its.end());
   }
-  c->batch_k0.push_back(c->n_k);
+  c->batch_g0.push_back(c->n_groups);
   c->batch_item0.push_back((int)c->items.size());
-  // modes without a k-reduction take every item in one list ordered by window
-  // (one launch per bucket); with one k-batch that is the list above
-  c->n_items_batched = (int)c->items.size();
-  c->all_item0 = 0;
-  if (c->batch_k0.size() > 2) {
-    std::vector<Item> all(c->items.begin(), c->items.end());
-    std::stable_sort(all.begin(), all.end(), by_window);
+  {
+    std::vector<Item> all;
+    for (int k = 0; k < c->n_k; ++k)
+      for (int ch = 0; ch < c->n_chunks; ++ch)
+        all.push_back(Item{k, ch * c->chunk_w, std::min(c->n_iw, (ch + 1) * c->chunk_w), ch, 1, k});
+    std::stable_sort(all.begin(), all.end(), [&](const Item& a, const Item& b) { return c->nb[a.k] > c->nb[b.k]; });
     c->all_item0 = (int)c->items.size();
+    c->n_items_all = (int)all.size();
     c->items.insert(c->items.end(), all.begin(), all.end());
   }
 
@@ -755,6 +794,8 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
     if ((e = ensure(c->kinfo_d, sizeof(KInfo) * c->n_k))) return e;
     if ((e = ensure(c->sinfo_d, sizeof(SInfo) * c->n_sys))) return e;
     if ((e = ensure(c->items_d, sizeof(Item) * c->items.size()))) return e;
+    if ((e = ensure(c->kperm_d, sizeof(int) * c->kperm.size()))) return e;
+    if ((e = ensure(c->sysg_d, sizeof(int) * 2 * c->n_sys))) return e;
     if ((e = ensure(c->offD_d, sizeof(int64_t) * c->n_k))) return e;
     if ((e = ensure(c->mu, sizeof(double) * c->n_sys))) return e;
     if ((e = ensure(c->nbar, sizeof(double) * c->n_sys))) return e;
@@ -771,6 +812,14 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
                              cudaMemcpyHostToDevice, c->stream)))
       return e;
     if ((e = cudaMemcpyAsync(c->items_d.p, c->items.data(), sizeof(Item) * c->items.size(),
+                             cudaMemcpyHostToDevice, c->stream)))
+      return e;
+    if ((e = cudaMemcpyAsync(c->kperm_d.p, c->kperm.data(), sizeof(int) * c->kperm.size(),
+                             cudaMemcpyHostToDevice, c->stream)))
+      return e;
+    std::vector<int> sysg(c->sys_g0);
+    sysg.insert(sysg.end(), c->sys_g1.begin(), c->sys_g1.end());
+    if ((e = cudaMemcpyAsync(c->sysg_d.p, sysg.data(), sizeof(int) * 2 * c->n_sys,
                              cudaMemcpyHostToDevice, c->stream)))
       return e;
     if ((e = cudaMemcpyAsync(c->offD_d.p, c->offD.data(), sizeof(int64_t) * c->n_k,

@@ -49,6 +49,16 @@ __device__ __forceinline__ double2 crcp(double2 a) {
   }
 }
 
+// Pivot key of a complex FP64 number: max(|Re|, |Im|) compared through the IEEE
+// bit pattern, which orders non-negative doubles like their values; no FP64
+// instruction.
+__device__ __forceinline__ unsigned long long pivot_key(double2 a) {
+  const unsigned long long mask = 0x7fffffffffffffffULL;
+  const unsigned long long r = (unsigned long long)__double_as_longlong(a.x) & mask;
+  const unsigned long long i = (unsigned long long)__double_as_longlong(a.y) & mask;
+  return r > i ? r : i;
+}
+
 // ------------------------------------------------------------------ FP32 pairs
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -158,7 +168,7 @@ __device__ __forceinline__ void csub_prod(cf& v, const cf& l, const cf& u) {
   renorm_fast(v.ih, v.il);
 }
 // 1/a in pairs: an FP32 reciprocal refined by one Newton step r0 + r0 (1 - a r0).
-__device__ __forceinline__ cf crcp_df(const cf& a) {
+__device__ inline cf crcp_df(const cf& a) {
   const float s = fmaxf(fabsf(a.rh), fabsf(a.ih));
   const float is = __frcp_rn(s);
   const float ar = a.rh * is, ai = a.ih * is;

@@ -117,10 +117,16 @@ struct gf_ctx {
   int sm_count = 0, smem_optin = 0;
   int chunk_w = 1, n_chunks = 1;
   size_t gq_budget = 0;
-  std::vector<Item> items;              // sorted by (k batch, -nb, k, chunk)
-  std::vector<int> batch_k0, batch_item0;  // batch b: k in [batch_k0[b], batch_k0[b+1])
-  int n_items_batched = 0;  // items of the k-batched list; the window-ordered list follows
-  int all_item0 = 0;        // first item of the list used by modes without a k-reduction
+  // work items: the k-group list of the k-reductions, batch after batch (groups
+  // [batch_g0[b], batch_g0[b+1]) from item batch_item0[b]), sorted by decreasing window in
+  // each batch; then the single-k list of the other modes from all_item0
+  std::vector<Item> items;
+  std::vector<int> batch_g0, batch_item0;
+  int n_items_all = 0, all_item0 = 0;
+  int kg = 1, n_groups = 0;                // k-points per group, number of groups
+  std::vector<int> kperm, group_k0, group_nk;  // group g: kperm[group_k0[g] .. + group_nk[g])
+  std::vector<int> sys_g0, sys_g1;         // groups of system s: [sys_g0[s], sys_g1[s])
+  DevBuf kperm_d, sysg_d;  // kperm, then sys_g0 | sys_g1
   DevBuf H, P, Sig, Sinf, Einf, trHE, kinfo_d, sinfo_d, items_d, offD_d, mu, nbar, gbar, status,
       queue, stage, occ_part, rho_part, rho_out, gq, kN, kdN, kNc, sysout, a_scratch, mubar_part,
       mubar_sys, gacc, sysout2;

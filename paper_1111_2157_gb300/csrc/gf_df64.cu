@@ -21,110 +21,26 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "gf_complex.cuh"
 #include "gf_internal.cuh"
 
 namespace gf {
 
 namespace {
 
+using namespace cx;
+
 // ---------------------------------------------------------------- FP32 pairs
 // The _rn intrinsics keep nvcc from contracting a product into a later add or
 // reassociating the sums, which would break the error-free transformations.
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
 
-// (sh, sl) += (ah + al)(bh + bl): exact head product, first-order cross terms,
-// head sum by two_sum; (sh, sl) is left unnormalised.
-__device__ __forceinline__ void acc_prod(float ah, float al, float bh, float bl, float& sh, float& sl) {
-  const float p = __fmul_rn(ah, bh);
-  float e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-  float s, t;
-  two_sum(sh, p, s, t);
-  sh = s;
-  sl = __fadd_rn(sl, __fadd_rn(t, e));
-}
 
-__device__ __forceinline__ void renorm(float& h, float& l) {
-  float s, e;
-  two_sum(h, l, s, e);
-  h = s;
-  l = e;
-}
 
-struct cf {
-  float rh, rl, ih, il;
-};
 
-__device__ __forceinline__ cf ld4(const float4& v) { return cf{v.x, v.y, v.z, v.w}; }
-__device__ __forceinline__ float4 st4(const cf& c) { return make_float4(c.rh, c.rl, c.ih, c.il); }
-__device__ __forceinline__ cf cneg(const cf& c) { return cf{-c.rh, -c.rl, -c.ih, -c.il}; }
-__device__ __forceinline__ cf czero() { return cf{0.f, 0.f, 0.f, 0.f}; }
-__device__ __forceinline__ void cnorm(cf& c) {
-  renorm(c.rh, c.rl);
-  renorm(c.ih, c.il);
-}
-__device__ __forceinline__ double2 to_d2(const cf& c) {
-  return make_double2((double)c.rh + (double)c.rl, (double)c.ih + (double)c.il);
-}
-// acc += a b
-__device__ __forceinline__ void cacc(cf& acc, const cf& a, const cf& b) {
-  acc_prod(a.rh, a.rl, b.rh, b.rl, acc.rh, acc.rl);
-  acc_prod(-a.ih, -a.il, b.ih, b.il, acc.rh, acc.rl);
-  acc_prod(a.rh, a.rl, b.ih, b.il, acc.ih, acc.il);
-  acc_prod(a.ih, a.il, b.rh, b.rl, acc.ih, acc.il);
-}
-// acc += conj(a) b
-__device__ __forceinline__ void cacc_ca(cf& acc, const cf& a, const cf& b) {
-  acc_prod(a.rh, a.rl, b.rh, b.rl, acc.rh, acc.rl);
-  acc_prod(a.ih, a.il, b.ih, b.il, acc.rh, acc.rl);
-  acc_prod(a.rh, a.rl, b.ih, b.il, acc.ih, acc.il);
-  acc_prod(-a.ih, -a.il, b.rh, b.rl, acc.ih, acc.il);
-}
-// acc += a conj(b)
-__device__ __forceinline__ void cacc_cb(cf& acc, const cf& a, const cf& b) {
-  acc_prod(a.rh, a.rl, b.rh, b.rl, acc.rh, acc.rl);
-  acc_prod(a.ih, a.il, b.ih, b.il, acc.rh, acc.rl);
-  acc_prod(a.ih, a.il, b.rh, b.rl, acc.ih, acc.il);
-  acc_prod(-a.rh, -a.rl, b.ih, b.il, acc.ih, acc.il);
-}
 
-// FP32 pair of a double: hi = RN(x), lo = RN(x - hi).
-__device__ __forceinline__ void split(double x, float& h, float& l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
-}
 
-// 1/a: FP32 estimate r0 (scaled by the larger component), then one Newton step
-// r = r0 + r0 (1 - a r0) with the residual 1 - a r0 in pair arithmetic.
-__device__ cf crcp_df(const cf& a) {
-  const float s = fmaxf(fabsf(a.rh), fabsf(a.ih));
-  const float is = __frcp_rn(s);
-  const float ar = a.rh * is, ai = a.ih * is;
-  const float id = __frcp_rn(ar * ar + ai * ai);
-  const float r0r = ar * id * is, r0i = -ai * id * is;
-  cf e = cf{1.0f, 0.0f, 0.0f, 0.0f};
-  const cf r0 = cf{r0r, 0.0f, r0i, 0.0f};
-  cacc(e, cneg(a), r0);
-  cnorm(e);
-  const float cr = __fsub_rn(__fmul_rn(r0r, e.rh), __fmul_rn(r0i, e.ih));
-  const float ci = __fadd_rn(__fmul_rn(r0r, e.ih), __fmul_rn(r0i, e.rh));
-  cf r;
-  two_sum(r0r, cr, r.rh, r.rl);
-  two_sum(r0i, ci, r.ih, r.il);
-  return r;
-}
 
-__device__ __forceinline__ unsigned pivot_key_f(const float4& a) {
-  const unsigned r = __float_as_uint(a.x) & 0x7fffffffu;
-  const unsigned i = __float_as_uint(a.z) & 0x7fffffffu;
-  return r > i ? r : i;
-}
 
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
   for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -164,15 +80,6 @@ __device__ __forceinline__ void pivot_warp(const float4* A, int N, int ld, int j
   }
 }
 
-// a' = a - l u for one entry of the elimination of column j (row j takes urow,
-// column j takes -l r since urow[j] = r).
-// (h, l) <- h + l assuming |h| >= |l| (Dekker); after an update the low word
-// holds only rounding errors of the high word.
-__device__ __forceinline__ void renorm_fast(float& h, float& l) {
-  const float s = __fadd_rn(h, l);
-  l = __fsub_rn(l, __fsub_rn(s, h));
-  h = s;
-}
 
 __device__ __forceinline__ void elim_entry(float4* A, int ld, const float4* col, const float4* urow,
                                            int i, int c, int j) {
@@ -277,192 +184,195 @@ __global__ void __launch_bounds__(kThreads) k_point_df64(const PointParams p) {
     const int itx = s_item;
     if (itx >= p.n_items) break;
     const Item it = p.items[itx];
-    const KInfo ki = p.kinfo[it.k];
-    const SInfo si = p.sinfo[ki.sys];
-    const int N = ki.nb, M = si.m, ld = N | 1;
-    float4* A = p.a_in_smem ? (sm + L.offA)
-                            : reinterpret_cast<float4*>(p.a_scratch + (int64_t)blockIdx.x * p.a_stride);
-    const float4* Hk = p.Hd + ki.offH;
-    const float4* Pg = p.Pd + ki.offP;
-    const double mu = p.mu[ki.sys];
-    const double beta = si.beta;
-    const double wk = ki.w;
-    double nbar = 0.0;
-    if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
-    float mu_h, mu_l;
-    split(mu, mu_h, mu_l);
-    for (int e = tid; e < M * N; e += kThreads) sP[e] = Pg[e];
+    for (int q = 0; q < it.nk; ++q) {
+      const int kk = item_k(it, p.kperm, q);
+      const KInfo ki = p.kinfo[kk];
+      const SInfo si = p.sinfo[ki.sys];
+      const int N = ki.nb, M = si.m, ld = N | 1;
+      float4* A = p.a_in_smem ? (sm + L.offA)
+                              : reinterpret_cast<float4*>(p.a_scratch + (int64_t)blockIdx.x * p.a_stride);
+      const float4* Hk = p.Hd + ki.offH;
+      const float4* Pg = p.Pd + ki.offP;
+      const double mu = p.mu[ki.sys];
+      const double beta = si.beta;
+      const double wk = ki.w;
+      double nbar = 0.0;
+      if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
+      float mu_h, mu_l;
+      split(mu, mu_h, mu_l);
+      for (int e = tid; e < M * N; e += kThreads) sP[e] = Pg[e];
 
-    double acc_tr = 0.0, acc_mu = 0.0;
-    float g2h = 0.f, g2l = 0.f;
-    for (int n = it.n0; n < it.n1; ++n) {
-      const double wn = (2.0 * n + 1.0) * M_PI / beta;
-      float wn_h, wn_l;
-      split(wn, wn_h, wn_l);
-      const float4* Sg = p.Sd + si.offSig + (int64_t)n * M * M;
-      __syncthreads();
-      for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
-      __syncthreads();
-      // T = Sigma(i w_n) P_k
-      for (int e = tid; e < M * N; e += kThreads) {
-        const int a = e / N, j = e - a * N;
-        cf acc = czero();
-        for (int b = 0; b < M; ++b) cacc(acc, ld4(sS[a * M + b]), ld4(sP[b * N + j]));
-        cnorm(acc);
-        sT[e] = st4(acc);
-      }
-      __syncthreads();
-      // A = (i w_n + mu) I - H_k - P_k^+ T
-      for (int e = tid; e < N * N; e += kThreads) {
-        const int i = e / N, j = e - i * N;
-        cf acc = cneg(ld4(Hk[e]));
-        if (i == j) {
-          float s, t;
-          two_sum(acc.rh, mu_h, s, t);
-          acc.rh = s;
-          acc.rl = __fadd_rn(acc.rl, __fadd_rn(t, mu_l));
-          two_sum(acc.ih, wn_h, s, t);
-          acc.ih = s;
-          acc.il = __fadd_rn(acc.il, __fadd_rn(t, wn_l));
-        }
-        for (int a = 0; a < M; ++a) cacc_ca(acc, cneg(ld4(sP[a * N + i])), ld4(sT[a * N + j]));
-        cnorm(acc);
-        A[i * ld + j] = st4(acc);
-      }
-      __syncthreads();
-      gauss_jordan_df64(A, N, ld, sCol, sU, sPiv, sIdx, p.status);
-
-      if (p.mode & kOcc) {
-        for (int i = tid; i < N; i += kThreads) {
-          const float4 g = A[i * ld + sIdx[i]];
-          acc_tr += (double)g.x + (double)g.y;
-        }
-        for (int e = tid; e < N * N; e += kThreads) {
-          const int i = e / N, c = e - i * N;
-          const float4 g1 = A[i * ld + sIdx[c]], g2 = A[c * ld + sIdx[i]];
-          acc_prod(g1.x, g1.y, g2.x, g2.y, g2h, g2l);
-          acc_prod(-g1.z, -g1.w, g2.z, g2.w, g2h, g2l);
-        }
-        renorm(g2h, g2l);
-      }
-      if (p.mode & kRho) {
-        double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
-        const bool first = (n == it.n0);
-        for (int e = tid; e < N * N; e += kThreads) {
-          const int i = e / N, c = e - i * N;
-          const double2 g = to_d2(ld4(A[i * ld + sIdx[c]]));
-          if (first) {
-            S[e] = g;
-          } else {
-            double2 s = S[e];
-            s.x += g.x;
-            s.y += g.y;
-            S[e] = s;
-          }
-        }
-      }
-      if (p.mode & (kGloc | kAdj)) {
-        for (int e = tid; e < N * M; e += kThreads) {
-          const int i = e / M, b = e - i * M;
+      double acc_tr = 0.0, acc_mu = 0.0;
+      float g2h = 0.f, g2l = 0.f;
+      for (int n = it.n0; n < it.n1; ++n) {
+        const double wn = (2.0 * n + 1.0) * M_PI / beta;
+        float wn_h, wn_l;
+        split(wn, wn_h, wn_l);
+        const float4* Sg = p.Sd + si.offSig + (int64_t)n * M * M;
+        __syncthreads();
+        for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
+        __syncthreads();
+        // T = Sigma(i w_n) P_k
+        for (int e = tid; e < M * N; e += kThreads) {
+          const int a = e / N, j = e - a * N;
           cf acc = czero();
-          for (int c = 0; c < N; ++c) {
-            cacc_cb(acc, ld4(A[i * ld + sIdx[c]]), ld4(sP[b * N + c]));
-            if ((c & 15) == 15) cnorm(acc);
-          }
+          for (int b = 0; b < M; ++b) cacc(acc, ld4(sS[a * M + b]), ld4(sP[b * N + j]));
           cnorm(acc);
           sT[e] = st4(acc);
         }
-        if (p.mode & kAdj) {
-          for (int e = tid; e < M * N; e += kThreads) {
-            const int a = e / N, c = e - a * N;
-            const int colx = sIdx[c];
-            cf acc = czero();
-            for (int i = 0; i < N; ++i) {
-              cacc(acc, ld4(sP[a * N + i]), ld4(A[i * ld + colx]));
-              if ((i & 15) == 15) cnorm(acc);
-            }
-            cnorm(acc);
-            sZ[e] = st4(acc);
-          }
-        }
         __syncthreads();
-      }
-      if (p.mode & kGloc) {
-        double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, b = e - a * M;
-          cf acc = czero();
-          for (int i = 0; i < N; ++i) {
-            cacc(acc, ld4(sP[a * N + i]), ld4(sT[i * M + b]));
-            if ((i & 15) == 15) cnorm(acc);
+        // A = (i w_n + mu) I - H_k - P_k^+ T
+        for (int e = tid; e < N * N; e += kThreads) {
+          const int i = e / N, j = e - i * N;
+          cf acc = cneg(ld4(Hk[e]));
+          if (i == j) {
+            float s, t;
+            two_sum(acc.rh, mu_h, s, t);
+            acc.rh = s;
+            acc.rl = __fadd_rn(acc.rl, __fadd_rn(t, mu_l));
+            two_sum(acc.ih, wn_h, s, t);
+            acc.ih = s;
+            acc.il = __fadd_rn(acc.il, __fadd_rn(t, wn_l));
           }
+          for (int a = 0; a < M; ++a) cacc_ca(acc, cneg(ld4(sP[a * N + i])), ld4(sT[a * N + j]));
           cnorm(acc);
-          const double2 q = to_d2(acc);
-          out[e] = make_double2(wk * q.x, wk * q.y);
-        }
-      }
-      if (p.mode & kAdj) {
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, b = e - a * M;
-          cf aa = czero(), bb = czero();
-          for (int i = 0; i < N; ++i) {
-            const cf y = ld4(sT[i * M + b]);
-            cacc(aa, ld4(sP[a * N + i]), y);
-            cacc(bb, ld4(sZ[a * N + i]), y);
-            if ((i & 15) == 15) { cnorm(aa); cnorm(bb); }
-          }
-          cnorm(aa);
-          cnorm(bb);
-          sQa[e] = st4(aa);
-          sQb[e] = st4(bb);
+          A[i * ld + j] = st4(acc);
         }
         __syncthreads();
-        const bool have_gbar = (p.Gbd != nullptr);
-        if (have_gbar) {
-          const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
-          for (int e = tid; e < M * M; e += kThreads) sS[e] = Gb[e];
-          __syncthreads();
-          for (int e = tid; e < M * M; e += kThreads) {
-            const int a = e / M, b = e - a * M;
+        gauss_jordan_df64(A, N, ld, sCol, sU, sPiv, sIdx, p.status);
+
+        if (p.mode & kOcc) {
+          for (int i = tid; i < N; i += kThreads) {
+            const float4 g = A[i * ld + sIdx[i]];
+            acc_tr += (double)g.x + (double)g.y;
+          }
+          for (int e = tid; e < N * N; e += kThreads) {
+            const int i = e / N, c = e - i * N;
+            const float4 g1 = A[i * ld + sIdx[c]], g2 = A[c * ld + sIdx[i]];
+            acc_prod(g1.x, g1.y, g2.x, g2.y, g2h, g2l);
+            acc_prod(-g1.z, -g1.w, g2.z, g2.w, g2h, g2l);
+          }
+          renorm(g2h, g2l);
+        }
+        if (p.mode & kRho) {
+          double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
+          const bool first = (n == it.n0);
+          for (int e = tid; e < N * N; e += kThreads) {
+            const int i = e / N, c = e - i * N;
+            const double2 g = to_d2(ld4(A[i * ld + sIdx[c]]));
+            if (first) {
+              S[e] = g;
+            } else {
+              double2 s = S[e];
+              s.x += g.x;
+              s.y += g.y;
+              S[e] = s;
+            }
+          }
+        }
+        if (p.mode & (kGloc | kAdj)) {
+          for (int e = tid; e < N * M; e += kThreads) {
+            const int i = e / M, b = e - i * M;
             cf acc = czero();
-            for (int c = 0; c < M; ++c) cacc_cb(acc, ld4(sS[a * M + c]), ld4(sQa[b * M + c]));
+            for (int c = 0; c < N; ++c) {
+              cacc_cb(acc, ld4(A[i * ld + sIdx[c]]), ld4(sP[b * N + c]));
+              if ((c & 15) == 15) cnorm(acc);
+            }
             cnorm(acc);
             sT[e] = st4(acc);
           }
+          if (p.mode & kAdj) {
+            for (int e = tid; e < M * N; e += kThreads) {
+              const int a = e / N, c = e - a * N;
+              const int colx = sIdx[c];
+              cf acc = czero();
+              for (int i = 0; i < N; ++i) {
+                cacc(acc, ld4(sP[a * N + i]), ld4(A[i * ld + colx]));
+                if ((i & 15) == 15) cnorm(acc);
+              }
+              cnorm(acc);
+              sZ[e] = st4(acc);
+            }
+          }
           __syncthreads();
+        }
+        if (p.mode & kGloc) {
+          double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
           for (int e = tid; e < M * M; e += kThreads) {
-            const double2 g = to_d2(ld4(sS[e])), b = to_d2(ld4(sQb[e]));
-            acc_mu -= wk * fma(g.x, b.x, g.y * b.y);
+            const int a = e / M, b = e - a * M;
+            cf acc = czero();
+            for (int i = 0; i < N; ++i) {
+              cacc(acc, ld4(sP[a * N + i]), ld4(sT[i * M + b]));
+              if ((i & 15) == 15) cnorm(acc);
+            }
+            cnorm(acc);
+            const double2 qv = to_d2(acc);
+            gq_put(&out[e], q, make_double2(wk * qv.x, wk * qv.y));
           }
         }
-        double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-        const double cb = nbar * 2.0 / beta;
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, b = e - a * M;
-          cf acc = czero();
-          if (have_gbar)
-            for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sT[c * M + b]));
-          cnorm(acc);
-          const double2 v = to_d2(acc);
-          const double2 bt = to_d2(ld4(sQb[b * M + a]));
-          out[e] = make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y));
+        if (p.mode & kAdj) {
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, b = e - a * M;
+            cf aa = czero(), bb = czero();
+            for (int i = 0; i < N; ++i) {
+              const cf y = ld4(sT[i * M + b]);
+              cacc(aa, ld4(sP[a * N + i]), y);
+              cacc(bb, ld4(sZ[a * N + i]), y);
+              if ((i & 15) == 15) { cnorm(aa); cnorm(bb); }
+            }
+            cnorm(aa);
+            cnorm(bb);
+            sQa[e] = st4(aa);
+            sQb[e] = st4(bb);
+          }
+          __syncthreads();
+          const bool have_gbar = (p.Gbd != nullptr);
+          if (have_gbar) {
+            const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
+            for (int e = tid; e < M * M; e += kThreads) sS[e] = Gb[e];
+            __syncthreads();
+            for (int e = tid; e < M * M; e += kThreads) {
+              const int a = e / M, b = e - a * M;
+              cf acc = czero();
+              for (int c = 0; c < M; ++c) cacc_cb(acc, ld4(sS[a * M + c]), ld4(sQa[b * M + c]));
+              cnorm(acc);
+              sT[e] = st4(acc);
+            }
+            __syncthreads();
+            for (int e = tid; e < M * M; e += kThreads) {
+              const double2 g = to_d2(ld4(sS[e])), b = to_d2(ld4(sQb[e]));
+              acc_mu -= wk * fma(g.x, b.x, g.y * b.y);
+            }
+          }
+          double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+          const double cb = nbar * 2.0 / beta;
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, b = e - a * M;
+            cf acc = czero();
+            if (have_gbar)
+              for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sT[c * M + b]));
+            cnorm(acc);
+            const double2 v = to_d2(acc);
+            const double2 bt = to_d2(ld4(sQb[b * M + a]));
+            gq_put(&out[e], q, make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y)));
+          }
         }
       }
-    }
-    if (p.mode & kOcc) {
-      const double tr = block_sum_d(acc_tr, s_red);
-      const double g2 = block_sum_d((double)g2h + (double)g2l, s_red);
-      if (tid == 0) {
-        double* o = p.occ_part + ((int64_t)it.k * p.n_chunks + it.chunk) * 2;
-        o[0] = tr;
-        o[1] = g2;
+      if (p.mode & kOcc) {
+        const double tr = block_sum_d(acc_tr, s_red);
+        const double g2 = block_sum_d((double)g2h + (double)g2l, s_red);
+        if (tid == 0) {
+          double* o = p.occ_part + ((int64_t)kk * p.n_chunks + it.chunk) * 2;
+          o[0] = tr;
+          o[1] = g2;
+        }
       }
+      if (p.mode & kAdj) {
+        const double mb = block_sum_d(acc_mu, s_red);
+        if (tid == 0) p.mubar_part[(int64_t)kk * p.n_chunks + it.chunk] = mb;
+      }
+      __syncthreads();
     }
-    if (p.mode & kAdj) {
-      const double mb = block_sum_d(acc_mu, s_red);
-      if (tid == 0) p.mubar_part[(int64_t)it.k * p.n_chunks + it.chunk] = mb;
-    }
-    __syncthreads();
   }
 }
 

@@ -14,106 +14,15 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "gf_complex.cuh"
 #include "gf_internal.cuh"
 
 namespace gf {
 
 namespace {
 
-// ---- FP32-pair arithmetic (see gf_df64.cu for the error analysis)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void acc_prod(float ah, float al, float bh, float bl, float& sh, float& sl) {
-  const float p = __fmul_rn(ah, bh);
-  float e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-  float s, t;
-  two_sum(sh, p, s, t);
-  sh = s;
-  sl = __fadd_rn(sl, __fadd_rn(t, e));
-}
-__device__ __forceinline__ void renorm(float& h, float& l) {
-  float s, e;
-  two_sum(h, l, s, e);
-  h = s;
-  l = e;
-}
-__device__ __forceinline__ void renorm_fast(float& h, float& l) {
-  const float s = __fadd_rn(h, l);
-  l = __fsub_rn(l, __fsub_rn(s, h));
-  h = s;
-}
-struct cf {
-  float rh, rl, ih, il;
-};
-__device__ __forceinline__ cf ld4(const float4& v) { return cf{v.x, v.y, v.z, v.w}; }
-__device__ __forceinline__ float4 st4(const cf& c) { return make_float4(c.rh, c.rl, c.ih, c.il); }
-__device__ __forceinline__ cf cneg(const cf& c) { return cf{-c.rh, -c.rl, -c.ih, -c.il}; }
-__device__ __forceinline__ cf czero() { return cf{0.f, 0.f, 0.f, 0.f}; }
-__device__ __forceinline__ void cnorm(cf& c) {
-  renorm(c.rh, c.rl);
-  renorm(c.ih, c.il);
-}
-__device__ __forceinline__ double2 to_d2(const cf& c) {
-  return make_double2((double)c.rh + (double)c.rl, (double)c.ih + (double)c.il);
-}
-__device__ __forceinline__ void cacc(cf& acc, const cf& a, const cf& b) {
-  acc_prod(a.rh, a.rl, b.rh, b.rl, acc.rh, acc.rl);
-  acc_prod(-a.ih, -a.il, b.ih, b.il, acc.rh, acc.rl);
-  acc_prod(a.rh, a.rl, b.ih, b.il, acc.ih, acc.il);
-  acc_prod(a.ih, a.il, b.rh, b.rl, acc.ih, acc.il);
-}
-__device__ __forceinline__ void cacc_ca(cf& acc, const cf& a, const cf& b) {
-  acc_prod(a.rh, a.rl, b.rh, b.rl, acc.rh, acc.rl);
-  acc_prod(a.ih, a.il, b.ih, b.il, acc.rh, acc.rl);
-  acc_prod(a.rh, a.rl, b.ih, b.il, acc.ih, acc.il);
-  acc_prod(-a.ih, -a.il, b.rh, b.rl, acc.ih, acc.il);
-}
-__device__ __forceinline__ void cacc_cb(cf& acc, const cf& a, const cf& b) {
-  acc_prod(a.rh, a.rl, b.rh, b.rl, acc.rh, acc.rl);
-  acc_prod(a.ih, a.il, b.ih, b.il, acc.rh, acc.rl);
-  acc_prod(a.ih, a.il, b.rh, b.rl, acc.ih, acc.il);
-  acc_prod(-a.rh, -a.rl, b.ih, b.il, acc.ih, acc.il);
-}
-// v -= l u
-__device__ __forceinline__ void csub_prod(cf& v, const cf& l, const cf& u) {
-  acc_prod(-l.rh, -l.rl, u.rh, u.rl, v.rh, v.rl);
-  acc_prod(l.ih, l.il, u.ih, u.il, v.rh, v.rl);
-  acc_prod(-l.rh, -l.rl, u.ih, u.il, v.ih, v.il);
-  acc_prod(-l.ih, -l.il, u.rh, u.rl, v.ih, v.il);
-  renorm_fast(v.rh, v.rl);
-  renorm_fast(v.ih, v.il);
-}
-__device__ __forceinline__ void split(double x, float& h, float& l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
-}
-__device__ cf crcp_df(const cf& a) {
-  const float s = fmaxf(fabsf(a.rh), fabsf(a.ih));
-  const float is = __frcp_rn(s);
-  const float ar = a.rh * is, ai = a.ih * is;
-  const float id = __frcp_rn(ar * ar + ai * ai);
-  const float r0r = ar * id * is, r0i = -ai * id * is;
-  cf e = cf{1.0f, 0.0f, 0.0f, 0.0f};
-  const cf r0 = cf{r0r, 0.0f, r0i, 0.0f};
-  cacc(e, cneg(a), r0);
-  cnorm(e);
-  const float cr = __fsub_rn(__fmul_rn(r0r, e.rh), __fmul_rn(r0i, e.ih));
-  const float ci = __fadd_rn(__fmul_rn(r0r, e.ih), __fmul_rn(r0i, e.rh));
-  cf r;
-  two_sum(r0r, cr, r.rh, r.rl);
-  two_sum(r0i, ci, r.ih, r.il);
-  return r;
-}
-__device__ __forceinline__ unsigned pivot_key_f(const float4& a) {
-  const unsigned r = __float_as_uint(a.x) & 0x7fffffffu;
-  const unsigned i = __float_as_uint(a.z) & 0x7fffffffu;
-  return r > i ? r : i;
-}
+using namespace cx;
+
 
 constexpr int kMaxWarps = 16;
 
@@ -186,414 +95,417 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_df64r(const PointParams p)
     const int itx = s_item;
     if (itx >= p.n_items) break;
     const Item it = p.items[itx];
-    const KInfo ki = p.kinfo[it.k];
-    const SInfo si = p.sinfo[ki.sys];
-    const int N = ki.nb, M = si.m, ld = N | 1;
-    // thread grid of this k-point's window
-    const int TR = (N + RA - 1) / RA, TC = (N + RB - 1) / RB;
-    const int ot = tid - 32;  // warp 0 owns no tile: it runs the pivot lookahead
-    const bool owner = ot >= 0 && ot < TR * TC;
-    const int tr = owner ? ot / TC : 0, tc = owner ? ot - (ot / TC) * TC : 0;
-    const float4* Hk = p.Hd + ki.offH;
-    const float4* Pg = p.Pd + ki.offP;
-    const double mu = p.mu[ki.sys];
-    const double beta = si.beta;
-    const double wk = ki.w;
-    double nbar = 0.0;
-    if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
-    float mu_h, mu_l;
-    split(mu, mu_h, mu_l);
-    for (int e = tid; e < M * N; e += nthr) sP[e] = Pg[e];
+    for (int q = 0; q < it.nk; ++q) {
+      const int kk = item_k(it, p.kperm, q);
+      const KInfo ki = p.kinfo[kk];
+      const SInfo si = p.sinfo[ki.sys];
+      const int N = ki.nb, M = si.m, ld = N | 1;
+      // thread grid of this k-point's window
+      const int TR = (N + RA - 1) / RA, TC = (N + RB - 1) / RB;
+      const int ot = tid - 32;  // warp 0 owns no tile: it runs the pivot lookahead
+      const bool owner = ot >= 0 && ot < TR * TC;
+      const int tr = owner ? ot / TC : 0, tc = owner ? ot - (ot / TC) * TC : 0;
+      const float4* Hk = p.Hd + ki.offH;
+      const float4* Pg = p.Pd + ki.offP;
+      const double mu = p.mu[ki.sys];
+      const double beta = si.beta;
+      const double wk = ki.w;
+      double nbar = 0.0;
+      if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
+      float mu_h, mu_l;
+      split(mu, mu_h, mu_l);
+      for (int e = tid; e < M * N; e += nthr) sP[e] = Pg[e];
 
-    double acc_tr = 0.0, acc_mu = 0.0;
-    float g2h = 0.f, g2l = 0.f;
-    for (int n = it.n0; n < it.n1; ++n) {
-      __syncthreads();
-      for (int e = tid; e < M * M; e += nthr) sS[e] = p.Sd[si.offSig + (int64_t)n * M * M + e];
-      __syncthreads();
-      // T = Sigma(i w_n) P_k
-      for (int e = tid; e < M * N; e += nthr) {
-        const int a = e / N, j = e - a * N;
-        cf acc = czero();
-        for (int b = 0; b < M; ++b) cacc(acc, ld4(sS[a * M + b]), ld4(sP[b * N + j]));
-        cnorm(acc);
-        sT[e] = st4(acc);
-      }
-      __syncthreads();
-      // A = (i w_n + mu) I - H_k - P_k^+ T, formed in the owners' registers
-      cf A[RA][RB];
-      {
-        float wn_h, wn_l;
-        split((2.0 * n + 1.0) * M_PI / beta, wn_h, wn_l);
-#pragma unroll
-        for (int a = 0; a < RA; ++a)
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            const int i = tr + TR * a, c = tc + TC * b;
-            A[a][b] = (owner && i < N && c < N) ? cneg(ld4(Hk[i * N + c])) : czero();
-            if (owner && i == c && i < N) {
-              float s, t;
-              two_sum(A[a][b].rh, mu_h, s, t);
-              A[a][b].rh = s;
-              A[a][b].rl = __fadd_rn(A[a][b].rl, __fadd_rn(t, mu_l));
-              two_sum(A[a][b].ih, wn_h, s, t);
-              A[a][b].ih = s;
-              A[a][b].il = __fadd_rn(A[a][b].il, __fadd_rn(t, wn_l));
-            }
-          }
-        if (owner) {
-          for (int x = 0; x < M; ++x) {
-            cf pv[RA];
-#pragma unroll
-            for (int a = 0; a < RA; ++a) {
-              const int i = tr + TR * a;
-              pv[a] = (i < N) ? cneg(ld4(sP[x * N + i])) : czero();
-            }
-#pragma unroll
-            for (int b = 0; b < RB; ++b) {
-              const int c = tc + TC * b;
-              const cf tv = (c < N) ? ld4(sT[x * N + c]) : czero();
-#pragma unroll
-              for (int a = 0; a < RA; ++a) cacc_ca(A[a][b], pv[a], tv);
-            }
-          }
-#pragma unroll
+      double acc_tr = 0.0, acc_mu = 0.0;
+      float g2h = 0.f, g2l = 0.f;
+      for (int n = it.n0; n < it.n1; ++n) {
+        __syncthreads();
+        for (int e = tid; e < M * M; e += nthr) sS[e] = p.Sd[si.offSig + (int64_t)n * M * M + e];
+        __syncthreads();
+        // T = Sigma(i w_n) P_k
+        for (int e = tid; e < M * N; e += nthr) {
+          const int a = e / N, j = e - a * N;
+          cf acc = czero();
+          for (int b = 0; b < M; ++b) cacc(acc, ld4(sS[a * M + b]), ld4(sP[b * N + j]));
+          cnorm(acc);
+          sT[e] = st4(acc);
+        }
+        __syncthreads();
+        // A = (i w_n + mu) I - H_k - P_k^+ T, formed in the owners' registers
+        cf A[RA][RB];
+        {
+          float wn_h, wn_l;
+          split((2.0 * n + 1.0) * M_PI / beta, wn_h, wn_l);
+  #pragma unroll
           for (int a = 0; a < RA; ++a)
-#pragma unroll
-            for (int b = 0; b < RB; ++b) cnorm(A[a][b]);
-        }
-      }
-      // Gauss-Jordan with partial pivoting on the register tiles, one pivot of
-      // lookahead.  Before step j the multipliers l = col (l[j] = 0,
-      // l[p] = A[j][j], l[i] = A[i][j]), the pivot row p and r = 1/pivot are known.
-      //  (R) owners of row p publish urow = r A[p][.] (urow[j] = r), owners of
-      //      row j publish the old row j (rowj), owners of column j+1 publish
-      //      their column j+1 (cnx);
-      //  (U) owners zero column j, replace row j by urow and row p by rowj, and
-      //      update every owned entry a -= l[i] urow[c]; meanwhile warp 0 applies
-      //      the same operations to cnx, searches the new column j+1 for the
-      //      next pivot, forms its reciprocal and the next multipliers.
-      // Two barriers per pivot; the search and the reciprocal overlap the update.
-      if (owner && tc == 0) {
-#pragma unroll
-        for (int a = 0; a < RA; ++a) {
-          const int i = tr + TR * a;
-          if (i < N) sm[L.offCx + p.nbmax + i] = st4(A[a][0]);
-        }
-      }
-      __syncthreads();
-      if (warp == 0) {
-        // pivot of column 0 from the published column (no transformation yet)
-        const float4* cx = sm + L.offCx + p.nbmax;
-        float4* col = sm + L.offCol;
-        unsigned best = 0u;
-        int bi = 0x7fffffff;
-        for (int i = lane; i < N; i += 32) {
-          const unsigned key = pivot_key_f(cx[i]);
-          if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
-        }
-        for (int off = 16; off; off >>= 1) {
-          const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        for (int i = lane; i < N; i += 32) col[i] = (i == 0) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                                            : ((i == bi) ? cx[0] : cx[i]);
-        if (lane == 0) {
-          if (best == 0u || best >= 0x7f800000u) atomicOr(p.status, kFlagSingular);
-          s_p[0] = bi;
-          s_pq[0] = bi / TR;
-          s_pm[0] = bi - (bi / TR) * TR;
-          s_r[0] = st4(crcp_df(ld4(cx[bi])));
-          sPiv[0] = bi;
-        }
-      }
-      __syncthreads();
-      int jqr = 0, jmr = 0, jqc = 0, jmc = 0;  // j / TR, j % TR, j / TC, j % TC
-      int nqc = (TC > 1) ? 0 : 1, nmc = (TC > 1) ? 1 : 0;  // (j+1) / TC, (j+1) % TC
-      for (int j = 0; j < N; ++j) {
-        const int bf = j & 1;
-        float4* col = sm + L.offCol + bf * p.nbmax;
-        float4* urow = sm + L.offU + bf * p.nbmax;
-        float4* rowj = sm + L.offRj + bf * p.nbmax;
-        float4* cx = sm + L.offCx + bf * p.nbmax;
-        const int pr = s_p[bf], prq = s_pq[bf], prm = s_pm[bf];
-        const cf r = ld4(s_r[bf]);
-        const int jn = j + 1;
-        if (owner) {
-          if (tr == prm) {
-#pragma unroll
+  #pragma unroll
+            for (int b = 0; b < RB; ++b) {
+              const int i = tr + TR * a, c = tc + TC * b;
+              A[a][b] = (owner && i < N && c < N) ? cneg(ld4(Hk[i * N + c])) : czero();
+              if (owner && i == c && i < N) {
+                float s, t;
+                two_sum(A[a][b].rh, mu_h, s, t);
+                A[a][b].rh = s;
+                A[a][b].rl = __fadd_rn(A[a][b].rl, __fadd_rn(t, mu_l));
+                two_sum(A[a][b].ih, wn_h, s, t);
+                A[a][b].ih = s;
+                A[a][b].il = __fadd_rn(A[a][b].il, __fadd_rn(t, wn_l));
+              }
+            }
+          if (owner) {
+            for (int x = 0; x < M; ++x) {
+              cf pv[RA];
+  #pragma unroll
+              for (int a = 0; a < RA; ++a) {
+                const int i = tr + TR * a;
+                pv[a] = (i < N) ? cneg(ld4(sP[x * N + i])) : czero();
+              }
+  #pragma unroll
+              for (int b = 0; b < RB; ++b) {
+                const int c = tc + TC * b;
+                const cf tv = (c < N) ? ld4(sT[x * N + c]) : czero();
+  #pragma unroll
+                for (int a = 0; a < RA; ++a) cacc_ca(A[a][b], pv[a], tv);
+              }
+            }
+  #pragma unroll
             for (int a = 0; a < RA; ++a)
-              if (a == prq)
-#pragma unroll
-                for (int b = 0; b < RB; ++b) {
-                  const int c = tc + TC * b;
-                  if (c < N) {
-                    cf u = r;
-                    if (c != j) {
-                      u = czero();
-                      cacc(u, A[a][b], r);
-                      cnorm(u);
-                    }
-                    urow[c] = st4(u);
-                  }
-                }
+  #pragma unroll
+              for (int b = 0; b < RB; ++b) cnorm(A[a][b]);
           }
-          if (tr == jmr) {
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-              if (a == jqr)
-#pragma unroll
-                for (int b = 0; b < RB; ++b) {
-                  const int c = tc + TC * b;
-                  if (c < N) rowj[c] = st4(A[a][b]);
-                }
-          }
-          if (jn < N && tc == nmc) {
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-#pragma unroll
-              for (int b = 0; b < RB; ++b)
-                if (b == nqc) {
-                  const int i = tr + TR * a;
-                  if (i < N) cx[i] = st4(A[a][b]);
-                }
+        }
+        // Gauss-Jordan with partial pivoting on the register tiles, one pivot of
+        // lookahead.  Before step j the multipliers l = col (l[j] = 0,
+        // l[p] = A[j][j], l[i] = A[i][j]), the pivot row p and r = 1/pivot are known.
+        //  (R) owners of row p publish urow = r A[p][.] (urow[j] = r), owners of
+        //      row j publish the old row j (rowj), owners of column j+1 publish
+        //      their column j+1 (cnx);
+        //  (U) owners zero column j, replace row j by urow and row p by rowj, and
+        //      update every owned entry a -= l[i] urow[c]; meanwhile warp 0 applies
+        //      the same operations to cnx, searches the new column j+1 for the
+        //      next pivot, forms its reciprocal and the next multipliers.
+        // Two barriers per pivot; the search and the reciprocal overlap the update.
+        if (owner && tc == 0) {
+  #pragma unroll
+          for (int a = 0; a < RA; ++a) {
+            const int i = tr + TR * a;
+            if (i < N) sm[L.offCx + p.nbmax + i] = st4(A[a][0]);
           }
         }
         __syncthreads();
-        if (owner) {
-          const bool own_j = (tr == jmr), own_p = (pr != j && tr == prm);
-          if (own_j || own_p) {
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-#pragma unroll
-              for (int b = 0; b < RB; ++b) {
-                const int c = tc + TC * b;
-                if (c < N) {
-                  if (own_p && a == prq && c != j) A[a][b] = ld4(rowj[c]);
-                }
-              }
-          }
-          if (tc == jmc) {
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-#pragma unroll
-              for (int b = 0; b < RB; ++b)
-                if (b == jqc) A[a][b] = czero();
-          }
-          if (own_j) {
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-              if (a == jqr)
-#pragma unroll
-                for (int b = 0; b < RB; ++b) {
-                  const int c = tc + TC * b;
-                  if (c < N) A[a][b] = ld4(urow[c]);
-                }
-          }
-          cf lv[RA];
-#pragma unroll
-          for (int a = 0; a < RA; ++a) {
-            const int i = tr + TR * a;
-            lv[a] = (i < N) ? ld4(col[i]) : czero();
-          }
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            const int c = tc + TC * b;
-            const cf u = (c < N) ? ld4(urow[c]) : czero();
-#pragma unroll
-            for (int a = 0; a < RA; ++a) csub_prod(A[a][b], lv[a], u);
-          }
-        } else if (warp == 0 && jn < N) {
-          // lookahead: column j+1 after step j, exactly as its owners compute it
-          float4* ncol = sm + L.offCol + (bf ^ 1) * p.nbmax;
-          const cf u = ld4(urow[jn]);
+        if (warp == 0) {
+          // pivot of column 0 from the published column (no transformation yet)
+          const float4* cx = sm + L.offCx + p.nbmax;
+          float4* col = sm + L.offCol;
           unsigned best = 0u;
           int bi = 0x7fffffff;
           for (int i = lane; i < N; i += 32) {
-            cf v;
-            if (i == j) v = ld4(urow[jn]);
-            else if (i == pr) v = ld4(rowj[jn]);
-            else v = ld4(cx[i]);
-            csub_prod(v, ld4(col[i]), u);
-            cx[i] = st4(v);
-            if (i >= jn) {
-              const unsigned key = pivot_key_f(cx[i]);
-              if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
-            }
+            const unsigned key = pivot_key_f(cx[i]);
+            if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
           }
           for (int off = 16; off; off >>= 1) {
             const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
           }
-          __syncwarp();
-          for (int i = lane; i < N; i += 32)
-            ncol[i] = (i == jn) ? make_float4(0.f, 0.f, 0.f, 0.f) : ((i == bi) ? cx[jn] : cx[i]);
+          for (int i = lane; i < N; i += 32) col[i] = (i == 0) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                              : ((i == bi) ? cx[0] : cx[i]);
           if (lane == 0) {
             if (best == 0u || best >= 0x7f800000u) atomicOr(p.status, kFlagSingular);
-            s_p[bf ^ 1] = bi;
-            s_pq[bf ^ 1] = bi / TR;
-            s_pm[bf ^ 1] = bi - (bi / TR) * TR;
-            s_r[bf ^ 1] = st4(crcp_df(ld4(cx[bi])));
-            sPiv[jn] = bi;
+            s_p[0] = bi;
+            s_pq[0] = bi / TR;
+            s_pm[0] = bi - (bi / TR) * TR;
+            s_r[0] = st4(crcp_df(ld4(cx[bi])));
+            sPiv[0] = bi;
           }
         }
         __syncthreads();
-        if (++jmr == TR) { jmr = 0; ++jqr; }
-        if (++jmc == TC) { jmc = 0; ++jqc; }
-        if (++nmc == TC) { nmc = 0; ++nqc; }
-      }
-      // inverse (columns permuted by idx) to shared memory for the epilogues
-      if (owner) {
-#pragma unroll
-        for (int a = 0; a < RA; ++a)
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            const int i = tr + TR * a, c = tc + TC * b;
-            if (i < N && c < N) sG[i * ld + c] = st4(A[a][b]);
-          }
-      }
-      if (tid == 0) {
-        for (int c = 0; c < N; ++c) sIdx[c] = c;
-        for (int j = N - 1; j >= 0; --j) {
-          const int pp = sPiv[j];
-          if (pp != j) { const int t = sIdx[j]; sIdx[j] = sIdx[pp]; sIdx[pp] = t; }
-        }
-      }
-      __syncthreads();
-
-      if (p.mode & kOcc) {
-        for (int i = tid; i < N; i += nthr) {
-          const float4 gv = sG[i * ld + sIdx[i]];
-          acc_tr += (double)gv.x + (double)gv.y;
-        }
-        for (int e = tid; e < N * N; e += nthr) {
-          const int i = e / N, c = e - i * N;
-          const float4 g1 = sG[i * ld + sIdx[c]], g2 = sG[c * ld + sIdx[i]];
-          acc_prod(g1.x, g1.y, g2.x, g2.y, g2h, g2l);
-          acc_prod(-g1.z, -g1.w, g2.z, g2.w, g2h, g2l);
-        }
-        renorm(g2h, g2l);
-      }
-      if (p.mode & kRho) {
-        double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
-        const bool first = (n == it.n0);
-        for (int e = tid; e < N * N; e += nthr) {
-          const int i = e / N, c = e - i * N;
-          const double2 gv = to_d2(ld4(sG[i * ld + sIdx[c]]));
-          if (first) {
-            S[e] = gv;
-          } else {
-            double2 s = S[e];
-            s.x += gv.x;
-            s.y += gv.y;
-            S[e] = s;
-          }
-        }
-      }
-      if (p.mode & (kGloc | kAdj)) {
-        for (int e = tid; e < N * M; e += nthr) {
-          const int i = e / M, b = e - i * M;
-          cf acc = czero();
-          for (int c = 0; c < N; ++c) {
-            cacc_cb(acc, ld4(sG[i * ld + sIdx[c]]), ld4(sP[b * N + c]));
-            if ((c & 15) == 15) cnorm(acc);
-          }
-          cnorm(acc);
-          sT[e] = st4(acc);
-        }
-        if (p.mode & kAdj) {
-          for (int e = tid; e < M * N; e += nthr) {
-            const int a = e / N, c = e - a * N;
-            const int colx = sIdx[c];
-            cf acc = czero();
-            for (int i = 0; i < N; ++i) {
-              cacc(acc, ld4(sP[a * N + i]), ld4(sG[i * ld + colx]));
-              if ((i & 15) == 15) cnorm(acc);
+        int jqr = 0, jmr = 0, jqc = 0, jmc = 0;  // j / TR, j % TR, j / TC, j % TC
+        int nqc = (TC > 1) ? 0 : 1, nmc = (TC > 1) ? 1 : 0;  // (j+1) / TC, (j+1) % TC
+        for (int j = 0; j < N; ++j) {
+          const int bf = j & 1;
+          float4* col = sm + L.offCol + bf * p.nbmax;
+          float4* urow = sm + L.offU + bf * p.nbmax;
+          float4* rowj = sm + L.offRj + bf * p.nbmax;
+          float4* cx = sm + L.offCx + bf * p.nbmax;
+          const int pr = s_p[bf], prq = s_pq[bf], prm = s_pm[bf];
+          const cf r = ld4(s_r[bf]);
+          const int jn = j + 1;
+          if (owner) {
+            if (tr == prm) {
+  #pragma unroll
+              for (int a = 0; a < RA; ++a)
+                if (a == prq)
+  #pragma unroll
+                  for (int b = 0; b < RB; ++b) {
+                    const int c = tc + TC * b;
+                    if (c < N) {
+                      cf u = r;
+                      if (c != j) {
+                        u = czero();
+                        cacc(u, A[a][b], r);
+                        cnorm(u);
+                      }
+                      urow[c] = st4(u);
+                    }
+                  }
             }
-            cnorm(acc);
-            sZ[e] = st4(acc);
-          }
-        }
-        __syncthreads();
-        if (p.mode & kGloc) {
-          double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            cf acc = czero();
-            for (int i = 0; i < N; ++i) {
-              cacc(acc, ld4(sP[a * N + i]), ld4(sT[i * M + b]));
-              if ((i & 15) == 15) cnorm(acc);
+            if (tr == jmr) {
+  #pragma unroll
+              for (int a = 0; a < RA; ++a)
+                if (a == jqr)
+  #pragma unroll
+                  for (int b = 0; b < RB; ++b) {
+                    const int c = tc + TC * b;
+                    if (c < N) rowj[c] = st4(A[a][b]);
+                  }
             }
-            cnorm(acc);
-            const double2 qv = to_d2(acc);
-            out[e] = make_double2(wk * qv.x, wk * qv.y);
-          }
-        }
-        if (p.mode & kAdj) {
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            cf aa = czero(), bb = czero();
-            for (int i = 0; i < N; ++i) {
-              const cf y = ld4(sT[i * M + b]);
-              cacc(aa, ld4(sP[a * N + i]), y);
-              cacc(bb, ld4(sZ[a * N + i]), y);
-              if ((i & 15) == 15) { cnorm(aa); cnorm(bb); }
+            if (jn < N && tc == nmc) {
+  #pragma unroll
+              for (int a = 0; a < RA; ++a)
+  #pragma unroll
+                for (int b = 0; b < RB; ++b)
+                  if (b == nqc) {
+                    const int i = tr + TR * a;
+                    if (i < N) cx[i] = st4(A[a][b]);
+                  }
             }
-            cnorm(aa);
-            cnorm(bb);
-            sQa[e] = st4(aa);
-            sQb[e] = st4(bb);
           }
           __syncthreads();
-          const bool have_gbar = (p.Gbd != nullptr);
-          if (have_gbar) {
-            const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
-            for (int e = tid; e < M * M; e += nthr) sS[e] = Gb[e];
-            __syncthreads();
+          if (owner) {
+            const bool own_j = (tr == jmr), own_p = (pr != j && tr == prm);
+            if (own_j || own_p) {
+  #pragma unroll
+              for (int a = 0; a < RA; ++a)
+  #pragma unroll
+                for (int b = 0; b < RB; ++b) {
+                  const int c = tc + TC * b;
+                  if (c < N) {
+                    if (own_p && a == prq && c != j) A[a][b] = ld4(rowj[c]);
+                  }
+                }
+            }
+            if (tc == jmc) {
+  #pragma unroll
+              for (int a = 0; a < RA; ++a)
+  #pragma unroll
+                for (int b = 0; b < RB; ++b)
+                  if (b == jqc) A[a][b] = czero();
+            }
+            if (own_j) {
+  #pragma unroll
+              for (int a = 0; a < RA; ++a)
+                if (a == jqr)
+  #pragma unroll
+                  for (int b = 0; b < RB; ++b) {
+                    const int c = tc + TC * b;
+                    if (c < N) A[a][b] = ld4(urow[c]);
+                  }
+            }
+            cf lv[RA];
+  #pragma unroll
+            for (int a = 0; a < RA; ++a) {
+              const int i = tr + TR * a;
+              lv[a] = (i < N) ? ld4(col[i]) : czero();
+            }
+  #pragma unroll
+            for (int b = 0; b < RB; ++b) {
+              const int c = tc + TC * b;
+              const cf u = (c < N) ? ld4(urow[c]) : czero();
+  #pragma unroll
+              for (int a = 0; a < RA; ++a) csub_prod(A[a][b], lv[a], u);
+            }
+          } else if (warp == 0 && jn < N) {
+            // lookahead: column j+1 after step j, exactly as its owners compute it
+            float4* ncol = sm + L.offCol + (bf ^ 1) * p.nbmax;
+            const cf u = ld4(urow[jn]);
+            unsigned best = 0u;
+            int bi = 0x7fffffff;
+            for (int i = lane; i < N; i += 32) {
+              cf v;
+              if (i == j) v = ld4(urow[jn]);
+              else if (i == pr) v = ld4(rowj[jn]);
+              else v = ld4(cx[i]);
+              csub_prod(v, ld4(col[i]), u);
+              cx[i] = st4(v);
+              if (i >= jn) {
+                const unsigned key = pivot_key_f(cx[i]);
+                if (bi == 0x7fffffff || key > best) { best = key; bi = i; }
+              }
+            }
+            for (int off = 16; off; off >>= 1) {
+              const unsigned ob = __shfl_xor_sync(0xffffffffu, best, off);
+              const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+              if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            __syncwarp();
+            for (int i = lane; i < N; i += 32)
+              ncol[i] = (i == jn) ? make_float4(0.f, 0.f, 0.f, 0.f) : ((i == bi) ? cx[jn] : cx[i]);
+            if (lane == 0) {
+              if (best == 0u || best >= 0x7f800000u) atomicOr(p.status, kFlagSingular);
+              s_p[bf ^ 1] = bi;
+              s_pq[bf ^ 1] = bi / TR;
+              s_pm[bf ^ 1] = bi - (bi / TR) * TR;
+              s_r[bf ^ 1] = st4(crcp_df(ld4(cx[bi])));
+              sPiv[jn] = bi;
+            }
+          }
+          __syncthreads();
+          if (++jmr == TR) { jmr = 0; ++jqr; }
+          if (++jmc == TC) { jmc = 0; ++jqc; }
+          if (++nmc == TC) { nmc = 0; ++nqc; }
+        }
+        // inverse (columns permuted by idx) to shared memory for the epilogues
+        if (owner) {
+  #pragma unroll
+          for (int a = 0; a < RA; ++a)
+  #pragma unroll
+            for (int b = 0; b < RB; ++b) {
+              const int i = tr + TR * a, c = tc + TC * b;
+              if (i < N && c < N) sG[i * ld + c] = st4(A[a][b]);
+            }
+        }
+        if (tid == 0) {
+          for (int c = 0; c < N; ++c) sIdx[c] = c;
+          for (int j = N - 1; j >= 0; --j) {
+            const int pp = sPiv[j];
+            if (pp != j) { const int t = sIdx[j]; sIdx[j] = sIdx[pp]; sIdx[pp] = t; }
+          }
+        }
+        __syncthreads();
+
+        if (p.mode & kOcc) {
+          for (int i = tid; i < N; i += nthr) {
+            const float4 gv = sG[i * ld + sIdx[i]];
+            acc_tr += (double)gv.x + (double)gv.y;
+          }
+          for (int e = tid; e < N * N; e += nthr) {
+            const int i = e / N, c = e - i * N;
+            const float4 g1 = sG[i * ld + sIdx[c]], g2 = sG[c * ld + sIdx[i]];
+            acc_prod(g1.x, g1.y, g2.x, g2.y, g2h, g2l);
+            acc_prod(-g1.z, -g1.w, g2.z, g2.w, g2h, g2l);
+          }
+          renorm(g2h, g2l);
+        }
+        if (p.mode & kRho) {
+          double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
+          const bool first = (n == it.n0);
+          for (int e = tid; e < N * N; e += nthr) {
+            const int i = e / N, c = e - i * N;
+            const double2 gv = to_d2(ld4(sG[i * ld + sIdx[c]]));
+            if (first) {
+              S[e] = gv;
+            } else {
+              double2 s = S[e];
+              s.x += gv.x;
+              s.y += gv.y;
+              S[e] = s;
+            }
+          }
+        }
+        if (p.mode & (kGloc | kAdj)) {
+          for (int e = tid; e < N * M; e += nthr) {
+            const int i = e / M, b = e - i * M;
+            cf acc = czero();
+            for (int c = 0; c < N; ++c) {
+              cacc_cb(acc, ld4(sG[i * ld + sIdx[c]]), ld4(sP[b * N + c]));
+              if ((c & 15) == 15) cnorm(acc);
+            }
+            cnorm(acc);
+            sT[e] = st4(acc);
+          }
+          if (p.mode & kAdj) {
+            for (int e = tid; e < M * N; e += nthr) {
+              const int a = e / N, c = e - a * N;
+              const int colx = sIdx[c];
+              cf acc = czero();
+              for (int i = 0; i < N; ++i) {
+                cacc(acc, ld4(sP[a * N + i]), ld4(sG[i * ld + colx]));
+                if ((i & 15) == 15) cnorm(acc);
+              }
+              cnorm(acc);
+              sZ[e] = st4(acc);
+            }
+          }
+          __syncthreads();
+          if (p.mode & kGloc) {
+            double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
             for (int e = tid; e < M * M; e += nthr) {
               const int a = e / M, b = e - a * M;
               cf acc = czero();
-              for (int c = 0; c < M; ++c) cacc_cb(acc, ld4(sS[a * M + c]), ld4(sQa[b * M + c]));
+              for (int i = 0; i < N; ++i) {
+                cacc(acc, ld4(sP[a * N + i]), ld4(sT[i * M + b]));
+                if ((i & 15) == 15) cnorm(acc);
+              }
               cnorm(acc);
-              sT[e] = st4(acc);
-            }
-            __syncthreads();
-            for (int e = tid; e < M * M; e += nthr) {
-              const double2 gv = to_d2(ld4(sS[e])), bv = to_d2(ld4(sQb[e]));
-              acc_mu -= wk * fma(gv.x, bv.x, gv.y * bv.y);
+              const double2 qv = to_d2(acc);
+              gq_put(&out[e], q, make_double2(wk * qv.x, wk * qv.y));
             }
           }
-          double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-          const double cb = nbar * 2.0 / beta;
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            cf acc = czero();
-            if (have_gbar)
-              for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sT[c * M + b]));
-            cnorm(acc);
-            const double2 v = to_d2(acc);
-            const double2 bt = to_d2(ld4(sQb[b * M + a]));
-            out[e] = make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y));
+          if (p.mode & kAdj) {
+            for (int e = tid; e < M * M; e += nthr) {
+              const int a = e / M, b = e - a * M;
+              cf aa = czero(), bb = czero();
+              for (int i = 0; i < N; ++i) {
+                const cf y = ld4(sT[i * M + b]);
+                cacc(aa, ld4(sP[a * N + i]), y);
+                cacc(bb, ld4(sZ[a * N + i]), y);
+                if ((i & 15) == 15) { cnorm(aa); cnorm(bb); }
+              }
+              cnorm(aa);
+              cnorm(bb);
+              sQa[e] = st4(aa);
+              sQb[e] = st4(bb);
+            }
+            __syncthreads();
+            const bool have_gbar = (p.Gbd != nullptr);
+            if (have_gbar) {
+              const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
+              for (int e = tid; e < M * M; e += nthr) sS[e] = Gb[e];
+              __syncthreads();
+              for (int e = tid; e < M * M; e += nthr) {
+                const int a = e / M, b = e - a * M;
+                cf acc = czero();
+                for (int c = 0; c < M; ++c) cacc_cb(acc, ld4(sS[a * M + c]), ld4(sQa[b * M + c]));
+                cnorm(acc);
+                sT[e] = st4(acc);
+              }
+              __syncthreads();
+              for (int e = tid; e < M * M; e += nthr) {
+                const double2 gv = to_d2(ld4(sS[e])), bv = to_d2(ld4(sQb[e]));
+                acc_mu -= wk * fma(gv.x, bv.x, gv.y * bv.y);
+              }
+            }
+            double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+            const double cb = nbar * 2.0 / beta;
+            for (int e = tid; e < M * M; e += nthr) {
+              const int a = e / M, b = e - a * M;
+              cf acc = czero();
+              if (have_gbar)
+                for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sT[c * M + b]));
+              cnorm(acc);
+              const double2 v = to_d2(acc);
+              const double2 bt = to_d2(ld4(sQb[b * M + a]));
+              gq_put(&out[e], q, make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y)));
+            }
           }
         }
       }
-    }
-    if (p.mode & kOcc) {
-      const double tr_ = block_sum_any(acc_tr, s_red);
-      const double g2 = block_sum_any((double)g2h + (double)g2l, s_red);
-      if (tid == 0) {
-        double* o = p.occ_part + ((int64_t)it.k * p.n_chunks + it.chunk) * 2;
-        o[0] = tr_;
-        o[1] = g2;
+      if (p.mode & kOcc) {
+        const double tr_ = block_sum_any(acc_tr, s_red);
+        const double g2 = block_sum_any((double)g2h + (double)g2l, s_red);
+        if (tid == 0) {
+          double* o = p.occ_part + ((int64_t)kk * p.n_chunks + it.chunk) * 2;
+          o[0] = tr_;
+          o[1] = g2;
+        }
       }
+      if (p.mode & kAdj) {
+        const double mb = block_sum_any(acc_mu, s_red);
+        if (tid == 0) p.mubar_part[(int64_t)kk * p.n_chunks + it.chunk] = mb;
+      }
+      __syncthreads();
     }
-    if (p.mode & kAdj) {
-      const double mb = block_sum_any(acc_mu, s_red);
-      if (tid == 0) p.mubar_part[(int64_t)it.k * p.n_chunks + it.chunk] = mb;
-    }
-    __syncthreads();
   }
 }
 

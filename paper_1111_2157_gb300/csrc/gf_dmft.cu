@@ -10,41 +10,15 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "gf_complex.cuh"
 #include "gf_internal.cuh"
 
 namespace gf {
 
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-}
-// acc += a * conj(b)
-__device__ __forceinline__ void cmac_cb(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
-}
-__device__ __forceinline__ double2 crcp(double2 a) {
-  if (fabs(a.x) >= fabs(a.y)) {
-    const double t = a.y / a.x;
-    const double id = 1.0 / fma(a.y, t, a.x);
-    return make_double2(id, -t * id);
-  } else {
-    const double t = a.x / a.y;
-    const double id = 1.0 / fma(a.x, t, a.y);
-    return make_double2(t * id, -id);
-  }
-}
-__device__ __forceinline__ unsigned long long pivot_key(double2 a) {
-  const unsigned long long mask = 0x7fffffffffffffffULL;
-  const unsigned long long r = (unsigned long long)__double_as_longlong(a.x) & mask;
-  const unsigned long long i = (unsigned long long)__double_as_longlong(a.y) & mask;
-  return r > i ? r : i;
-}
+using namespace cx;
+
 
 // part[k][a][b] = w_k (P_k H_k P_k^+)_{ab}, one CTA per k: T = H P^+ (N x m)
 // in shared memory, then P T.

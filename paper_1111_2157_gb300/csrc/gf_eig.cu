@@ -22,31 +22,17 @@
 
 #include <algorithm>
 
+#include "gf_complex.cuh"
 #include "gf_internal.cuh"
 
 namespace gf {
 
 namespace {
 
+using namespace cx;
+
 constexpr int kEigThreads = 256;
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-}
-// acc += conj(a) * b
-__device__ __forceinline__ void cmac_ca(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
-}
-// acc += a * conj(b)
-__device__ __forceinline__ void cmac_cb(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
-}
 
 __device__ __forceinline__ double eig_block_sum(double v, double* red) {
   // Deterministic: fixed xor tree inside each warp, then warp 0 over the warps.

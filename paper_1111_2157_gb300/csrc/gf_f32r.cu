@@ -297,393 +297,396 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_f32r(const PointParams p) 
     const int itx = s_item;
     if (itx >= p.n_items) break;
     const Item it = p.items[itx];
-    const KInfo ki = p.kinfo[it.k];
-    const SInfo si = p.sinfo[ki.sys];
-    const int N = ki.nb, M = si.m, ld = N | 1;
-    const int TR = (N + RA - 1) / RA, TC = (N + RB - 1) / RB;
-    const int ot = tid - 32;  // warp 0 owns no tile: it runs the pivot lookahead
-    const bool owner = ot >= 0 && ot < TR * TC;
-    const int tr = owner ? ot / TC : 0, tc = owner ? ot - (ot / TC) * TC : 0;
-    const float2* Hk = p.Hs + ki.offH;
-    const double2* Hk64 = p.H + ki.offH;
-    const float4* Hkp = p.Hd + ki.offH;
-    const float4* Pkp = p.Pd + ki.offP;
-    const double mu = p.mu[ki.sys];
-    const double beta = si.beta;
-    const double wk = ki.w;
-    double nbar = 0.0;
-    if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
-    for (int e = tid; e < M * N; e += nthr) sP[e] = p.Ps[ki.offP + e];
-    for (int i = tid; i < N; i += nthr) sHii[i] = Hk64[i * N + i];
-    for (int i = tid; i < 2 * nbp; i += nthr) bCol[i] = f2zero();  // zero tails of l
-    const double pib = M_PI / beta;
+    for (int q = 0; q < it.nk; ++q) {
+      const int kk = item_k(it, p.kperm, q);
+      const KInfo ki = p.kinfo[kk];
+      const SInfo si = p.sinfo[ki.sys];
+      const int N = ki.nb, M = si.m, ld = N | 1;
+      const int TR = (N + RA - 1) / RA, TC = (N + RB - 1) / RB;
+      const int ot = tid - 32;  // warp 0 owns no tile: it runs the pivot lookahead
+      const bool owner = ot >= 0 && ot < TR * TC;
+      const int tr = owner ? ot / TC : 0, tc = owner ? ot - (ot / TC) * TC : 0;
+      const float2* Hk = p.Hs + ki.offH;
+      const double2* Hk64 = p.H + ki.offH;
+      const float4* Hkp = p.Hd + ki.offH;
+      const float4* Pkp = p.Pd + ki.offP;
+      const double mu = p.mu[ki.sys];
+      const double beta = si.beta;
+      const double wk = ki.w;
+      double nbar = 0.0;
+      if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
+      for (int e = tid; e < M * N; e += nthr) sP[e] = p.Ps[ki.offP + e];
+      for (int i = tid; i < N; i += nthr) sHii[i] = Hk64[i * N + i];
+      for (int i = tid; i < 2 * nbp; i += nthr) bCol[i] = f2zero();  // zero tails of l
+      const double pib = M_PI / beta;
 
-    double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
-    for (int n = it.n0; n < it.n1; ++n) {
-      const double wn = (2.0 * n + 1.0) * pib;
-      __syncthreads();  // previous epilogue done with the shared buffers
-      for (int e = tid; e < M * M; e += nthr) sS[e] = p.Ss[si.offSig + (int64_t)n * M * M + e];
-      __syncthreads();
-      // T = Sigma(i w_n) P_k  (M x N), in the G region
-      for (int e = tid; e < M * N; e += nthr) {
-        const int a = e / N, j = e - a * N;
-        float2 acc = f2zero();
-        for (int b = 0; b < M; ++b) fmac(acc, sS[a * M + b], sP[b * N + j]);
-        sT[e] = acc;
-      }
-      for (int i = tid; i < N; i += nthr)
-        sD[i] = make_float2(__double2float_rn(mu - sHii[i].x), __double2float_rn(wn - sHii[i].y));
-      __syncthreads();
-      // A = (i w_n + mu) I - H_k - P_k^+ T in the owners' registers; the diagonal
-      // (i w_n + mu - H_ii) comes from sD, formed in FP64 and rounded once
-      float2 A[RA][RB];
-#pragma unroll
-      for (int a = 0; a < RA; ++a)
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-          const int i = tr + TR * a, c = tc + TC * b;
-          float2 v = f2zero();
-          if (owner && i < N && c < N) v = (i == c) ? sD[i] : fneg(Hk[i * N + c]);
-          A[a][b] = v;
-        }
-      if (owner) {
-        for (int x = 0; x < M; ++x) {
-          float2 pv[RA];
-#pragma unroll
-          for (int a = 0; a < RA; ++a) {
-            const int i = tr + TR * a;
-            pv[a] = (i < N) ? fneg(sP[x * N + i]) : f2zero();
-          }
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            const int c = tc + TC * b;
-            const float2 tv = (c < N) ? sT[x * N + c] : f2zero();
-#pragma unroll
-            for (int a = 0; a < RA; ++a) fmac_ca(A[a][b], pv[a], tv);
-          }
-        }
-      }
-      // Gauss-Jordan elimination with partial pivoting, without row interchanges
-      // (the exchange or sweep form of the elimination): step j pivots on
-      // (p_j, j), p_j the unused row of largest |A[i][j]|, so that afterwards
-      // X[i][c] = B[p_i][q_c] with q the inverse permutation of p.  Every step is
-      // one uniform rank-1 update of the whole tile,
-      //   A[i][c] -= l[i] u[c],  u = A[p][.] / A[p][j] with u[j] = 1/A[p][j],
-      //   l[i] = A[i][j] (i != p), l[p] = -1,
-      // after the owners of row p and of column j have zeroed them (so that row p
-      // becomes u and column j becomes -l u[j]).  Phases per step:
-      //  (R) owners of row p publish u and zero the row, owners of column j zero
-      //      it, owners of column j+1 publish it (cx);
-      //  (U) owners update their tiles; warp 0 applies the same update to cx,
-      //      picks p_{j+1} among the unused rows and forms the next l and
-      //      1/pivot (one pivot of lookahead).  Two barriers per step.
-      if (owner && tc == 0) {
-#pragma unroll
-        for (int a = 0; a < RA; ++a) bCx[nbp + tr + TR * a] = A[a][0];
-      }
-      __syncthreads();
-      unsigned used = 0u;  // warp 0: bit t marks row lane + 32 t as a pivot row already
-      if (warp == 0) {
-        const float2* cx0 = bCx + nbp;
-        float2 v[4];
-        unsigned best = 0u;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int i = lane + 32 * t;
-          v[t] = (i < N) ? cx0[i] : f2zero();
-          if (i < N) best = max(best, pack_key(v[t], i));
-        }
-        best = __reduce_max_sync(0xffffffffu, best);
-        // a zero or non-finite pivot is flagged; the row index stays in range
-        const int bi = min(127 - (int)(best & 127u), N - 1);
-        if (lane == 0 && ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u))
-          atomicOr(p.status, kFlagSingular);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int i = lane + 32 * t;
-          if (i < N) bCol[i] = (i == bi) ? make_float2(-1.f, 0.f) : v[t];
-          if (i == bi) {
-            used |= 1u << t;
-            s_r[0] = frcp(v[t]);
-            s_p[0] = bi;
-            s_pq[0] = bi / TR;
-            s_pm[0] = bi - (bi / TR) * TR;
-            sPiv[0] = bi;
-          }
-        }
-      }
-      __syncthreads();
-      int jqc = 0, jmc = 0;                                 // j / TC, j % TC
-      int nqc = (TC > 1) ? 0 : 1, nmc = (TC > 1) ? 1 : 0;  // (j+1) / TC, (j+1) % TC
-      for (int j = 0; j < N; ++j) {
-        const int bf = j & 1;
-        const float2* col = bCol + bf * nbp;
-        float2* urow = bU + bf * nbp;
-        float2* cxb = bCx + bf * nbp;
-        const int prq = s_pq[bf], prm = s_pm[bf];
-        const float2 r = s_r[bf];
-        const int jn = j + 1;
-        if (owner) {
-          if (tr == prm) {
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-              if (a == prq) {
-#pragma unroll
-                for (int b = 0; b < RB; ++b) {
-                  const int c = tc + TC * b;
-                  urow[c] = (c == j) ? r : fmul(A[a][b], r);
-                  A[a][b] = f2zero();
-                }
-              }
-          }
-          if (tc == jmc) {
-#pragma unroll
-            for (int b = 0; b < RB; ++b)
-              if (b == jqc) {
-#pragma unroll
-                for (int a = 0; a < RA; ++a) A[a][b] = f2zero();
-              }
-          }
-          if (jn < N && tc == nmc) {
-#pragma unroll
-            for (int b = 0; b < RB; ++b)
-              if (b == nqc) {
-#pragma unroll
-                for (int a = 0; a < RA; ++a) cxb[tr + TR * a] = A[a][b];
-              }
-          }
-        }
+      double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
+      for (int n = it.n0; n < it.n1; ++n) {
+        const double wn = (2.0 * n + 1.0) * pib;
+        __syncthreads();  // previous epilogue done with the shared buffers
+        for (int e = tid; e < M * M; e += nthr) sS[e] = p.Ss[si.offSig + (int64_t)n * M * M + e];
         __syncthreads();
-        if (owner) {
-          float2 lv[RA];
-#pragma unroll
-          for (int a = 0; a < RA; ++a) lv[a] = col[tr + TR * a];
-#pragma unroll
+        // T = Sigma(i w_n) P_k  (M x N), in the G region
+        for (int e = tid; e < M * N; e += nthr) {
+          const int a = e / N, j = e - a * N;
+          float2 acc = f2zero();
+          for (int b = 0; b < M; ++b) fmac(acc, sS[a * M + b], sP[b * N + j]);
+          sT[e] = acc;
+        }
+        for (int i = tid; i < N; i += nthr)
+          sD[i] = make_float2(__double2float_rn(mu - sHii[i].x), __double2float_rn(wn - sHii[i].y));
+        __syncthreads();
+        // A = (i w_n + mu) I - H_k - P_k^+ T in the owners' registers; the diagonal
+        // (i w_n + mu - H_ii) comes from sD, formed in FP64 and rounded once
+        float2 A[RA][RB];
+  #pragma unroll
+        for (int a = 0; a < RA; ++a)
+  #pragma unroll
           for (int b = 0; b < RB; ++b) {
-            const float2 u = urow[tc + TC * b];
-#pragma unroll
-            for (int a = 0; a < RA; ++a) fsub_prod(A[a][b], lv[a], u);
+            const int i = tr + TR * a, c = tc + TC * b;
+            float2 v = f2zero();
+            if (owner && i < N && c < N) v = (i == c) ? sD[i] : fneg(Hk[i * N + c]);
+            A[a][b] = v;
           }
-        } else if (warp == 0 && jn < N) {
-          float2* ncol = bCol + (bf ^ 1) * nbp;
-          const float2 u = urow[jn];
-          float2 v[4];
-          unsigned best = 0u;
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const int i = lane + 32 * t;
-            v[t] = f2zero();
-            if (i < N) {
-              v[t] = cxb[i];
-              fsub_prod(v[t], col[i], u);
-              if (!((used >> t) & 1u)) best = max(best, pack_key(v[t], i));
+        if (owner) {
+          for (int x = 0; x < M; ++x) {
+            float2 pv[RA];
+  #pragma unroll
+            for (int a = 0; a < RA; ++a) {
+              const int i = tr + TR * a;
+              pv[a] = (i < N) ? fneg(sP[x * N + i]) : f2zero();
+            }
+  #pragma unroll
+            for (int b = 0; b < RB; ++b) {
+              const int c = tc + TC * b;
+              const float2 tv = (c < N) ? sT[x * N + c] : f2zero();
+  #pragma unroll
+              for (int a = 0; a < RA; ++a) fmac_ca(A[a][b], pv[a], tv);
             }
           }
+        }
+        // Gauss-Jordan elimination with partial pivoting, without row interchanges
+        // (the exchange or sweep form of the elimination): step j pivots on
+        // (p_j, j), p_j the unused row of largest |A[i][j]|, so that afterwards
+        // X[i][c] = B[p_i][q_c] with q the inverse permutation of p.  Every step is
+        // one uniform rank-1 update of the whole tile,
+        //   A[i][c] -= l[i] u[c],  u = A[p][.] / A[p][j] with u[j] = 1/A[p][j],
+        //   l[i] = A[i][j] (i != p), l[p] = -1,
+        // after the owners of row p and of column j have zeroed them (so that row p
+        // becomes u and column j becomes -l u[j]).  Phases per step:
+        //  (R) owners of row p publish u and zero the row, owners of column j zero
+        //      it, owners of column j+1 publish it (cx);
+        //  (U) owners update their tiles; warp 0 applies the same update to cx,
+        //      picks p_{j+1} among the unused rows and forms the next l and
+        //      1/pivot (one pivot of lookahead).  Two barriers per step.
+        if (owner && tc == 0) {
+  #pragma unroll
+          for (int a = 0; a < RA; ++a) bCx[nbp + tr + TR * a] = A[a][0];
+        }
+        __syncthreads();
+        unsigned used = 0u;  // warp 0: bit t marks row lane + 32 t as a pivot row already
+        if (warp == 0) {
+          const float2* cx0 = bCx + nbp;
+          float2 v[4];
+          unsigned best = 0u;
+  #pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            v[t] = (i < N) ? cx0[i] : f2zero();
+            if (i < N) best = max(best, pack_key(v[t], i));
+          }
           best = __reduce_max_sync(0xffffffffu, best);
+          // a zero or non-finite pivot is flagged; the row index stays in range
           const int bi = min(127 - (int)(best & 127u), N - 1);
           if (lane == 0 && ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u))
             atomicOr(p.status, kFlagSingular);
-#pragma unroll
+  #pragma unroll
           for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            if (i < N) ncol[i] = (i == bi) ? make_float2(-1.f, 0.f) : v[t];
+            if (i < N) bCol[i] = (i == bi) ? make_float2(-1.f, 0.f) : v[t];
             if (i == bi) {
               used |= 1u << t;
-              s_r[bf ^ 1] = frcp(v[t]);
-              s_p[bf ^ 1] = bi;
-              s_pq[bf ^ 1] = bi / TR;
-              s_pm[bf ^ 1] = bi - (bi / TR) * TR;
-              sPiv[jn] = bi;
+              s_r[0] = frcp(v[t]);
+              s_p[0] = bi;
+              s_pq[0] = bi / TR;
+              s_pm[0] = bi - (bi / TR) * TR;
+              sPiv[0] = bi;
             }
           }
         }
         __syncthreads();
-        if (++jmc == TC) { jmc = 0; ++jqc; }
-        if (++nmc == TC) { nmc = 0; ++nqc; }
-      }
-      // B to shared memory; X[i][c] = B[p_i][q_c]: sPiv = p, sIdx = q = p^{-1}
-      if (owner) {
-#pragma unroll
-        for (int a = 0; a < RA; ++a)
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            const int i = tr + TR * a, c = tc + TC * b;
-            if (i < N && c < N) sG[i * ld + c] = A[a][b];
+        int jqc = 0, jmc = 0;                                 // j / TC, j % TC
+        int nqc = (TC > 1) ? 0 : 1, nmc = (TC > 1) ? 1 : 0;  // (j+1) / TC, (j+1) % TC
+        for (int j = 0; j < N; ++j) {
+          const int bf = j & 1;
+          const float2* col = bCol + bf * nbp;
+          float2* urow = bU + bf * nbp;
+          float2* cxb = bCx + bf * nbp;
+          const int prq = s_pq[bf], prm = s_pm[bf];
+          const float2 r = s_r[bf];
+          const int jn = j + 1;
+          if (owner) {
+            if (tr == prm) {
+  #pragma unroll
+              for (int a = 0; a < RA; ++a)
+                if (a == prq) {
+  #pragma unroll
+                  for (int b = 0; b < RB; ++b) {
+                    const int c = tc + TC * b;
+                    urow[c] = (c == j) ? r : fmul(A[a][b], r);
+                    A[a][b] = f2zero();
+                  }
+                }
+            }
+            if (tc == jmc) {
+  #pragma unroll
+              for (int b = 0; b < RB; ++b)
+                if (b == jqc) {
+  #pragma unroll
+                  for (int a = 0; a < RA; ++a) A[a][b] = f2zero();
+                }
+            }
+            if (jn < N && tc == nmc) {
+  #pragma unroll
+              for (int b = 0; b < RB; ++b)
+                if (b == nqc) {
+  #pragma unroll
+                  for (int a = 0; a < RA; ++a) cxb[tr + TR * a] = A[a][b];
+                }
+            }
           }
-      }
-      for (int j = tid; j < N; j += nthr) sIdx[sPiv[j]] = j;
-      __syncthreads();
-      for (int i = tid; i < N; i += nthr) sRow[i] = sPiv[i] * ld;
-      __syncthreads();
-
-      if (p.mode & kOcc) {
-        for (int i = tid; i < N; i += nthr) acc_tr += (double)sG[sRow[i] + sIdx[i]].x;
-        float g2 = 0.f;
-        for (int e = tid; e < N * N; e += nthr) {
-          const int i = e / N, c = e - i * N;
-          const float2 g1 = sG[sRow[i] + sIdx[c]], gt = sG[sRow[c] + sIdx[i]];
-          g2 = __fmaf_rn(g1.x, gt.x, __fmaf_rn(-g1.y, gt.y, g2));
-        }
-        acc_g2 += (double)g2;
-      }
-      if (p.mode & kRho) {
-        double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
-        const bool first = (n == it.n0);
-        for (int e = tid; e < N * N; e += nthr) {
-          const int i = e / N, c = e - i * N;
-          const float2 g = sG[sRow[i] + sIdx[c]];
-          if (first) {
-            S[e] = make_double2((double)g.x, (double)g.y);
-          } else {
-            double2 s = S[e];
-            s.x += (double)g.x;
-            s.y += (double)g.y;
-            S[e] = s;
-          }
-        }
-      }
-      if (p.mode & (kGloc | kAdj)) {
-        const bool adj = (p.mode & kAdj) != 0;
-        cf zw;  // -(i w_n + mu) as a pair
-        split(-mu, zw.rh, zw.rl);
-        split(-wn, zw.ih, zw.il);
-        const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
-        auto X = [&](int i, int c) { return sG[sRow[i] + sIdx[c]]; };
-        // Y0 = X P^+ (N x M)
-        mm_f32(N, M, N, X, [&](int c, int b) { return fconj(sP[b * N + c]); },
-               [&](int i, int b, float2 v) { sY0[i * M + b] = v; });
-        // Z0 = P X (M x N)
-        if (adj)
-          mm_f32(M, N, N, [&](int a, int i) { return sP[a * N + i]; }, X,
-                 [&](int a, int c, float2 v) { sZ0[a * N + c] = v; });
-        __syncthreads();
-        // W = P Y0 (pairs; the sum over bands split in S parts, partials in the R region)
-        const int S = max(1, min(4, N / M));
-        mm_pair(M, M, N, S, sPart, [&](int a, int i) { return ld4(Pkp[a * N + i]); },
-                [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
-                [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
-        __syncthreads();
-        // V = Sigma W (pairs)
-        mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(Sgp[a * M + x]); },
-                [&](int x, int b) { return ld4(sW[x * M + b]); }, [&](int, int) { return czero(); },
-                [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
-        __syncthreads();
-        // R = P^+ - A Y0 = P^+ - (i w + mu) Y0 + H Y0 + P^+ V  (pairs, rounded to FP32)
-        mm_pair(N, M, N, 1, sPart, [&](int i, int c) { return ld4(Hkp[i * N + c]); },
-                [&](int c, int b) { return sY0[c * M + b]; },
-                [&](int i, int b) {
-                  cf acc = conj_cf(ld4(Pkp[b * N + i]));
-                  cacc1(acc, zw, sY0[i * M + b]);
-                  for (int a = 0; a < M; ++a) cacc_ca(acc, ld4(Pkp[a * N + i]), ld4(sV[a * M + b]));
-                  return acc;
-                },
-                [&](int i, int b, const cf& v) { sR[i * M + b] = round_cf(v); });
-        __syncthreads();
-        // dY = X R (FP32);  Y = Y0 + dY
-        mm_f32(N, M, N, X, [&](int c, int b) { return sR[c * M + b]; },
-               [&](int i, int b, float2 v) { sdY[i * M + b] = v; });
-        __syncthreads();
-        // P Y = W + P dY (the second term in FP32)
-        if (p.mode & kGloc) {
-          double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-          mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
-                 [&](int i, int b) { return sdY[i * M + b]; },
-                 [&](int a, int b, float2 d) {
-                   const double2 w = to_d2(ld4(sW[a * M + b]));
-                   out[a * M + b] = make_double2(wk * (w.x + (double)d.x), wk * (w.y + (double)d.y));
-                 });
-        }
-        if (adj) {
-          // A_k = P Y in pairs
-          mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
-                 [&](int i, int b) { return sdY[i * M + b]; },
-                 [&](int a, int b, float2 d) {
-                   cf q = ld4(sW[a * M + b]);
-                   add_single(q, d);
-                   sQa[a * M + b] = st4(q);
-                 });
           __syncthreads();
-          // W' = Z0 P^+ (pairs), then V' = W' Sigma
-          mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
-                  [&](int i, int b) { return conj_cf(ld4(Pkp[b * N + i])); }, [&](int, int) { return czero(); },
+          if (owner) {
+            float2 lv[RA];
+  #pragma unroll
+            for (int a = 0; a < RA; ++a) lv[a] = col[tr + TR * a];
+  #pragma unroll
+            for (int b = 0; b < RB; ++b) {
+              const float2 u = urow[tc + TC * b];
+  #pragma unroll
+              for (int a = 0; a < RA; ++a) fsub_prod(A[a][b], lv[a], u);
+            }
+          } else if (warp == 0 && jn < N) {
+            float2* ncol = bCol + (bf ^ 1) * nbp;
+            const float2 u = urow[jn];
+            float2 v[4];
+            unsigned best = 0u;
+  #pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const int i = lane + 32 * t;
+              v[t] = f2zero();
+              if (i < N) {
+                v[t] = cxb[i];
+                fsub_prod(v[t], col[i], u);
+                if (!((used >> t) & 1u)) best = max(best, pack_key(v[t], i));
+              }
+            }
+            best = __reduce_max_sync(0xffffffffu, best);
+            const int bi = min(127 - (int)(best & 127u), N - 1);
+            if (lane == 0 && ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u))
+              atomicOr(p.status, kFlagSingular);
+  #pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const int i = lane + 32 * t;
+              if (i < N) ncol[i] = (i == bi) ? make_float2(-1.f, 0.f) : v[t];
+              if (i == bi) {
+                used |= 1u << t;
+                s_r[bf ^ 1] = frcp(v[t]);
+                s_p[bf ^ 1] = bi;
+                s_pq[bf ^ 1] = bi / TR;
+                s_pm[bf ^ 1] = bi - (bi / TR) * TR;
+                sPiv[jn] = bi;
+              }
+            }
+          }
+          __syncthreads();
+          if (++jmc == TC) { jmc = 0; ++jqc; }
+          if (++nmc == TC) { nmc = 0; ++nqc; }
+        }
+        // B to shared memory; X[i][c] = B[p_i][q_c]: sPiv = p, sIdx = q = p^{-1}
+        if (owner) {
+  #pragma unroll
+          for (int a = 0; a < RA; ++a)
+  #pragma unroll
+            for (int b = 0; b < RB; ++b) {
+              const int i = tr + TR * a, c = tc + TC * b;
+              if (i < N && c < N) sG[i * ld + c] = A[a][b];
+            }
+        }
+        for (int j = tid; j < N; j += nthr) sIdx[sPiv[j]] = j;
+        __syncthreads();
+        for (int i = tid; i < N; i += nthr) sRow[i] = sPiv[i] * ld;
+        __syncthreads();
+
+        if (p.mode & kOcc) {
+          for (int i = tid; i < N; i += nthr) acc_tr += (double)sG[sRow[i] + sIdx[i]].x;
+          float g2 = 0.f;
+          for (int e = tid; e < N * N; e += nthr) {
+            const int i = e / N, c = e - i * N;
+            const float2 g1 = sG[sRow[i] + sIdx[c]], gt = sG[sRow[c] + sIdx[i]];
+            g2 = __fmaf_rn(g1.x, gt.x, __fmaf_rn(-g1.y, gt.y, g2));
+          }
+          acc_g2 += (double)g2;
+        }
+        if (p.mode & kRho) {
+          double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
+          const bool first = (n == it.n0);
+          for (int e = tid; e < N * N; e += nthr) {
+            const int i = e / N, c = e - i * N;
+            const float2 g = sG[sRow[i] + sIdx[c]];
+            if (first) {
+              S[e] = make_double2((double)g.x, (double)g.y);
+            } else {
+              double2 s = S[e];
+              s.x += (double)g.x;
+              s.y += (double)g.y;
+              S[e] = s;
+            }
+          }
+        }
+        if (p.mode & (kGloc | kAdj)) {
+          const bool adj = (p.mode & kAdj) != 0;
+          cf zw;  // -(i w_n + mu) as a pair
+          split(-mu, zw.rh, zw.rl);
+          split(-wn, zw.ih, zw.il);
+          const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
+          auto X = [&](int i, int c) { return sG[sRow[i] + sIdx[c]]; };
+          // Y0 = X P^+ (N x M)
+          mm_f32(N, M, N, X, [&](int c, int b) { return fconj(sP[b * N + c]); },
+                 [&](int i, int b, float2 v) { sY0[i * M + b] = v; });
+          // Z0 = P X (M x N)
+          if (adj)
+            mm_f32(M, N, N, [&](int a, int i) { return sP[a * N + i]; }, X,
+                   [&](int a, int c, float2 v) { sZ0[a * N + c] = v; });
+          __syncthreads();
+          // W = P Y0 (pairs; the sum over bands split in S parts, partials in the R region)
+          const int S = max(1, min(4, N / M));
+          mm_pair(M, M, N, S, sPart, [&](int a, int i) { return ld4(Pkp[a * N + i]); },
+                  [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
                   [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
           __syncthreads();
-          mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(sW[a * M + x]); },
-                  [&](int x, int b) { return ld4(Sgp[x * M + b]); }, [&](int, int) { return czero(); },
+          // V = Sigma W (pairs)
+          mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(Sgp[a * M + x]); },
+                  [&](int x, int b) { return ld4(sW[x * M + b]); }, [&](int, int) { return czero(); },
                   [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
           __syncthreads();
-          // R' = P - Z0 A = P - (i w + mu) Z0 + Z0 H + V' P  (pairs, rounded), M x N
-          mm_pair(M, N, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
-                  [&](int i, int c) { return ld4(Hkp[i * N + c]); },
-                  [&](int a, int c) {
-                    cf acc = ld4(Pkp[a * N + c]);
-                    cacc1(acc, zw, sZ0[a * N + c]);
-                    for (int b = 0; b < M; ++b) cacc(acc, ld4(sV[a * M + b]), ld4(Pkp[b * N + c]));
+          // R = P^+ - A Y0 = P^+ - (i w + mu) Y0 + H Y0 + P^+ V  (pairs, rounded to FP32)
+          mm_pair(N, M, N, 1, sPart, [&](int i, int c) { return ld4(Hkp[i * N + c]); },
+                  [&](int c, int b) { return sY0[c * M + b]; },
+                  [&](int i, int b) {
+                    cf acc = conj_cf(ld4(Pkp[b * N + i]));
+                    cacc1(acc, zw, sY0[i * M + b]);
+                    for (int a = 0; a < M; ++a) cacc_ca(acc, ld4(Pkp[a * N + i]), ld4(sV[a * M + b]));
                     return acc;
                   },
-                  [&](int a, int c, const cf& v) { sR[a * N + c] = round_cf(v); });
+                  [&](int i, int b, const cf& v) { sR[i * M + b] = round_cf(v); });
           __syncthreads();
-          // dZ = R' X (FP32)
-          mm_f32(M, N, N, [&](int a, int i) { return sR[a * N + i]; }, X,
-                 [&](int a, int c, float2 v) { sdZ[a * N + c] = v; });
+          // dY = X R (FP32);  Y = Y0 + dY
+          mm_f32(N, M, N, X, [&](int c, int b) { return sR[c * M + b]; },
+                 [&](int i, int b, float2 v) { sdY[i * M + b] = v; });
           __syncthreads();
-          // B_k = Z Y = Z0 Y0 (pairs of exact FP32 products) + Z0 dY + dZ Y0 (FP32)
-          mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
-                  [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
-                  [&](int a, int b, const cf& v) { sQb[a * M + b] = st4(v); });
-          __syncthreads();
-          mm_f32(M, M, 2 * N,
-                 [&](int a, int k) { return k < N ? sZ0[a * N + k] : sdZ[a * N + k - N]; },
-                 [&](int k, int b) { return k < N ? sdY[k * M + b] : sY0[(k - N) * M + b]; },
-                 [&](int a, int b, float2 d) {
-                   cf q = ld4(sQb[a * M + b]);
-                   add_single(q, d);
-                   sQb[a * M + b] = st4(q);
-                 });
-          __syncthreads();
-          const bool have_gbar = (p.Gbd != nullptr);
-          if (have_gbar) {
-            const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
-            // Mt = Gbar A_k^+ (pairs)
-            mm_pair(M, M, M, 1, sPart, [&](int a, int c) { return ld4(Gb[a * M + c]); },
-                    [&](int c, int b) { return conj_cf(ld4(sQa[b * M + c])); }, [&](int, int) { return czero(); },
-                    [&](int a, int b, const cf& v) { sMt[a * M + b] = st4(v); });
-            // mu_bar partial: - w_k Re<Gbar, B_k>
-            for (int e = tid; e < M * M; e += nthr) {
-              const double2 gv = to_d2(ld4(Gb[e])), bv = to_d2(ld4(sQb[e]));
-              acc_mu -= wk * fma(gv.x, bv.x, gv.y * bv.y);
-            }
-            __syncthreads();
+          // P Y = W + P dY (the second term in FP32)
+          if (p.mode & kGloc) {
+            double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+            mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
+                   [&](int i, int b) { return sdY[i * M + b]; },
+                   [&](int a, int b, float2 d) {
+                     const double2 w = to_d2(ld4(sW[a * M + b]));
+                     gq_put(&out[a * M + b], q, make_double2(wk * (w.x + (double)d.x), wk * (w.y + (double)d.y)));
+                   });
           }
-          double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-          const double cb = nbar * 2.0 / beta;
-          for (int e = tid; e < M * M; e += nthr) {
-            const int a = e / M, b = e - a * M;
-            cf acc = czero();
-            if (have_gbar)
-              for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sMt[c * M + b]));
-            cnorm(acc);
-            const double2 v = to_d2(acc);
-            const double2 bt = to_d2(ld4(sQb[b * M + a]));
-            out[e] = make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y));
+          if (adj) {
+            // A_k = P Y in pairs
+            mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
+                   [&](int i, int b) { return sdY[i * M + b]; },
+                   [&](int a, int b, float2 d) {
+                     cf q = ld4(sW[a * M + b]);
+                     add_single(q, d);
+                     sQa[a * M + b] = st4(q);
+                   });
+            __syncthreads();
+            // W' = Z0 P^+ (pairs), then V' = W' Sigma
+            mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+                    [&](int i, int b) { return conj_cf(ld4(Pkp[b * N + i])); }, [&](int, int) { return czero(); },
+                    [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
+            __syncthreads();
+            mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(sW[a * M + x]); },
+                    [&](int x, int b) { return ld4(Sgp[x * M + b]); }, [&](int, int) { return czero(); },
+                    [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
+            __syncthreads();
+            // R' = P - Z0 A = P - (i w + mu) Z0 + Z0 H + V' P  (pairs, rounded), M x N
+            mm_pair(M, N, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+                    [&](int i, int c) { return ld4(Hkp[i * N + c]); },
+                    [&](int a, int c) {
+                      cf acc = ld4(Pkp[a * N + c]);
+                      cacc1(acc, zw, sZ0[a * N + c]);
+                      for (int b = 0; b < M; ++b) cacc(acc, ld4(sV[a * M + b]), ld4(Pkp[b * N + c]));
+                      return acc;
+                    },
+                    [&](int a, int c, const cf& v) { sR[a * N + c] = round_cf(v); });
+            __syncthreads();
+            // dZ = R' X (FP32)
+            mm_f32(M, N, N, [&](int a, int i) { return sR[a * N + i]; }, X,
+                   [&](int a, int c, float2 v) { sdZ[a * N + c] = v; });
+            __syncthreads();
+            // B_k = Z Y = Z0 Y0 (pairs of exact FP32 products) + Z0 dY + dZ Y0 (FP32)
+            mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+                    [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
+                    [&](int a, int b, const cf& v) { sQb[a * M + b] = st4(v); });
+            __syncthreads();
+            mm_f32(M, M, 2 * N,
+                   [&](int a, int k) { return k < N ? sZ0[a * N + k] : sdZ[a * N + k - N]; },
+                   [&](int k, int b) { return k < N ? sdY[k * M + b] : sY0[(k - N) * M + b]; },
+                   [&](int a, int b, float2 d) {
+                     cf q = ld4(sQb[a * M + b]);
+                     add_single(q, d);
+                     sQb[a * M + b] = st4(q);
+                   });
+            __syncthreads();
+            const bool have_gbar = (p.Gbd != nullptr);
+            if (have_gbar) {
+              const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
+              // Mt = Gbar A_k^+ (pairs)
+              mm_pair(M, M, M, 1, sPart, [&](int a, int c) { return ld4(Gb[a * M + c]); },
+                      [&](int c, int b) { return conj_cf(ld4(sQa[b * M + c])); }, [&](int, int) { return czero(); },
+                      [&](int a, int b, const cf& v) { sMt[a * M + b] = st4(v); });
+              // mu_bar partial: - w_k Re<Gbar, B_k>
+              for (int e = tid; e < M * M; e += nthr) {
+                const double2 gv = to_d2(ld4(Gb[e])), bv = to_d2(ld4(sQb[e]));
+                acc_mu -= wk * fma(gv.x, bv.x, gv.y * bv.y);
+              }
+              __syncthreads();
+            }
+            double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+            const double cb = nbar * 2.0 / beta;
+            for (int e = tid; e < M * M; e += nthr) {
+              const int a = e / M, b = e - a * M;
+              cf acc = czero();
+              if (have_gbar)
+                for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sMt[c * M + b]));
+              cnorm(acc);
+              const double2 v = to_d2(acc);
+              const double2 bt = to_d2(ld4(sQb[b * M + a]));
+              gq_put(&out[e], q, make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y)));
+            }
           }
         }
       }
-    }
-    if (p.mode & kOcc) {
-      const double tr_ = block_sum_f(acc_tr, s_red);
-      const double g2 = block_sum_f(acc_g2, s_red);
-      if (tid == 0) {
-        double* o = p.occ_part + ((int64_t)it.k * p.n_chunks + it.chunk) * 2;
-        o[0] = tr_;
-        o[1] = g2;
+      if (p.mode & kOcc) {
+        const double tr_ = block_sum_f(acc_tr, s_red);
+        const double g2 = block_sum_f(acc_g2, s_red);
+        if (tid == 0) {
+          double* o = p.occ_part + ((int64_t)kk * p.n_chunks + it.chunk) * 2;
+          o[0] = tr_;
+          o[1] = g2;
+        }
       }
+      if (p.mode & kAdj) {
+        const double mb = block_sum_f(acc_mu, s_red);
+        if (tid == 0) p.mubar_part[(int64_t)kk * p.n_chunks + it.chunk] = mb;
+      }
+      __syncthreads();
     }
-    if (p.mode & kAdj) {
-      const double mb = block_sum_f(acc_mu, s_red);
-      if (tid == 0) p.mubar_part[(int64_t)it.k * p.n_chunks + it.chunk] = mb;
-    }
-    __syncthreads();
   }
 }
 

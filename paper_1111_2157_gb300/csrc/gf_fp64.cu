@@ -17,53 +17,17 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "gf_complex.cuh"
 #include "gf_internal.cuh"
 
 namespace gf {
 
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-// acc += a * b
-__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-}
-// acc += conj(a) * b
-__device__ __forceinline__ void cmac_ca(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
-}
-// acc += a * conj(b)
-__device__ __forceinline__ void cmac_cb(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
-}
+using namespace cx;
 
-// 1/a by Smith's algorithm (R. L. Smith, CACM 5(8), 1962): scale by the
-// larger component so that no intermediate squares the inputs.
-__device__ __forceinline__ double2 crcp(double2 a) {
-  if (fabs(a.x) >= fabs(a.y)) {
-    const double t = a.y / a.x;
-    const double id = 1.0 / fma(a.y, t, a.x);
-    return make_double2(id, -t * id);
-  } else {
-    const double t = a.x / a.y;
-    const double id = 1.0 / fma(a.x, t, a.y);
-    return make_double2(t * id, -id);
-  }
-}
 
-// Pivot key: max(|Re|, |Im|) compared through the IEEE bit pattern, which
-// orders non-negative doubles like their values; no FP64 instruction.
-__device__ __forceinline__ unsigned long long pivot_key(double2 a) {
-  const unsigned long long mask = 0x7fffffffffffffffULL;
-  const unsigned long long r = (unsigned long long)__double_as_longlong(a.x) & mask;
-  const unsigned long long i = (unsigned long long)__double_as_longlong(a.y) & mask;
-  return r > i ? r : i;
-}
+
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
   // Deterministic: fixed xor tree inside each warp, then warp 0 over the warps.
@@ -179,164 +143,167 @@ __global__ void __launch_bounds__(kThreads) k_point_fp64(const PointParams p) {
     const int itx = s_item;
     if (itx >= p.n_items) break;
     const Item it = p.items[itx];
-    const KInfo ki = p.kinfo[it.k];
-    const SInfo si = p.sinfo[ki.sys];
-    const int N = ki.nb, M = si.m, ld = N | 1;
-    double2* A = p.a_in_smem ? (sm + L.offA) : (p.a_scratch + (int64_t)blockIdx.x * p.a_stride);
-    const double2* Hk = p.H + ki.offH;
-    const double2* Pg = p.P + ki.offP;
-    const double mu = p.mu[ki.sys];
-    const double beta = si.beta;
-    const double wk = ki.w;
-    double nbar = 0.0;
-    if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
-    for (int e = tid; e < M * N; e += kThreads) sP[e] = Pg[e];
+    for (int q = 0; q < it.nk; ++q) {
+      const int kk = item_k(it, p.kperm, q);
+      const KInfo ki = p.kinfo[kk];
+      const SInfo si = p.sinfo[ki.sys];
+      const int N = ki.nb, M = si.m, ld = N | 1;
+      double2* A = p.a_in_smem ? (sm + L.offA) : (p.a_scratch + (int64_t)blockIdx.x * p.a_stride);
+      const double2* Hk = p.H + ki.offH;
+      const double2* Pg = p.P + ki.offP;
+      const double mu = p.mu[ki.sys];
+      const double beta = si.beta;
+      const double wk = ki.w;
+      double nbar = 0.0;
+      if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
+      for (int e = tid; e < M * N; e += kThreads) sP[e] = Pg[e];
 
-    double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
-    for (int n = it.n0; n < it.n1; ++n) {
-      const double wn = (2.0 * n + 1.0) * M_PI / beta;
-      const double2* Sg = p.Sig + si.offSig + (int64_t)n * M * M;
-      __syncthreads();  // previous epilogue done with sS / sT; sP loaded
-      for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
-      __syncthreads();
-      // T = Sigma(i w_n) P_k   (M x N)
-      for (int e = tid; e < M * N; e += kThreads) {
-        const int a = e / N, j = e - a * N;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int b = 0; b < M; ++b) cmac(acc, sS[a * M + b], sP[b * N + j]);
-        sT[e] = acc;
-      }
-      __syncthreads();
-      // A = (i w_n + mu) I - H_k - P_k^+ T, accumulated as d - H - sum_a conj(P_ai) T_aj
-      for (int e = tid; e < N * N; e += kThreads) {
-        const int i = e / N, j = e - i * N;
-        const double2 h = Hk[e];
-        double2 v = make_double2((i == j ? mu : 0.0) - h.x, (i == j ? wn : 0.0) - h.y);
-        for (int a = 0; a < M; ++a) {
-          const double2 p = sP[a * N + i], t = sT[a * N + j];
-          v.x = fma(-p.x, t.x, fma(-p.y, t.y, v.x));
-          v.y = fma(-p.x, t.y, fma(p.y, t.x, v.y));
-        }
-        A[i * ld + j] = v;
-      }
-      __syncthreads();
-      gauss_jordan_fp64(A, N, ld, sCol, sU, sPiv, sIdx, p.status);
-      // G[i][c] = A[i * ld + sIdx[c]]
-
-      if (p.mode & kOcc) {
-        for (int i = tid; i < N; i += kThreads) acc_tr += A[i * ld + sIdx[i]].x;
-        for (int e = tid; e < N * N; e += kThreads) {
-          const int i = e / N, c = e - i * N;
-          const double2 g1 = A[i * ld + sIdx[c]], g2 = A[c * ld + sIdx[i]];
-          acc_g2 = fma(g1.x, g2.x, fma(-g1.y, g2.y, acc_g2));
-        }
-      }
-      if (p.mode & kRho) {
-        double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
-        const bool first = (n == it.n0);
-        for (int e = tid; e < N * N; e += kThreads) {
-          const int i = e / N, c = e - i * N;
-          const double2 g = A[i * ld + sIdx[c]];
-          if (first) {
-            S[e] = g;
-          } else {
-            double2 s = S[e];
-            s.x += g.x; s.y += g.y;
-            S[e] = s;
-          }
-        }
-      }
-      if (p.mode & (kGloc | kAdj)) {
-        // Y = G P^+ (N x M), in sT
-        for (int e = tid; e < N * M; e += kThreads) {
-          const int i = e / M, b = e - i * M;
+      double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
+      for (int n = it.n0; n < it.n1; ++n) {
+        const double wn = (2.0 * n + 1.0) * M_PI / beta;
+        const double2* Sg = p.Sig + si.offSig + (int64_t)n * M * M;
+        __syncthreads();  // previous epilogue done with sS / sT; sP loaded
+        for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
+        __syncthreads();
+        // T = Sigma(i w_n) P_k   (M x N)
+        for (int e = tid; e < M * N; e += kThreads) {
+          const int a = e / N, j = e - a * N;
           double2 acc = make_double2(0.0, 0.0);
-          for (int c = 0; c < N; ++c) cmac_cb(acc, A[i * ld + sIdx[c]], sP[b * N + c]);
+          for (int b = 0; b < M; ++b) cmac(acc, sS[a * M + b], sP[b * N + j]);
           sT[e] = acc;
         }
-        if (p.mode & kAdj) {
-          // Z = P G (M x N)
-          for (int e = tid; e < M * N; e += kThreads) {
-            const int a = e / N, c = e - a * N;
+        __syncthreads();
+        // A = (i w_n + mu) I - H_k - P_k^+ T, accumulated as d - H - sum_a conj(P_ai) T_aj
+        for (int e = tid; e < N * N; e += kThreads) {
+          const int i = e / N, j = e - i * N;
+          const double2 h = Hk[e];
+          double2 v = make_double2((i == j ? mu : 0.0) - h.x, (i == j ? wn : 0.0) - h.y);
+          for (int a = 0; a < M; ++a) {
+            const double2 p = sP[a * N + i], t = sT[a * N + j];
+            v.x = fma(-p.x, t.x, fma(-p.y, t.y, v.x));
+            v.y = fma(-p.x, t.y, fma(p.y, t.x, v.y));
+          }
+          A[i * ld + j] = v;
+        }
+        __syncthreads();
+        gauss_jordan_fp64(A, N, ld, sCol, sU, sPiv, sIdx, p.status);
+        // G[i][c] = A[i * ld + sIdx[c]]
+
+        if (p.mode & kOcc) {
+          for (int i = tid; i < N; i += kThreads) acc_tr += A[i * ld + sIdx[i]].x;
+          for (int e = tid; e < N * N; e += kThreads) {
+            const int i = e / N, c = e - i * N;
+            const double2 g1 = A[i * ld + sIdx[c]], g2 = A[c * ld + sIdx[i]];
+            acc_g2 = fma(g1.x, g2.x, fma(-g1.y, g2.y, acc_g2));
+          }
+        }
+        if (p.mode & kRho) {
+          double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
+          const bool first = (n == it.n0);
+          for (int e = tid; e < N * N; e += kThreads) {
+            const int i = e / N, c = e - i * N;
+            const double2 g = A[i * ld + sIdx[c]];
+            if (first) {
+              S[e] = g;
+            } else {
+              double2 s = S[e];
+              s.x += g.x; s.y += g.y;
+              S[e] = s;
+            }
+          }
+        }
+        if (p.mode & (kGloc | kAdj)) {
+          // Y = G P^+ (N x M), in sT
+          for (int e = tid; e < N * M; e += kThreads) {
+            const int i = e / M, b = e - i * M;
             double2 acc = make_double2(0.0, 0.0);
-            const int col = sIdx[c];
-            for (int i = 0; i < N; ++i) cmac(acc, sP[a * N + i], A[i * ld + col]);
-            sZ[e] = acc;
+            for (int c = 0; c < N; ++c) cmac_cb(acc, A[i * ld + sIdx[c]], sP[b * N + c]);
+            sT[e] = acc;
           }
-        }
-        __syncthreads();
-      }
-      if (p.mode & kGloc) {
-        double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, b = e - a * M;
-          double2 acc = make_double2(0.0, 0.0);
-          for (int i = 0; i < N; ++i) cmac(acc, sP[a * N + i], sT[i * M + b]);
-          out[e] = make_double2(wk * acc.x, wk * acc.y);
-        }
-      }
-      if (p.mode & kAdj) {
-        // A_k = P Y, B_k = Z Y  (M x M)
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, b = e - a * M;
-          double2 aa = make_double2(0.0, 0.0), bb = make_double2(0.0, 0.0);
-          for (int i = 0; i < N; ++i) {
-            const double2 y = sT[i * M + b];
-            cmac(aa, sP[a * N + i], y);
-            cmac(bb, sZ[a * N + i], y);
+          if (p.mode & kAdj) {
+            // Z = P G (M x N)
+            for (int e = tid; e < M * N; e += kThreads) {
+              const int a = e / N, c = e - a * N;
+              double2 acc = make_double2(0.0, 0.0);
+              const int col = sIdx[c];
+              for (int i = 0; i < N; ++i) cmac(acc, sP[a * N + i], A[i * ld + col]);
+              sZ[e] = acc;
+            }
           }
-          sQa[e] = aa;
-          sQb[e] = bb;
-        }
-        __syncthreads();
-        const bool have_gbar = (p.gbar != nullptr);
-        if (have_gbar) {
-          const double2* Gb = p.gbar + si.offSig + (int64_t)n * M * M;
-          for (int e = tid; e < M * M; e += kThreads) sS[e] = Gb[e];
           __syncthreads();
-          // Mt = Gbar A^+  (M x M), in sT
+        }
+        if (p.mode & kGloc) {
+          double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
           for (int e = tid; e < M * M; e += kThreads) {
             const int a = e / M, b = e - a * M;
             double2 acc = make_double2(0.0, 0.0);
-            for (int c = 0; c < M; ++c) cmac_cb(acc, sS[a * M + c], sQa[b * M + c]);
-            sT[e] = acc;
+            for (int i = 0; i < N; ++i) cmac(acc, sP[a * N + i], sT[i * M + b]);
+            gq_put(&out[e], q, make_double2(wk * acc.x, wk * acc.y));
+          }
+        }
+        if (p.mode & kAdj) {
+          // A_k = P Y, B_k = Z Y  (M x M)
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, b = e - a * M;
+            double2 aa = make_double2(0.0, 0.0), bb = make_double2(0.0, 0.0);
+            for (int i = 0; i < N; ++i) {
+              const double2 y = sT[i * M + b];
+              cmac(aa, sP[a * N + i], y);
+              cmac(bb, sZ[a * N + i], y);
+            }
+            sQa[e] = aa;
+            sQb[e] = bb;
           }
           __syncthreads();
-          // mu_bar partial: - w_k Re<Gbar, B>
+          const bool have_gbar = (p.gbar != nullptr);
+          if (have_gbar) {
+            const double2* Gb = p.gbar + si.offSig + (int64_t)n * M * M;
+            for (int e = tid; e < M * M; e += kThreads) sS[e] = Gb[e];
+            __syncthreads();
+            // Mt = Gbar A^+  (M x M), in sT
+            for (int e = tid; e < M * M; e += kThreads) {
+              const int a = e / M, b = e - a * M;
+              double2 acc = make_double2(0.0, 0.0);
+              for (int c = 0; c < M; ++c) cmac_cb(acc, sS[a * M + c], sQa[b * M + c]);
+              sT[e] = acc;
+            }
+            __syncthreads();
+            // mu_bar partial: - w_k Re<Gbar, B>
+            for (int e = tid; e < M * M; e += kThreads) {
+              const double2 g = sS[e], b = sQb[e];
+              acc_mu -= wk * fma(g.x, b.x, g.y * b.y);
+            }
+          }
+          double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+          const double cb = nbar * 2.0 / beta;
           for (int e = tid; e < M * M; e += kThreads) {
-            const double2 g = sS[e], b = sQb[e];
-            acc_mu -= wk * fma(g.x, b.x, g.y * b.y);
+            const int a = e / M, b = e - a * M;
+            double2 acc = make_double2(0.0, 0.0);
+            if (have_gbar)
+              for (int c = 0; c < M; ++c) cmac_ca(acc, sQa[c * M + a], sT[c * M + b]);
+            const double2 bt = sQb[b * M + a];  // (B^+)_{ab} = conj(B_{ba})
+            acc.x = fma(cb, bt.x, acc.x);
+            acc.y = fma(-cb, bt.y, acc.y);
+            gq_put(&out[e], q, make_double2(wk * acc.x, wk * acc.y));
           }
         }
-        double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-        const double cb = nbar * 2.0 / beta;
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, b = e - a * M;
-          double2 acc = make_double2(0.0, 0.0);
-          if (have_gbar)
-            for (int c = 0; c < M; ++c) cmac_ca(acc, sQa[c * M + a], sT[c * M + b]);
-          const double2 bt = sQb[b * M + a];  // (B^+)_{ab} = conj(B_{ba})
-          acc.x = fma(cb, bt.x, acc.x);
-          acc.y = fma(-cb, bt.y, acc.y);
-          out[e] = make_double2(wk * acc.x, wk * acc.y);
+      }
+      // Item end: deterministic block reductions of the per-thread partials.
+      if (p.mode & kOcc) {
+        const double tr = block_sum(acc_tr, s_red);
+        const double g2 = block_sum(acc_g2, s_red);
+        if (tid == 0) {
+          double* o = p.occ_part + ((int64_t)kk * p.n_chunks + it.chunk) * 2;
+          o[0] = tr;
+          o[1] = g2;
         }
       }
-    }
-    // Item end: deterministic block reductions of the per-thread partials.
-    if (p.mode & kOcc) {
-      const double tr = block_sum(acc_tr, s_red);
-      const double g2 = block_sum(acc_g2, s_red);
-      if (tid == 0) {
-        double* o = p.occ_part + ((int64_t)it.k * p.n_chunks + it.chunk) * 2;
-        o[0] = tr;
-        o[1] = g2;
+      if (p.mode & kAdj) {
+        const double mb = block_sum(acc_mu, s_red);
+        if (tid == 0) p.mubar_part[(int64_t)kk * p.n_chunks + it.chunk] = mb;
       }
+      __syncthreads();
     }
-    if (p.mode & kAdj) {
-      const double mb = block_sum(acc_mu, s_red);
-      if (tid == 0) p.mubar_part[(int64_t)it.k * p.n_chunks + it.chunk] = mb;
-    }
-    __syncthreads();
   }
 }
 
@@ -427,10 +394,11 @@ __global__ void __launch_bounds__(kThreads) k_rho_finalize(
   }
 }
 
-// acc[s][n][e] (+)= sum_{k in s, kb0 <= k < kb1} gq[k - kb0][n][e], k in increasing order.
-__global__ void k_gq_reduce(const KInfo* __restrict__ kinfo, const SInfo* __restrict__ sinfo,
-                            const double2* __restrict__ gq, int kb0, int kb1, int n_iw, int mmax,
-                            int first, double2* __restrict__ acc) {
+// acc[s][n][e] (+)= sum over the k-groups g of system s in [gb0, gb1) of gq[g - gb0][n][e], in
+// increasing g (each group's slot already holds its k-points' sum in k order).
+__global__ void k_gq_reduce(const SInfo* __restrict__ sinfo, const int* __restrict__ sys_g0,
+                            const int* __restrict__ sys_g1, const double2* __restrict__ gq, int gb0,
+                            int gb1, int n_iw, int mmax, int first, double2* __restrict__ acc) {
   const int s = blockIdx.y;
   const SInfo si = sinfo[s];
   const int M = si.m;
@@ -439,13 +407,13 @@ __global__ void k_gq_reduce(const KInfo* __restrict__ kinfo, const SInfo* __rest
   if (t >= total) return;
   const int n = (int)(t / (M * M));
   const int e = (int)(t - (int64_t)n * M * M);
-  const int ka = si.k0 > kb0 ? si.k0 : kb0;
-  const int kz = si.k1 < kb1 ? si.k1 : kb1;
+  const int ga = sys_g0[s] > gb0 ? sys_g0[s] : gb0;
+  const int gz = sys_g1[s] < gb1 ? sys_g1[s] : gb1;
   double2 v = first ? make_double2(0.0, 0.0) : acc[si.offSig + t];
-  for (int k = ka; k < kz; ++k) {
-    const double2 g = gq[((int64_t)(k - kb0) * n_iw + n) * mmax * mmax + e];
-    v.x += g.x;
-    v.y += g.y;
+  for (int g = ga; g < gz; ++g) {
+    const double2 x = gq[((int64_t)(g - gb0) * n_iw + n) * mmax * mmax + e];
+    v.x += x.x;
+    v.y += x.y;
   }
   acc[si.offSig + t] = v;
 }
@@ -555,11 +523,11 @@ cudaError_t launch_rho_finalize(const KInfo* kinfo, const SInfo* sinfo, const do
   return cudaGetLastError();
 }
 
-cudaError_t launch_gq_reduce(const KInfo* kinfo, const SInfo* sinfo, int n_sys, int max_mm_total,
-                             const double2* gq, int kb0, int kb1, int n_iw, int mmax, int first,
-                             double2* acc, cudaStream_t s) {
+cudaError_t launch_gq_reduce(const SInfo* sinfo, int n_sys, int max_mm_total, const int* sys_g0,
+                             const int* sys_g1, const double2* gq, int gb0, int gb1, int n_iw,
+                             int mmax, int first, double2* acc, cudaStream_t s) {
   dim3 grid((max_mm_total + 255) / 256, n_sys);
-  k_gq_reduce<<<grid, 256, 0, s>>>(kinfo, sinfo, gq, kb0, kb1, n_iw, mmax, first, acc);
+  k_gq_reduce<<<grid, 256, 0, s>>>(sinfo, sys_g0, sys_g1, gq, gb0, gb1, n_iw, mmax, first, acc);
   return cudaGetLastError();
 }
 

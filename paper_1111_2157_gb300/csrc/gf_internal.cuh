@@ -41,8 +41,12 @@ struct SInfo {          // one system
   int64_t offSinf;      // offset of [m][m] in Sigma_inf (complex elements)
 };
 
-struct Item {           // one unit of work: k-point k, frequencies [n0, n1)
-  int k, n0, n1, chunk;
+// One unit of work: frequencies [n0, n1) of nk k-points.  Modes with a k-reduction (kGloc,
+// kAdj) take the k-points kperm[k .. k+nk) of k-group g, whose contributions the CTA sums in
+// k order into one slot per (group, frequency); the other modes take the single k-point k
+// (nk = 1, no kperm).
+struct Item {
+  int k, n0, n1, chunk, nk, g;
 };
 
 struct PointParams {
@@ -76,8 +80,9 @@ struct PointParams {
   double* occ_part;     // [n_k][n_chunks][2]
   double2* rho_part;    // [n_chunks][sum_k N_b^2]
   int64_t rho_chunk_stride;
-  double2* gq;          // [k - kb0][n][mmax^2]
-  int kb0;
+  double2* gq;          // [g - gb0][n][mmax^2]: k-group sums of w_k P G P^+ (or the adjoint's)
+  int gb0;              // first k-group of the batch
+  const int* kperm;     // k-points of the k-groups (group items), or null (single-k items)
   int n_iw;
   // adjoint
   const double2* gbar;  // [sum_s n_iw m_s^2] or null
@@ -130,6 +135,20 @@ struct PoleParams {
 };
 
 __host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
+
+// k-point q of an item (see Item)
+__device__ __forceinline__ int item_k(const Item& it, const int* kperm, int q) {
+  return kperm ? kperm[it.k + q] : it.k + q;
+}
+// slot of a k-group sum: the first k-point of the group writes, the later ones add (in k order)
+__device__ __forceinline__ void gq_put(double2* out, int q, double2 v) {
+  if (q) {
+    const double2 o = *out;
+    v.x += o.x;
+    v.y += o.y;
+  }
+  *out = v;
+}
 
 // Thread t's share (of nthr threads) of Re Tr H_k + Re Tr(Sigma_inf P_k P_k^+), the trace
 // of the first-moment matrix H_k + P_k^+ Sigma_inf P_k that the tail needs; summing the
@@ -306,9 +325,11 @@ cudaError_t launch_rho_finalize(const KInfo* kinfo, const SInfo* sinfo, const do
                                 const double2* Einf, const double2* P, const double* mu,
                                 const double2* rho_part, int64_t rho_chunk_stride, int n_chunks,
                                 int n_k, double2* rho_out, double* kN, double* kNc, cudaStream_t s);
-cudaError_t launch_gq_reduce(const KInfo* kinfo, const SInfo* sinfo, int n_sys, int max_mm_total,
-                             const double2* gq, int kb0, int kb1, int n_iw, int mmax, int first,
-                             double2* acc, cudaStream_t s);
+// acc[s] (+)= sum over the k-groups g of system s in [gb0, gb1), in increasing g, of gq[g - gb0];
+// sys_g0 / sys_g1: [n_sys] first and end group of each system.
+cudaError_t launch_gq_reduce(const SInfo* sinfo, int n_sys, int max_mm_total, const int* sys_g0,
+                             const int* sys_g1, const double2* gq, int gb0, int gb1, int n_iw,
+                             int mmax, int first, double2* acc, cudaStream_t s);
 cudaError_t launch_einf(const KInfo* kinfo, const SInfo* sinfo, const double2* H, const double2* P,
                         const double2* Sinf, int n_k, double2* Einf, double* trHE, cudaStream_t s);
 cudaError_t launch_upcast(const float2* in, double2* out, int64_t n, cudaStream_t s);

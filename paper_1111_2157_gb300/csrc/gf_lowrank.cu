@@ -18,6 +18,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "gf_complex.cuh"
 #include "gf_internal.cuh"
 #include "gf_pair.cuh"
 
@@ -25,43 +26,10 @@ namespace gf {
 
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-}
-// acc += conj(a) * b
-__device__ __forceinline__ void cmac_ca(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
-}
-// acc += a * conj(b)
-__device__ __forceinline__ void cmac_cb(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
-}
+using namespace cx;
 
-// 1/a by Smith's algorithm (R. L. Smith, CACM 5(8), 1962).
-__device__ __forceinline__ double2 crcp(double2 a) {
-  if (fabs(a.x) >= fabs(a.y)) {
-    const double t = a.y / a.x;
-    const double id = 1.0 / fma(a.y, t, a.x);
-    return make_double2(id, -t * id);
-  } else {
-    const double t = a.x / a.y;
-    const double id = 1.0 / fma(a.x, t, a.y);
-    return make_double2(t * id, -id);
-  }
-}
 
-__device__ __forceinline__ unsigned long long pivot_key(double2 a) {
-  const unsigned long long mask = 0x7fffffffffffffffULL;
-  const unsigned long long r = (unsigned long long)__double_as_longlong(a.x) & mask;
-  const unsigned long long i = (unsigned long long)__double_as_longlong(a.y) & mask;
-  return r > i ? r : i;
-}
+
 
 __device__ __forceinline__ double lr_block_sum(double v, double* red) {
   for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -368,287 +336,290 @@ __global__ void __launch_bounds__(kThreads) k_point_lr(const PointParams p, cons
     const int itx = s_item;
     if (itx >= p.n_items) break;
     const Item it = p.items[itx];
-    const KInfo ki = p.kinfo[it.k];
-    const SInfo si = p.sinfo[ki.sys];
-    const int N = ki.nb, M = si.m, W = 2 * M;
-    const double mu = p.mu[ki.sys];
-    const double beta = si.beta;
-    const double wk = ki.w;
-    const double* eps = lr.eps + lr.offD[it.k];
-    double nbar = 0.0;
-    if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
-    for (int e = tid; e < M * N; e += kThreads) sPt[e] = lr.Pt[ki.offP + e];
-    // pairs a <= c, enumerated row by row; S threads share one pair's band sum
-    const int NP = M * (M + 1) / 2;
-    const int S = NP >= kThreads ? 1 : (2 * NP <= kThreads ? (4 * NP <= kThreads ? 4 : 2) : 1);
-    if (PAIR) {
-      for (int e = tid; e < M * N; e += kThreads) {
-        const double2 v = lr.Pt[ki.offP + e];
-        const pair::f2 re = pair::split(v.x), im = pair::split(v.y);
-        sPtd[e] = make_float4(re.h, re.l, im.h, im.l);
-      }
-    }
-    if (lr.t_in_smem) {
-      __syncthreads();
-      for (int e = tid; e < NP * N; e += kThreads) {
-        const int pq = e / N, b = e - (e / N) * N;
-        int a = 0, rem = pq;
-        while (rem >= M - a) { rem -= M - a; ++a; }
-        const int c = a + rem;
-        double2 t = make_double2(0.0, 0.0);
-        cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
-        if (PAIR) {
-          const pair::f2 re = pair::split(t.x), im = pair::split(t.y);
-          sTpd[e] = make_float4(re.h, re.l, im.h, im.l);
-        } else {
-          sTp[e] = t;
-        }
-      }
-    }
-    double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
-    for (int n = it.n0; n < it.n1; ++n) {
-      const double wn = (2.0 * n + 1.0) * M_PI / beta;
-      const double2* Sg = p.Sig + si.offSig + (int64_t)n * M * M;
-      __syncthreads();
-      for (int b = tid; b < N; b += kThreads) {
-        // d = 1 / (x + i w) = (x - i w) / (x^2 + w^2), x = mu - eps_b
-        const double x = mu - eps[b];
-        const double q = 1.0 / fma(x, x, wn * wn);
-        const double2 d = make_double2(x * q, -wn * q);
-        const double2 d2 = cmul(d, d);
-        sD[b] = d;
-        sD[N + b] = d2;
-        sD[2 * N + b] = cmul(d2, d);
-        if (PAIR) {
-          const double2 d3 = sD[2 * N + b];
-          const double2 dd[3] = {d, d2, d3};
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            const pair::f2 re = pair::split(dd[j].x), im = pair::split(dd[j].y);
-            sDd[j * N + b] = make_float4(re.h, re.l, im.h, im.l);
-          }
-        }
-      }
-      for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
-      __syncthreads();
-      // g_j = Pt D^{j+1} Pt^+.  With d = dr + i di and t = Pt_ab conj(Pt_cb):
-      // (g_j)_ac = Xr + i Xi and (g_j)_ca = conj(Xr) + i conj(Xi), Xr = sum t dr,
-      // Xi = sum t di, so only the pairs a <= c are summed.
-      const bool need_g2 = (p.mode & kOcc) != 0;
-      const bool need_g1 = (p.mode & (kOcc | kAdj)) != 0;
-      // (the loop bound is uniform across the block, so every lane of a warp reaches the
-      // shuffles; lanes past the end sum nothing and write nothing)
+    for (int q = 0; q < it.nk; ++q) {
+      const int kk = item_k(it, p.kperm, q);
+      const KInfo ki = p.kinfo[kk];
+      const SInfo si = p.sinfo[ki.sys];
+      const int N = ki.nb, M = si.m, W = 2 * M;
+      const double mu = p.mu[ki.sys];
+      const double beta = si.beta;
+      const double wk = ki.w;
+      const double* eps = lr.eps + lr.offD[kk];
+      double nbar = 0.0;
+      if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
+      for (int e = tid; e < M * N; e += kThreads) sPt[e] = lr.Pt[ki.offP + e];
+      // pairs a <= c, enumerated row by row; S threads share one pair's band sum
+      const int NP = M * (M + 1) / 2;
+      const int S = NP >= kThreads ? 1 : (2 * NP <= kThreads ? (4 * NP <= kThreads ? 4 : 2) : 1);
       if (PAIR) {
-        pair_band_sums(NP, S, M, N, need_g1, need_g2, lr.t_in_smem, sPtd, sTpd, sDd, g0, g1, g2,
-                       reinterpret_cast<float4*>(sC));
-      } else
-      for (int base = 0; base < NP * S; base += kThreads) {
-        const int e = base + tid;
-        const bool valid = e < NP * S;
-        const int pq = valid ? e / S : 0, part = valid ? e - (e / S) * S : 0;
-        int a = 0, rem = pq;
-        while (rem >= M - a) { rem -= M - a; ++a; }
-        const int c = a + rem;
-        double2 xr0 = make_double2(0.0, 0.0), xi0 = xr0, xr1 = xr0, xi1 = xr0, xr2 = xr0, xi2 = xr0;
-        for (int b = part; valid && b < N; b += S) {
-          double2 t;
-          if (lr.t_in_smem) {
-            t = sTp[pq * N + b];
-          } else {
-            t = make_double2(0.0, 0.0);
-            cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
-          }
-          const double2 d0 = sD[b];
-          xr0.x = fma(t.x, d0.x, xr0.x); xr0.y = fma(t.y, d0.x, xr0.y);
-          xi0.x = fma(t.x, d0.y, xi0.x); xi0.y = fma(t.y, d0.y, xi0.y);
-          if (need_g1) {
-            const double2 d1 = sD[N + b];
-            xr1.x = fma(t.x, d1.x, xr1.x); xr1.y = fma(t.y, d1.x, xr1.y);
-            xi1.x = fma(t.x, d1.y, xi1.x); xi1.y = fma(t.y, d1.y, xi1.y);
-          }
-          if (need_g2) {
-            const double2 d2 = sD[2 * N + b];
-            xr2.x = fma(t.x, d2.x, xr2.x); xr2.y = fma(t.y, d2.x, xr2.y);
-            xi2.x = fma(t.x, d2.y, xi2.x); xi2.y = fma(t.y, d2.y, xi2.y);
-          }
-        }
-        // the S partial sums of a pair sit in consecutive lanes of one warp (S | 32 and
-        // base is a multiple of 32)
-        for (int off = 1; off < S; off <<= 1) {
-#define GF_LR_RED(v)                                        \
-  v.x += __shfl_xor_sync(0xffffffffu, v.x, off);            \
-  v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
-          GF_LR_RED(xr0) GF_LR_RED(xi0) GF_LR_RED(xr1) GF_LR_RED(xi1) GF_LR_RED(xr2) GF_LR_RED(xi2)
-#undef GF_LR_RED
-        }
-        if (valid && part == 0) {
-          g0[a * M + c] = make_double2(xr0.x - xi0.y, xr0.y + xi0.x);
-          g0[c * M + a] = make_double2(xr0.x + xi0.y, xi0.x - xr0.y);
-          g1[a * M + c] = make_double2(xr1.x - xi1.y, xr1.y + xi1.x);
-          g1[c * M + a] = make_double2(xr1.x + xi1.y, xi1.x - xr1.y);
-          g2[a * M + c] = make_double2(xr2.x - xi2.y, xr2.y + xi2.x);
-          g2[c * M + a] = make_double2(xr2.x + xi2.y, xi2.x - xr2.y);
-        }
-      }
-      __syncthreads();
-      if (PAIR) {
-        // Sigma as pairs in sC2's storage (sC holds g0 as pairs); both are free until K exists
-        float4* Sp = reinterpret_cast<float4*>(sC2);
-        for (int e = tid; e < M * M; e += kThreads) {
-          const pair::f2 re = pair::split(sS[e].x), im = pair::split(sS[e].y);
-          Sp[e] = make_float4(re.h, re.l, im.h, im.l);
-        }
-        __syncthreads();
-        pair_solve(Sp, reinterpret_cast<const float4*>(sC), aug, M, reinterpret_cast<float4*>(sCol),
-                   reinterpret_cast<float4*>(sU), p.status);
-      } else {
-        // aug = [I - Sigma g0 | Sigma]
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, c = e - (e / M) * M;
-          double2 acc = make_double2(a == c ? 1.0 : 0.0, 0.0);
-          for (int x = 0; x < M; ++x) {
-            const double2 s = sS[a * M + x], g = g0[x * M + c];
-            acc.x -= fma(s.x, g.x, -s.y * g.y);
-            acc.y -= fma(s.x, g.y, s.y * g.x);
-          }
-          aug[a * W + c] = acc;
-          aug[a * W + M + c] = sS[e];
-        }
-        __syncthreads();
-        gj_augmented(aug, M, sCol, sU, p.status);
-      }
-      const double2* K = aug + M;  // K[a * W + c]
-      if (p.mode & (kOcc | kAdj)) mm(sC, K, W, g1, M);
-      if (p.mode & (kGloc | kAdj)) mm(sC2, K, W, g0, M);
-      __syncthreads();
-      if (p.mode & kOcc) {
-        for (int b = tid; b < N; b += kThreads) {
-          acc_tr += sD[b].x;
-          acc_g2 += sD[N + b].x;
-        }
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, c = e - (e / M) * M;
-          // Re of K_ac g1_ca, 2 K_ac g2_ca and (K g1)_ac (K g1)_ca
-          const double2 kk = K[a * W + c];
-          const double2 u = g1[c * M + a], v = g2[c * M + a];
-          const double2 x = sC[e], y = sC[c * M + a];
-          acc_tr += fma(kk.x, u.x, -kk.y * u.y);
-          acc_g2 += 2.0 * fma(kk.x, v.x, -kk.y * v.y) + fma(x.x, y.x, -x.y * y.y);
-        }
-      }
-      if (p.mode & kRho) {
-        // X = K Pt (M x N), then S' += D + D Pt^+ X D in the eigenbasis
         for (int e = tid; e < M * N; e += kThreads) {
-          const int a = e / N, b = e - (e / N) * N;
-          double2 acc = make_double2(0.0, 0.0);
-          for (int c = 0; c < M; ++c) cmac(acc, K[a * W + c], sPt[c * N + b]);
-          sX[e] = acc;
+          const double2 v = lr.Pt[ki.offP + e];
+          const pair::f2 re = pair::split(v.x), im = pair::split(v.y);
+          sPtd[e] = make_float4(re.h, re.l, im.h, im.l);
         }
+      }
+      if (lr.t_in_smem) {
         __syncthreads();
-        double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
-        const bool first = (n == it.n0);
-        for (int e = tid; e < N * N; e += kThreads) {
-          const int b = e / N, c = e - (e / N) * N;
-          double2 acc = make_double2(0.0, 0.0);
-          for (int a = 0; a < M; ++a) cmac_ca(acc, sPt[a * N + b], sX[a * N + c]);
-          double2 g = cmul(cmul(sD[b], acc), sD[c]);
-          if (b == c) { g.x += sD[b].x; g.y += sD[b].y; }
-          if (first) {
-            S[e] = g;
+        for (int e = tid; e < NP * N; e += kThreads) {
+          const int pq = e / N, b = e - (e / N) * N;
+          int a = 0, rem = pq;
+          while (rem >= M - a) { rem -= M - a; ++a; }
+          const int c = a + rem;
+          double2 t = make_double2(0.0, 0.0);
+          cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
+          if (PAIR) {
+            const pair::f2 re = pair::split(t.x), im = pair::split(t.y);
+            sTpd[e] = make_float4(re.h, re.l, im.h, im.l);
           } else {
-            double2 s = S[e];
-            s.x += g.x; s.y += g.y;
-            S[e] = s;
+            sTp[e] = t;
           }
         }
       }
-      if (p.mode & kGloc) {
-        // P G P^+ = g0 + g0 (K g0)
-        double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, c = e - (e / M) * M;
-          double2 acc = g0[e];
-          for (int x = 0; x < M; ++x) cmac(acc, g0[a * M + x], sC2[x * M + c]);
-          out[e] = make_double2(wk * acc.x, wk * acc.y);
-        }
-      }
-      if (p.mode & kAdj) {
-        double2* Aq = sX;
-        double2* Bq = sX + M * M;
-        double2* Gb = sX + 2 * M * M;
-        double2* Mt = sX + 3 * M * M;
-        double2* CC2 = aug;  // K no longer needed: (K g1)(K g0) in the left half of aug
+      double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
+      for (int n = it.n0; n < it.n1; ++n) {
+        const double wn = (2.0 * n + 1.0) * M_PI / beta;
+        const double2* Sg = p.Sig + si.offSig + (int64_t)n * M * M;
         __syncthreads();
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, c = e - (e / M) * M;
-          double2 acc = make_double2(0.0, 0.0);
-          for (int x = 0; x < M; ++x) cmac(acc, sC[a * M + x], sC2[x * M + c]);
-          CC2[a * W + c] = acc;
-        }
-        __syncthreads();
-        // A = g0 + g0 C2;  B = g1 + g1 C2 + g0 (C + C C2)
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, c = e - (e / M) * M;
-          double2 aa = g0[e], bb = g1[e];
-          for (int x = 0; x < M; ++x) {
-            const double2 c2 = sC2[x * M + c];
-            cmac(aa, g0[a * M + x], c2);
-            cmac(bb, g1[a * M + x], c2);
-            double2 t = sC[x * M + c];
-            const double2 u = CC2[x * W + c];
-            t.x += u.x;
-            t.y += u.y;
-            cmac(bb, g0[a * M + x], t);
+        for (int b = tid; b < N; b += kThreads) {
+          // d = 1 / (x + i w) = (x - i w) / (x^2 + w^2), x = mu - eps_b
+          const double x = mu - eps[b];
+          const double q = 1.0 / fma(x, x, wn * wn);
+          const double2 d = make_double2(x * q, -wn * q);
+          const double2 d2 = cmul(d, d);
+          sD[b] = d;
+          sD[N + b] = d2;
+          sD[2 * N + b] = cmul(d2, d);
+          if (PAIR) {
+            const double2 d3 = sD[2 * N + b];
+            const double2 dd[3] = {d, d2, d3};
+  #pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              const pair::f2 re = pair::split(dd[j].x), im = pair::split(dd[j].y);
+              sDd[j * N + b] = make_float4(re.h, re.l, im.h, im.l);
+            }
           }
-          Aq[e] = aa;
-          Bq[e] = bb;
+        }
+        for (int e = tid; e < M * M; e += kThreads) sS[e] = Sg[e];
+        __syncthreads();
+        // g_j = Pt D^{j+1} Pt^+.  With d = dr + i di and t = Pt_ab conj(Pt_cb):
+        // (g_j)_ac = Xr + i Xi and (g_j)_ca = conj(Xr) + i conj(Xi), Xr = sum t dr,
+        // Xi = sum t di, so only the pairs a <= c are summed.
+        const bool need_g2 = (p.mode & kOcc) != 0;
+        const bool need_g1 = (p.mode & (kOcc | kAdj)) != 0;
+        // (the loop bound is uniform across the block, so every lane of a warp reaches the
+        // shuffles; lanes past the end sum nothing and write nothing)
+        if (PAIR) {
+          pair_band_sums(NP, S, M, N, need_g1, need_g2, lr.t_in_smem, sPtd, sTpd, sDd, g0, g1, g2,
+                         reinterpret_cast<float4*>(sC));
+        } else
+        for (int base = 0; base < NP * S; base += kThreads) {
+          const int e = base + tid;
+          const bool valid = e < NP * S;
+          const int pq = valid ? e / S : 0, part = valid ? e - (e / S) * S : 0;
+          int a = 0, rem = pq;
+          while (rem >= M - a) { rem -= M - a; ++a; }
+          const int c = a + rem;
+          double2 xr0 = make_double2(0.0, 0.0), xi0 = xr0, xr1 = xr0, xi1 = xr0, xr2 = xr0, xi2 = xr0;
+          for (int b = part; valid && b < N; b += S) {
+            double2 t;
+            if (lr.t_in_smem) {
+              t = sTp[pq * N + b];
+            } else {
+              t = make_double2(0.0, 0.0);
+              cmac_cb(t, sPt[a * N + b], sPt[c * N + b]);
+            }
+            const double2 d0 = sD[b];
+            xr0.x = fma(t.x, d0.x, xr0.x); xr0.y = fma(t.y, d0.x, xr0.y);
+            xi0.x = fma(t.x, d0.y, xi0.x); xi0.y = fma(t.y, d0.y, xi0.y);
+            if (need_g1) {
+              const double2 d1 = sD[N + b];
+              xr1.x = fma(t.x, d1.x, xr1.x); xr1.y = fma(t.y, d1.x, xr1.y);
+              xi1.x = fma(t.x, d1.y, xi1.x); xi1.y = fma(t.y, d1.y, xi1.y);
+            }
+            if (need_g2) {
+              const double2 d2 = sD[2 * N + b];
+              xr2.x = fma(t.x, d2.x, xr2.x); xr2.y = fma(t.y, d2.x, xr2.y);
+              xi2.x = fma(t.x, d2.y, xi2.x); xi2.y = fma(t.y, d2.y, xi2.y);
+            }
+          }
+          // the S partial sums of a pair sit in consecutive lanes of one warp (S | 32 and
+          // base is a multiple of 32)
+          for (int off = 1; off < S; off <<= 1) {
+  #define GF_LR_RED(v)                                        \
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);            \
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+            GF_LR_RED(xr0) GF_LR_RED(xi0) GF_LR_RED(xr1) GF_LR_RED(xi1) GF_LR_RED(xr2) GF_LR_RED(xi2)
+  #undef GF_LR_RED
+          }
+          if (valid && part == 0) {
+            g0[a * M + c] = make_double2(xr0.x - xi0.y, xr0.y + xi0.x);
+            g0[c * M + a] = make_double2(xr0.x + xi0.y, xi0.x - xr0.y);
+            g1[a * M + c] = make_double2(xr1.x - xi1.y, xr1.y + xi1.x);
+            g1[c * M + a] = make_double2(xr1.x + xi1.y, xi1.x - xr1.y);
+            g2[a * M + c] = make_double2(xr2.x - xi2.y, xr2.y + xi2.x);
+            g2[c * M + a] = make_double2(xr2.x + xi2.y, xi2.x - xr2.y);
+          }
         }
         __syncthreads();
-        const bool have_gbar = (p.gbar != nullptr);
-        if (have_gbar) {
-          const double2* Gsrc = p.gbar + si.offSig + (int64_t)n * M * M;
-          for (int e = tid; e < M * M; e += kThreads) Gb[e] = Gsrc[e];
+        if (PAIR) {
+          // Sigma as pairs in sC2's storage (sC holds g0 as pairs); both are free until K exists
+          float4* Sp = reinterpret_cast<float4*>(sC2);
+          for (int e = tid; e < M * M; e += kThreads) {
+            const pair::f2 re = pair::split(sS[e].x), im = pair::split(sS[e].y);
+            Sp[e] = make_float4(re.h, re.l, im.h, im.l);
+          }
           __syncthreads();
+          pair_solve(Sp, reinterpret_cast<const float4*>(sC), aug, M, reinterpret_cast<float4*>(sCol),
+                     reinterpret_cast<float4*>(sU), p.status);
+        } else {
+          // aug = [I - Sigma g0 | Sigma]
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, c = e - (e / M) * M;
+            double2 acc = make_double2(a == c ? 1.0 : 0.0, 0.0);
+            for (int x = 0; x < M; ++x) {
+              const double2 s = sS[a * M + x], g = g0[x * M + c];
+              acc.x -= fma(s.x, g.x, -s.y * g.y);
+              acc.y -= fma(s.x, g.y, s.y * g.x);
+            }
+            aug[a * W + c] = acc;
+            aug[a * W + M + c] = sS[e];
+          }
+          __syncthreads();
+          gj_augmented(aug, M, sCol, sU, p.status);
+        }
+        const double2* K = aug + M;  // K[a * W + c]
+        if (p.mode & (kOcc | kAdj)) mm(sC, K, W, g1, M);
+        if (p.mode & (kGloc | kAdj)) mm(sC2, K, W, g0, M);
+        __syncthreads();
+        if (p.mode & kOcc) {
+          for (int b = tid; b < N; b += kThreads) {
+            acc_tr += sD[b].x;
+            acc_g2 += sD[N + b].x;
+          }
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, c = e - (e / M) * M;
+            // Re of K_ac g1_ca, 2 K_ac g2_ca and (K g1)_ac (K g1)_ca
+            const double2 kk = K[a * W + c];
+            const double2 u = g1[c * M + a], v = g2[c * M + a];
+            const double2 x = sC[e], y = sC[c * M + a];
+            acc_tr += fma(kk.x, u.x, -kk.y * u.y);
+            acc_g2 += 2.0 * fma(kk.x, v.x, -kk.y * v.y) + fma(x.x, y.x, -x.y * y.y);
+          }
+        }
+        if (p.mode & kRho) {
+          // X = K Pt (M x N), then S' += D + D Pt^+ X D in the eigenbasis
+          for (int e = tid; e < M * N; e += kThreads) {
+            const int a = e / N, b = e - (e / N) * N;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int c = 0; c < M; ++c) cmac(acc, K[a * W + c], sPt[c * N + b]);
+            sX[e] = acc;
+          }
+          __syncthreads();
+          double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
+          const bool first = (n == it.n0);
+          for (int e = tid; e < N * N; e += kThreads) {
+            const int b = e / N, c = e - (e / N) * N;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int a = 0; a < M; ++a) cmac_ca(acc, sPt[a * N + b], sX[a * N + c]);
+            double2 g = cmul(cmul(sD[b], acc), sD[c]);
+            if (b == c) { g.x += sD[b].x; g.y += sD[b].y; }
+            if (first) {
+              S[e] = g;
+            } else {
+              double2 s = S[e];
+              s.x += g.x; s.y += g.y;
+              S[e] = s;
+            }
+          }
+        }
+        if (p.mode & kGloc) {
+          // P G P^+ = g0 + g0 (K g0)
+          double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, c = e - (e / M) * M;
+            double2 acc = g0[e];
+            for (int x = 0; x < M; ++x) cmac(acc, g0[a * M + x], sC2[x * M + c]);
+            gq_put(&out[e], q, make_double2(wk * acc.x, wk * acc.y));
+          }
+        }
+        if (p.mode & kAdj) {
+          double2* Aq = sX;
+          double2* Bq = sX + M * M;
+          double2* Gb = sX + 2 * M * M;
+          double2* Mt = sX + 3 * M * M;
+          double2* CC2 = aug;  // K no longer needed: (K g1)(K g0) in the left half of aug
+          __syncthreads();
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, c = e - (e / M) * M;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int x = 0; x < M; ++x) cmac(acc, sC[a * M + x], sC2[x * M + c]);
+            CC2[a * W + c] = acc;
+          }
+          __syncthreads();
+          // A = g0 + g0 C2;  B = g1 + g1 C2 + g0 (C + C C2)
+          for (int e = tid; e < M * M; e += kThreads) {
+            const int a = e / M, c = e - (e / M) * M;
+            double2 aa = g0[e], bb = g1[e];
+            for (int x = 0; x < M; ++x) {
+              const double2 c2 = sC2[x * M + c];
+              cmac(aa, g0[a * M + x], c2);
+              cmac(bb, g1[a * M + x], c2);
+              double2 t = sC[x * M + c];
+              const double2 u = CC2[x * W + c];
+              t.x += u.x;
+              t.y += u.y;
+              cmac(bb, g0[a * M + x], t);
+            }
+            Aq[e] = aa;
+            Bq[e] = bb;
+          }
+          __syncthreads();
+          const bool have_gbar = (p.gbar != nullptr);
+          if (have_gbar) {
+            const double2* Gsrc = p.gbar + si.offSig + (int64_t)n * M * M;
+            for (int e = tid; e < M * M; e += kThreads) Gb[e] = Gsrc[e];
+            __syncthreads();
+            for (int e = tid; e < M * M; e += kThreads) {
+              const int a = e / M, b = e - (e / M) * M;
+              double2 acc = make_double2(0.0, 0.0);
+              for (int c = 0; c < M; ++c) cmac_cb(acc, Gb[a * M + c], Aq[b * M + c]);
+              Mt[e] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < M * M; e += kThreads) {
+              const double2 g = Gb[e], b = Bq[e];
+              acc_mu -= wk * fma(g.x, b.x, g.y * b.y);
+            }
+          }
+          double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+          const double cb = nbar * 2.0 / beta;
           for (int e = tid; e < M * M; e += kThreads) {
             const int a = e / M, b = e - (e / M) * M;
             double2 acc = make_double2(0.0, 0.0);
-            for (int c = 0; c < M; ++c) cmac_cb(acc, Gb[a * M + c], Aq[b * M + c]);
-            Mt[e] = acc;
-          }
-          __syncthreads();
-          for (int e = tid; e < M * M; e += kThreads) {
-            const double2 g = Gb[e], b = Bq[e];
-            acc_mu -= wk * fma(g.x, b.x, g.y * b.y);
+            if (have_gbar)
+              for (int c = 0; c < M; ++c) cmac_ca(acc, Aq[c * M + a], Mt[c * M + b]);
+            const double2 bt = Bq[b * M + a];
+            acc.x = fma(cb, bt.x, acc.x);
+            acc.y = fma(-cb, bt.y, acc.y);
+            gq_put(&out[e], q, make_double2(wk * acc.x, wk * acc.y));
           }
         }
-        double2* out = p.gq + ((int64_t)(it.k - p.kb0) * p.n_iw + n) * p.mmax * p.mmax;
-        const double cb = nbar * 2.0 / beta;
-        for (int e = tid; e < M * M; e += kThreads) {
-          const int a = e / M, b = e - (e / M) * M;
-          double2 acc = make_double2(0.0, 0.0);
-          if (have_gbar)
-            for (int c = 0; c < M; ++c) cmac_ca(acc, Aq[c * M + a], Mt[c * M + b]);
-          const double2 bt = Bq[b * M + a];
-          acc.x = fma(cb, bt.x, acc.x);
-          acc.y = fma(-cb, bt.y, acc.y);
-          out[e] = make_double2(wk * acc.x, wk * acc.y);
+      }
+      if (p.mode & kOcc) {
+        const double tr = lr_block_sum(acc_tr, s_red);
+        const double g2s = lr_block_sum(acc_g2, s_red);
+        if (tid == 0) {
+          double* o = p.occ_part + ((int64_t)kk * p.n_chunks + it.chunk) * 2;
+          o[0] = tr;
+          o[1] = g2s;
         }
       }
-    }
-    if (p.mode & kOcc) {
-      const double tr = lr_block_sum(acc_tr, s_red);
-      const double g2s = lr_block_sum(acc_g2, s_red);
-      if (tid == 0) {
-        double* o = p.occ_part + ((int64_t)it.k * p.n_chunks + it.chunk) * 2;
-        o[0] = tr;
-        o[1] = g2s;
+      if (p.mode & kAdj) {
+        const double mb = lr_block_sum(acc_mu, s_red);
+        if (tid == 0) p.mubar_part[(int64_t)kk * p.n_chunks + it.chunk] = mb;
       }
+      __syncthreads();
     }
-    if (p.mode & kAdj) {
-      const double mb = lr_block_sum(acc_mu, s_red);
-      if (tid == 0) p.mubar_part[(int64_t)it.k * p.n_chunks + it.chunk] = mb;
-    }
-    __syncthreads();
   }
 }
 

@@ -1,11 +1,12 @@
-// FP32-pair ("double-float") arithmetic for the low-rank kernel's band sums: a
-// value is the unevaluated sum hi + lo of two FP32 numbers.  Error-free
-// transformations (Knuth's two_sum, the FMA two_prod) keep about 2^-48 relative
-// precision per operation on the FP32 pipes.  The _rn intrinsics keep nvcc from
-// contracting or reassociating the steps.
+// FP32-pair ("double-float") scalars for the low-rank kernel's band sums: a value
+// is the unevaluated sum hi + lo of two FP32 numbers.  The error-free
+// transformations are those of gf_complex.cuh (Knuth's two_sum, the FMA
+// two_prod), about 2^-48 relative precision per operation on the FP32 pipes.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include "gf_complex.cuh"
 
 namespace gf {
 namespace pair {
@@ -14,24 +15,11 @@ struct f2 {
   float h, l;
 };
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
+using cx::two_sum;
 
 // acc += a * b: exact head product, first-order cross terms, head sum by two_sum;
 // acc is left unnormalised (its low word collects the rounding errors).
-__device__ __forceinline__ void mac(f2& acc, f2 a, f2 b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  float s, t;
-  two_sum(acc.h, p, s, t);
-  acc.h = s;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(t, e));
-}
+__device__ __forceinline__ void mac(f2& acc, f2 a, f2 b) { cx::acc_prod(a.h, a.l, b.h, b.l, acc.h, acc.l); }
 
 // acc += a (pairs)
 __device__ __forceinline__ void add(f2& acc, f2 a) {
@@ -43,8 +31,7 @@ __device__ __forceinline__ void add(f2& acc, f2 a) {
 
 __device__ __forceinline__ f2 split(double x) {
   f2 r;
-  r.h = __double2float_rn(x);
-  r.l = __double2float_rn(x - (double)r.h);
+  cx::split(x, r.h, r.l);
   return r;
 }
 

@@ -82,6 +82,8 @@ __global__ void __launch_bounds__(256) k_static_setup(
     it.n0 = ch * chunk_w;
     it.n1 = min(n_iw, (ch + 1) * chunk_w);
     it.chunk = ch;
+    it.nk = 1;
+    it.g = k;
     items[(int64_t)k * n_chunks + ch] = it;
   }
   double v = gf::trhe_partial(H + (int64_t)k * nb * nb, P + (int64_t)k * m * nb, Sinf, nb, m,
