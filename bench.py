@@ -13,6 +13,14 @@ iteration needs it:
   3. the adjoint at mu*: Sigma_bar and mu_bar for a seeded G_loc_bar and N_bar = 1.
 value = (k, i w_n) points evaluated per second (every pass counts its points).
 
+The same line carries, beside the FP64 headline: the mixed-precision step
+(FP32 inverse, FP64 sums, refined projections) and the FP32-pair step on the
+same workload; the low-rank (eigenbasis) algorithm; the NiO-like workload
+(N_k = 4096, N_b = 96, m = 20, 2048 frequencies): one fixed-mu fused pass on
+the FP64 and on the mixed path and the mixed mu search, with errors against
+the oracle; and the batched workload (8 systems, ragged windows of 48-128
+bands, complex128 and complex64 inputs in one context) on both paths.
+
 ``--impl reference`` times the FP64 CPU oracle (the plain definition, one LU
 inverse per point) on the host cores instead, on a bounded sample of the same
 workload, and prints the same JSON line with "impl": "reference".
@@ -801,7 +809,7 @@ def main():
         gloc_h = torch.empty(g.tot_sig, dtype=torch.complex128).pin_memory()
         rho_h = torch.empty(g.tot_h, dtype=torch.complex128).pin_memory()
         sbar_h = torch.empty(g.tot_sig, dtype=torch.complex128).pin_memory()
-        e2e_steps = max(1, min(args.steps, 2))
+        e2e_steps = max(1, min(args.steps, 5))
         pts = 0
 
         def step_host():

@@ -43,7 +43,7 @@ namespace {
 
 using namespace cx;
 
-constexpr int kMaxWarpsF = 18;
+constexpr int kMaxWarpsF = 24;
 
 __device__ __forceinline__ double block_sum_f(double v, double* red) {
   // Deterministic: fixed xor tree in each warp, then warp 0 over the warps.
@@ -697,9 +697,9 @@ struct ShapeF {
   int ra, rb, maxt, minb, nmax;
 };
 constexpr ShapeF kShapesF[] = {
-    {2, 2, 96, 4, 16}, {2, 5, 192, 3, 40}, {4, 5, 128, 4, 40}, {4, 4, 288, 2, 64},
-    {4, 8, 160, 3, 64}, {6, 8, 224, 2, 96}, {4, 8, 352, 1, 96}, {4, 8, 544, 1, 128},
-    {8, 8, 288, 1, 128},
+    {2, 2, 96, 4, 16},   {2, 5, 192, 3, 40},  {4, 5, 128, 4, 40},  {4, 4, 288, 2, 64},
+    {4, 8, 160, 3, 64},  {6, 8, 224, 2, 96},  {4, 8, 352, 1, 96},  {4, 8, 544, 1, 128},
+    {8, 8, 288, 1, 128}, {4, 4, 640, 1, 96},  {4, 6, 736, 1, 128},
 };
 constexpr int kNumShapesF = (int)(sizeof(kShapesF) / sizeof(kShapesF[0]));
 
@@ -734,7 +734,9 @@ int bps_f(int threads, size_t smem) {
   X(5, 6, 8, 224, 2)      \
   X(6, 4, 8, 352, 1)      \
   X(7, 4, 8, 544, 1)      \
-  X(8, 8, 8, 288, 1)
+  X(8, 8, 8, 288, 1)      \
+  X(9, 4, 4, 640, 1)      \
+  X(10, 4, 6, 736, 1)
 
 }  // namespace
 
