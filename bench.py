@@ -78,8 +78,10 @@ def parse():
                     help="arithmetic of the point kernel (mixed: FP32 inverse with refined "
                          "projections; pair: FP32 pairs on the FP32 pipes)")
     ap.add_argument("--workload", choices=["ce_like", "nio_like", "batched", "adjoint", "lowrank",
-                                           "pole", "dmft_step"],
+                                           "pole", "dmft_step", "mixed_kernel"],
                     default="ce_like", help="non-default workloads print one measurement line each")
+    ap.add_argument("--system", choices=["nio_like", "ce_like"], default="nio_like",
+                    help="--workload mixed_kernel: the shapes to run (with --nk / --n-iw)")
     ap.add_argument("--peaks", action="store_true",
                     help="compile and run the pipe-throughput microbenchmark (peaks.cu) and exit")
     return ap.parse_args()
@@ -442,6 +444,22 @@ def run_workload(args):
     out = {"workload": args.workload}
     if args.workload == "nio_like":
         out.update(nio_leg(gf, synth, o, nk=args.nk or 4096, n_iw=args.n_iw or 2048))
+    elif args.workload == "mixed_kernel":
+        # one N(mu) pass and one fused G_loc + N pass of the mixed kernel (profiling captures)
+        kw = {k: v for k, v in (("nk", args.nk), ("n_iw", args.n_iw)) if v}
+        s = (synth.nio_like(**kw) if args.system == "nio_like" else synth.ce_like(**kw)).systems[0]
+        g = _dev_context(gf, [s], args.precision if args.precision != "fp64" else "mixed")
+        res = {}
+        for name, call in (("occupation", lambda: g.occupation([0.1])),
+                           ("fused_gloc_N", lambda: g.evaluate([0.1], rho=False, n_corr=False))):
+            _, t = _sync_time(call)
+            st = g.stats()
+            res[name] = {"s": t, "kernel_s": st["kernel_ms"] / 1e3,
+                         "points_per_s": st["points"] / (st["kernel_ms"] / 1e3),
+                         "alg_tflops": st["flops"] / st["kernel_ms"] / 1e9}
+        out.update({"config": f"{args.system}: N_k={s.nk}, N_b={s.H.shape[-1]}, m={s.m}, N_w={s.n_iw}",
+                    "passes": res, "kernel_choice": g.tuning_log()})
+        g.close()
     elif args.workload == "batched":
         out.update(batched_leg(gf, synth, o, nk_scale=args.nk_scale))
     elif args.workload == "adjoint":

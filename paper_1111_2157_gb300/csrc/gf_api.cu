@@ -166,15 +166,18 @@ gf_status autotune(gf_ctx* c, int key, const std::vector<LaunchCfg>& cands, gf::
     *out = cands.back();
     return GF_OK;
   }
+  // the sample: one item per CTA of the largest candidate grid; a second run of a
+  // candidate only when its first took under 50 ms (the first run of a kernel also loads
+  // its module, which is noise against a long sample)
   int maxgrid = 1;
   for (const LaunchCfg& g : cands) maxgrid = std::max(maxgrid, g.grid);
-  const int n_sample = std::min(n_items, 2 * maxgrid);
+  const int n_sample = std::min(n_items, maxgrid);
   p.items = items;
   std::vector<float> ms(cands.size(), 0.f);
   ScopedEvents ev;
   GF_CU(ev.create());
   for (size_t cand = 0; cand < cands.size(); ++cand) {
-    for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the module
+    for (int rep = 0; rep < 2; ++rep) {
       GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
       GF_CU(cudaEventRecord(ev.start, c->stream));
       gf_status st = launch_cfg(c, cands[cand], p, n_sample);
@@ -183,6 +186,7 @@ gf_status autotune(gf_ctx* c, int key, const std::vector<LaunchCfg>& cands, gf::
       GF_CU(cudaEventSynchronize(ev.stop));
       GF_CU(cudaEventElapsedTime(&ms[cand], ev.start, ev.stop));
       c->last_launches += 1;
+      if (ms[cand] > 50.f) break;
     }
   }
   int best = 0;
