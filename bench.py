@@ -78,10 +78,10 @@ def parse():
                     help="arithmetic of the point kernel (mixed: FP32 inverse with refined "
                          "projections; pair: FP32 pairs on the FP32 pipes)")
     ap.add_argument("--workload", choices=["ce_like", "nio_like", "batched", "adjoint", "lowrank",
-                                           "pole", "dmft_step", "mixed_kernel"],
+                                           "pole", "dmft_step", "passes"],
                     default="ce_like", help="non-default workloads print one measurement line each")
     ap.add_argument("--system", choices=["nio_like", "ce_like"], default="nio_like",
-                    help="--workload mixed_kernel: the shapes to run (with --nk / --n-iw)")
+                    help="--workload passes: the shapes to run (with --nk / --n-iw)")
     ap.add_argument("--peaks", action="store_true",
                     help="compile and run the pipe-throughput microbenchmark (peaks.cu) and exit")
     return ap.parse_args()
@@ -324,8 +324,29 @@ def nio_leg(gf, synth, o, nk=4096, n_iw=2048):
     n_sub, dn_sub = gs.occupation(mu)
     gs.close()
     k_m, k_d = stm["kernel_ms"] / 1e3, st64["kernel_ms"] / 1e3
+    # the N(mu) pass at mu* on the tcgen05 tensor-core kernel (selected with GF_KERNEL=tc)
+    # beside the FP32 register kernel; N against the FP64 pass
+    n64 = float(ev64["N"][0])
+    tcl = {}
+    for kern in ("tc", "f32r"):
+        os.environ["GF_KERNEL"] = kern
+        try:
+            gk = _dev_context(gf, [s], "mixed")
+            gk.occupation(mu)  # the first call autotunes
+            (n_k, _), t_k = _sync_time(lambda: gk.occupation(mu))
+            stk = gk.stats()
+            tcl[kern] = {"pass_s": t_k, "pass_kernel_s": stk["kernel_ms"] / 1e3,
+                         "points_per_s": npts / (stk["kernel_ms"] / 1e3),
+                         "alg_tflops": stk["flops"] / stk["kernel_ms"] / 1e9,
+                         "N_rel_err_vs_fp64_gpu": abs(float(n_k[0]) - n64) / n64,
+                         "kernel_choice": gk.tuning_log()}
+            gk.close()
+        finally:
+            del os.environ["GF_KERNEL"]
+    tcl["tc_speed_vs_f32r"] = tcl["f32r"]["pass_kernel_s"] / tcl["tc"]["pass_kernel_s"]
     out.update({
         "mu_star": float(mu[0]), "N_at_mu_star": float(evm["N"][0]),
+        "N_pass_tensor_core_vs_fp32_kernel": tcl,
         "fp64": {"pass_s": t_64, "pass_kernel_s": k_d, "points_per_s": npts / k_d,
                  "kernel_tflops": st64["flops"] / st64["kernel_ms"] / 1e9,
                  "frac_of_fp64_peak": st64["flops"] / st64["kernel_ms"] / 1e9 / FP64_PEAK_TFLOPS,
@@ -444,11 +465,12 @@ def run_workload(args):
     out = {"workload": args.workload}
     if args.workload == "nio_like":
         out.update(nio_leg(gf, synth, o, nk=args.nk or 4096, n_iw=args.n_iw or 2048))
-    elif args.workload == "mixed_kernel":
-        # one N(mu) pass and one fused G_loc + N pass of the mixed kernel (profiling captures)
+    elif args.workload == "passes":
+        # one N(mu) pass and one fused G_loc + N pass of the point kernel of --precision
+        # (profiling captures; GF_KERNEL=tc puts the mixed N(mu) pass on the tensor cores)
         kw = {k: v for k, v in (("nk", args.nk), ("n_iw", args.n_iw)) if v}
         s = (synth.nio_like(**kw) if args.system == "nio_like" else synth.ce_like(**kw)).systems[0]
-        g = _dev_context(gf, [s], args.precision if args.precision != "fp64" else "mixed")
+        g = _dev_context(gf, [s], args.precision)
         res = {}
         for name, call in (("occupation", lambda: g.occupation([0.1])),
                            ("fused_gloc_N", lambda: g.evaluate([0.1], rho=False, n_corr=False))):

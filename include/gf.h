@@ -58,7 +58,7 @@ typedef enum {
     GF_ECUDA = 3,      /* a CUDA runtime call failed (message in gf_last_error)    */
     GF_ESINGULAR = 4,  /* a zero or non-finite pivot in some (k, i w_n) inverse    */
     GF_ENOTCONV = 5,   /* a mu search missed tol in max_iter, or Jacobi its sweep cap */
-    GF_ETIMEOUT = 6,   /* reserved: no kernel waits on a flag or a peer            */
+    GF_ETIMEOUT = 6,   /* a bounded wait of the tensor-core kernel on its MMAs gave up */
     GF_ESTATE = 7      /* inputs missing (e.g. gf_local before gf_set_sigma)        */
 } gf_status;
 
@@ -73,6 +73,9 @@ typedef enum {
  *                residual in FP32 pairs.  Errors against FP64: about
  *                kappa(A) 2^-24 per G entry before refinement, which averages
  *                to ~1e-9 relative on N(mu); ~1e-11 on G_loc after it.
+ *                With the environment variable GF_KERNEL=tc the N(mu) passes run
+ *                on the tcgen05 tensor cores instead (blocked elimination, TF32
+ *                split operands): N within ~1e-7 of FP64.
  *  GF_PREC_PAIR  every matrix entry an FP32 pair (hi + lo) with error-free
  *                transformations on the FP32 pipes: ~1e-14 of FP64 results. */
 typedef enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1, GF_PREC_PAIR = 2 } gf_precision;

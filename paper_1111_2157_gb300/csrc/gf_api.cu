@@ -100,8 +100,9 @@ gf_status check_ready(gf_ctx* c) {
 // Kernel configuration of one launch, i.e. of one bucket of band-window sizes.
 struct LaunchCfg {
   int kind = 0;        // 0 FP64, 1 FP32-pair shared-memory, 2 FP32-pair register-resident,
-                       // 3 low-rank, 4 FP32 register-resident with refined projections
-  int shape = -1;      // register tile shape (kinds 2 and 4)
+                       // 3 low-rank, 4 FP32 register-resident with refined projections,
+                       // 5 tensor-core (tcgen05) blocked elimination, N(mu) passes
+  int shape = -1;      // register tile shape (kinds 2 and 4); matrices per CTA (kind 5)
   int threads = gf::kThreads;
   size_t smem = 0;
   int grid = 1;
@@ -127,7 +128,12 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
     GF_CU(gf::launch_point_lr(p, lr, grid, cfg.smem, c->stream));
     return GF_OK;
   }
-  if (cfg.kind == 4) GF_CU(gf::launch_point_f32r(cfg.shape, p, grid, cfg.threads, cfg.smem, c->stream));
+  if (cfg.kind == 5) {
+    // GF_TC_TEST_SKIP_MMA=1 (failure-detection tests): the kernel's bounded waits run out
+    const char* skip = std::getenv("GF_TC_TEST_SKIP_MMA");
+    p.tc_skip_mma = (skip && std::atoi(skip) == 1) ? 1 : 0;
+    GF_CU(gf::launch_point_tc(cfg.shape, p, grid, cfg.smem, c->stream));
+  } else if (cfg.kind == 4) GF_CU(gf::launch_point_f32r(cfg.shape, p, grid, cfg.threads, cfg.smem, c->stream));
   else if (cfg.kind == 2) GF_CU(gf::launch_point_df64r(cfg.shape, p, grid, cfg.threads, cfg.smem, c->stream));
   else if (cfg.kind == 1) GF_CU(gf::launch_point_df64(p, grid, cfg.smem, c->stream));
   else GF_CU(gf::launch_point_fp64(p, grid, cfg.smem, c->stream));
@@ -136,7 +142,10 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
 
 std::string cfg_name(const LaunchCfg& g) {
   char buf[96];
-  if (g.kind == 4)
+  if (g.kind == 5)
+    std::snprintf(buf, sizeof(buf), "tensor cores (TF32 split), %d matrices x 128 threads, %d CTAs", g.shape,
+                  g.grid);
+  else if (g.kind == 4)
     std::snprintf(buf, sizeof(buf), "FP32 register %dx%d tiles x %d threads, %d CTAs",
                   gf::f32r_tile(g.shape, 0), gf::f32r_tile(g.shape, 1), g.threads, g.grid);
   else if (g.kind == 2)
@@ -217,8 +226,27 @@ gf_status choose_cfg(gf_ctx* c, int mode, int bucket, int nbmax, const gf::Point
   const size_t limit = (size_t)c->smem_optin - 1024;
   std::vector<LaunchCfg> cands;
   if (c->precision == GF_PREC_MIXED) {
+    // GF_KERNEL=tc or GF_KERNEL=f32r restricts the mixed candidates to one kernel family
+    const char* only = std::getenv("GF_KERNEL");
+    const bool use_tc = only && std::strcmp(only, "tc") == 0;
+    const bool use_f32r = !only || std::strcmp(only, "tc") != 0;
+    // N(mu) passes: the tensor-core elimination with 4 to 1 matrices per CTA
+    for (int ng = 4; use_tc && mode == gf::kOcc && ng >= 1; --ng) {
+      if (!gf::tc_fits(nbmax, ng)) continue;
+      LaunchCfg t;
+      t.kind = 5;
+      t.shape = ng;
+      t.nbmax = nbmax;
+      t.threads = 128 * ng;
+      t.smem = gf::point_tc_smem(nbmax, c->mmax, ng);
+      if (t.smem > limit) continue;
+      const int bps = gf::point_tc_blocks_per_sm(nbmax, ng, t.smem);
+      if (bps < 1) continue;
+      t.grid = c->sm_count * bps;
+      cands.push_back(t);
+    }
     // single-word FP32 register tiles for every shape that serves the window
-    for (int sh = 0; sh < gf::f32r_num_shapes(); ++sh) {
+    for (int sh = 0; use_f32r && sh < gf::f32r_num_shapes(); ++sh) {
       if (!gf::f32r_shape_fits(sh, nbmax)) continue;
       LaunchCfg f;
       f.kind = 4;
@@ -467,6 +495,8 @@ gf_status finish_occupation(gf_ctx* c, cudaStream_t s, double* n_out, double* dn
   c->ev_used = 0;
   int flags = 0;
   std::memcpy(&flags, c->hp_status(), sizeof(int));
+  if (flags & gf::kFlagTimeout)
+    return fail(c, GF_ETIMEOUT, "a bounded wait for the tensor cores gave up in the point kernel");
   if (flags & gf::kFlagSingular)
     return fail(c, GF_ESINGULAR, "zero or non-finite pivot in a (k, i w_n) inverse");
   for (int s2 = 0; s2 < c->n_sys; ++s2) {

@@ -14,6 +14,7 @@ namespace gf {
 
 constexpr int kThreads = 256;          // threads per CTA of every point kernel
 constexpr int kFlagSingular = 1;       // status bit: zero or non-finite pivot
+constexpr int kFlagTimeout = 2;        // status bit: a bounded wait on the tensor cores gave up
 
 // Work modes of the point kernels (bit set).
 enum Mode : int {
@@ -89,6 +90,8 @@ struct PointParams {
   const double* nbar;   // [n_sys] device, or null
   double* mubar_part;   // [n_k][n_chunks]
   int* status;
+  int tc_skip_mma;      // tensor-core kernel, failure-detection tests only: issue no MMA, so
+                        // the bounded wait for it runs out and the kernel reports kFlagTimeout
 };
 
 struct PInfo {          // pole form of one system's Sigma
@@ -308,6 +311,13 @@ bool f32r_shape_fits(int shape, int nbmax);
 int f32r_threads(int shape, int nbmax);
 size_t point_f32r_smem(int nbmax, int mmax, int mode);
 int point_f32r_blocks_per_sm(int shape, int threads, size_t smem);
+
+// Mixed-precision N(mu) kernel on the tcgen05 tensor cores (gf_tc.cu): ng matrix
+// groups of 128 threads per CTA, windows up to 128 bands.
+bool tc_fits(int nbmax, int ng);
+size_t point_tc_smem(int nbmax, int mmax, int ng);
+int point_tc_blocks_per_sm(int nbmax, int ng, size_t smem);
+cudaError_t launch_point_tc(int ng, const PointParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_point_f32r(int shape, const PointParams& p, int grid, int threads, size_t smem,
                               cudaStream_t s);
 // out[i] = complex FP32 rounding of in[i], for n complex numbers
