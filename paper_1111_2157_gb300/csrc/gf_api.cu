@@ -749,7 +749,7 @@ gf_status init_ctx(gf_ctx* c, const gf_desc* d) {
   // about 8 items per resident CTA.
   // groups share a window bucket; order by the window of their first k-point
   auto by_window = [&](const Item& a, const Item& b) { return c->nb[c->kperm[a.k]] > c->nb[c->kperm[b.k]]; };
-  c->kg = (int)std::max(1.0, std::min(16.0, std::floor((double)c->n_k * c->n_chunks / (8.0 * resident))));
+  c->kg = (int)std::max(1.0, std::min((double)gf::kMaxKGroup, std::floor((double)c->n_k * c->n_chunks / (8.0 * resident))));
   c->kperm.clear();
   c->group_k0.clear();
   c->group_nk.clear();

@@ -15,6 +15,7 @@ namespace gf {
 constexpr int kThreads = 256;          // threads per CTA of every point kernel
 constexpr int kFlagSingular = 1;       // status bit: zero or non-finite pivot
 constexpr int kFlagTimeout = 2;        // status bit: a bounded wait on the tensor cores gave up
+constexpr int kMaxKGroup = 16;         // k-points per k-group item (modes with a k-reduction)
 
 // Work modes of the point kernels (bit set).
 enum Mode : int {
