@@ -144,14 +144,23 @@ __host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
 __device__ __forceinline__ int item_k(const Item& it, const int* kperm, int q) {
   return kperm ? kperm[it.k + q] : it.k + q;
 }
-// slot of a k-group sum: the first k-point of the group writes, the later ones add (in k order)
+// slot of a k-group sum: the first k-point of the group writes, the later ones add (in k order).
+// The slot is stored and reloaded with an L2 evict-last policy: a CTA revisits its group's
+// slots one chunk of frequencies later, and the policy keeps them in L2 until then instead
+// of writing each visit back to HBM.
 __device__ __forceinline__ void gq_put(double2* out, int q, double2 v) {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   if (q) {
-    const double2 o = *out;
+    double2 o;
+    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(o.x), "=d"(o.y)
+                 : "l"(out), "l"(pol));
     v.x += o.x;
     v.y += o.y;
   }
-  *out = v;
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(out), "d"(v.x), "d"(v.y), "l"(pol)
+               : "memory");
 }
 
 // Thread t's share (of nthr threads) of Re Tr H_k + Re Tr(Sigma_inf P_k P_k^+), the trace
