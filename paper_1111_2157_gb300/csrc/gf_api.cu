@@ -101,7 +101,8 @@ gf_status check_ready(gf_ctx* c) {
 struct LaunchCfg {
   int kind = 0;        // 0 FP64, 1 FP32-pair shared-memory, 2 FP32-pair register-resident,
                        // 3 low-rank, 4 FP32 register-resident with refined projections,
-                       // 5 tensor-core (tcgen05) blocked elimination, N(mu) passes
+                       // 5 tensor-core (tcgen05) blocked elimination, N(mu) passes,
+                       // 6 one warp per matrix (windows <= 40), N(mu) passes
   int shape = -1;      // register tile shape (kinds 2 and 4); matrices per CTA (kind 5)
   int threads = gf::kThreads;
   size_t smem = 0;
@@ -128,7 +129,9 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
     GF_CU(gf::launch_point_lr(p, lr, grid, cfg.smem, c->stream));
     return GF_OK;
   }
-  if (cfg.kind == 5) {
+  if (cfg.kind == 6) {
+    GF_CU(gf::launch_point_w32(cfg.nbmax, p, grid, cfg.smem, c->stream));
+  } else if (cfg.kind == 5) {
     // GF_TC_TEST_SKIP_MMA=1 (failure-detection tests): the kernel's bounded waits run out
     const char* skip = std::getenv("GF_TC_TEST_SKIP_MMA");
     p.tc_skip_mma = (skip && std::atoi(skip) == 1) ? 1 : 0;
@@ -142,7 +145,9 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
 
 std::string cfg_name(const LaunchCfg& g) {
   char buf[96];
-  if (g.kind == 5)
+  if (g.kind == 6)
+    std::snprintf(buf, sizeof(buf), "FP32 one warp per matrix, %d threads, %d CTAs", g.threads, g.grid);
+  else if (g.kind == 5)
     std::snprintf(buf, sizeof(buf), "tensor cores (TF32 split), %d matrices x 128 threads, %d CTAs", g.shape,
                   g.grid);
   else if (g.kind == 4)
@@ -226,10 +231,12 @@ gf_status choose_cfg(gf_ctx* c, int mode, int bucket, int nbmax, const gf::Point
   const size_t limit = (size_t)c->smem_optin - 1024;
   std::vector<LaunchCfg> cands;
   if (c->precision == GF_PREC_MIXED) {
-    // GF_KERNEL=tc or GF_KERNEL=f32r restricts the mixed candidates to one kernel family
+    // GF_KERNEL restricts the mixed candidates to one kernel family: tc (tensor cores),
+    // w32 (one warp per matrix) or f32r (register tiles)
     const char* only = std::getenv("GF_KERNEL");
     const bool use_tc = only && std::strcmp(only, "tc") == 0;
-    const bool use_f32r = !only || std::strcmp(only, "tc") != 0;
+    const bool use_w32 = !only || std::strcmp(only, "w32") == 0;
+    const bool use_f32r = !only || std::strcmp(only, "f32r") == 0;
     // N(mu) passes: the tensor-core elimination with 4 to 1 matrices per CTA
     for (int ng = 4; use_tc && mode == gf::kOcc && ng >= 1; --ng) {
       if (!gf::tc_fits(nbmax, ng)) continue;
@@ -244,6 +251,17 @@ gf_status choose_cfg(gf_ctx* c, int mode, int bucket, int nbmax, const gf::Point
       if (bps < 1) continue;
       t.grid = c->sm_count * bps;
       cands.push_back(t);
+    }
+    // N(mu) passes of windows up to 40 bands: one warp per matrix
+    if (use_w32 && mode == gf::kOcc && gf::w32_nmax(nbmax) > 0) {
+      LaunchCfg w;
+      w.kind = 6;
+      w.nbmax = nbmax;
+      w.threads = gf::w32_threads();
+      w.smem = gf::point_w32_smem(nbmax, c->mmax);
+      const int bps = w.smem <= limit ? gf::point_w32_blocks_per_sm(nbmax, w.smem) : 0;
+      w.grid = c->sm_count * bps;
+      if (bps >= 1) cands.push_back(w);
     }
     // single-word FP32 register tiles for every shape that serves the window
     for (int sh = 0; use_f32r && sh < gf::f32r_num_shapes(); ++sh) {

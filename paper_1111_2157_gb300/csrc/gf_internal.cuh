@@ -322,6 +322,14 @@ int f32r_threads(int shape, int nbmax);
 size_t point_f32r_smem(int nbmax, int mmax, int mode);
 int point_f32r_blocks_per_sm(int shape, int threads, size_t smem);
 
+// Mixed-precision N(mu) kernel for windows up to 40 bands (gf_w32.cu): one warp per
+// matrix, the matrix in registers.
+int w32_nmax(int nbmax);
+int w32_threads();
+size_t point_w32_smem(int nbmax, int mmax);
+int point_w32_blocks_per_sm(int nbmax, size_t smem);
+cudaError_t launch_point_w32(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s);
+
 // Mixed-precision N(mu) kernel on the tcgen05 tensor cores (gf_tc.cu): ng matrix
 // groups of 128 threads per CTA, windows up to 128 bands.
 bool tc_fits(int nbmax, int ng);

@@ -1,0 +1,305 @@
+// Mixed-precision N(mu) pass for small windows (N_b <= 40): one warp per matrix,
+// the matrix in the warp's registers, no block barrier in the elimination.
+//
+// Per (k, i w_n) point, as the FP32 register kernel computes it (Eq. dmftloop1):
+// A = (i w_n + mu) I - H_k - P_k^+ (Sigma(i w_n) P_k) in FP32 (the diagonal formed in
+// FP64 and rounded once), X = A^{-1}, and Re Tr X, Re Tr X^2 summed over the item's
+// frequencies in FP64 (the N(mu) and dN/dmu partial sums).
+//
+// Lane l holds rows l and l + 32 (all N_b columns, NMAX complex registers per row).
+// Gauss-Jordan in exchange form with partial pivoting, every register index static
+// (each step rotates the rows by one column, so the pivot column is register 0), and
+// lazy row scaling: the stored matrix is the true one with each
+// former pivot row divided by its scale s_p.  Step j, pivot row p (unused, largest
+// |a_ij|), u = row p as stored (its scale is still 1), r = 1 / u_j:
+//   every other row i:  l_i = a_ij r;  a_ic -= l_i u_c (c != j);  a_ij = -l_i
+//   row p:              unchanged except a_pj = 1, and its scale becomes r
+// which is the sweep of the true matrix written in stored terms (a former pivot row
+// updates with its stored values, because its true l and its true entries carry the
+// same scale).  The row reaches the warp through a shared-memory buffer, the pivot
+// through a warp max-reduction; the true inverse is s_r a_rc at the end.
+#include <math.h>
+#include <stdint.h>
+
+#include "gf_complex.cuh"
+#include "gf_internal.cuh"
+
+namespace gf {
+
+namespace {
+
+using namespace cx;
+
+__device__ __forceinline__ float2 zero2() { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ unsigned pack_key_w(float2 v, int i) {
+  return (pivot_key_s(v) & ~127u) | (unsigned)(127 - i);
+}
+
+}  // namespace
+
+// Shared memory of k_point_w32 (bytes): per CTA P and H_ii of the item's k-point; per
+// warp Sigma, T = Sigma P (then the inverse for the traces), the diagonal, the pivot
+// row buffer and the pivot tables.
+struct LayoutW {
+  size_t oP, oHii, warp0, wstride, wS, wX, wD, wBuf, wPiv, bytes;
+};
+
+__host__ __device__ inline LayoutW make_layout_w(int nbmax, int mmax, int nmax, int nwarps) {
+  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  LayoutW L;
+  size_t o = 0;
+  L.oP = o; o = al(o + 8 * (size_t)mmax * nbmax);
+  L.oHii = o; o = al(o + 16 * (size_t)nbmax);
+  L.warp0 = o;
+  size_t g = 0;
+  const size_t ld = (size_t)(nbmax | 1);
+  size_t x = (size_t)mmax * nbmax;
+  if (x < (size_t)nbmax * ld) x = (size_t)nbmax * ld;
+  L.wS = g; g = al(g + 8 * (size_t)mmax * mmax);
+  L.wX = g; g = al(g + 8 * x);
+  L.wD = g; g = al(g + 8 * (size_t)nbmax);
+  L.wBuf = g; g = al(g + 8 * (size_t)nmax);
+  L.wPiv = g; g = al(g + 3 * sizeof(int) * (size_t)nmax);
+  L.wstride = g;
+  L.bytes = L.warp0 + (size_t)nwarps * g;
+  return L;
+}
+
+namespace {
+
+template <int NMAX, int ROWS, int W>
+__global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_item;
+  __shared__ double s_part[W][2];
+  const LayoutW L = make_layout_w(p.nbmax, p.mmax, NMAX, W);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  float2* sP = reinterpret_cast<float2*>(smraw + L.oP);
+  double2* sHii = reinterpret_cast<double2*>(smraw + L.oHii);
+  unsigned char* wb = smraw + L.warp0 + (size_t)wp * L.wstride;
+  float2* sS = reinterpret_cast<float2*>(wb + L.wS);
+  float2* sX = reinterpret_cast<float2*>(wb + L.wX);
+  float2* sD = reinterpret_cast<float2*>(wb + L.wD);
+  float2* sBuf = reinterpret_cast<float2*>(wb + L.wBuf);
+  int* sPiv = reinterpret_cast<int*>(wb + L.wPiv);
+  int* sIdx = sPiv + NMAX;
+  int* sRow = sIdx + NMAX;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1);
+    __syncthreads();
+    const int itx = s_item;
+    if (itx >= p.n_items) break;
+    const Item it = p.items[itx];
+    const int kk = item_k(it, p.kperm, 0);  // N(mu) items hold one k-point
+    const KInfo ki = p.kinfo[kk];
+    const SInfo si = p.sinfo[ki.sys];
+    const int N = ki.nb, M = si.m, ld = N | 1;
+    const float2* Hk = p.Hs + ki.offH;
+    const double2* Hk64 = p.H + ki.offH;
+    const double mu = p.mu[ki.sys];
+    const double pib = M_PI / si.beta;
+    for (int e = tid; e < M * N; e += 32 * W) sP[e] = p.Ps[ki.offP + e];
+    for (int x = tid; x < N; x += 32 * W) sHii[x] = Hk64[x * N + x];
+    __syncthreads();
+    double acc_tr = 0.0, acc_g2 = 0.0;
+
+    for (int n = it.n0 + wp; n < it.n1; n += W) {
+      const double wn = (2.0 * n + 1.0) * pib;
+      for (int e = lane; e < M * M; e += 32) sS[e] = p.Ss[si.offSig + (int64_t)n * M * M + e];
+      for (int x = lane; x < N; x += 32)
+        sD[x] = make_float2(__double2float_rn(mu - sHii[x].x), __double2float_rn(wn - sHii[x].y));
+      __syncwarp();
+      for (int e = lane; e < M * N; e += 32) {  // T = Sigma P (M x N)
+        const int a = e / N, j = e - a * N;
+        float2 acc = zero2();
+        for (int b = 0; b < M; ++b) fmac(acc, sS[a * M + b], sP[b * N + j]);
+        sX[e] = acc;
+      }
+      __syncwarp();
+      // A = diag - H - P^+ T, rows lane and lane + 32
+      float2 a[ROWS][NMAX];
+#pragma unroll
+      for (int s = 0; s < ROWS; ++s) {
+        const int r = lane + 32 * s;
+#pragma unroll
+        for (int c = 0; c < NMAX; ++c) {
+          float2 v = zero2();
+          if (r < N && c < N) {
+            const float2 h = Hk[r * N + c];
+            v = (r == c) ? sD[r] : make_float2(-h.x, -h.y);
+          }
+          a[s][c] = v;
+        }
+        if (r < N) {
+          for (int x = 0; x < M; ++x) {
+            const float2 pv = sP[x * N + r];
+            const float2 mp = make_float2(-pv.x, pv.y);  // -conj(P[x][r])
+#pragma unroll
+            for (int c = 0; c < NMAX; ++c)
+              if (c < N) fmac(a[s][c], mp, sX[x * N + c]);
+          }
+        }
+      }
+      // Gauss-Jordan, lazy row scales.  Each step rotates every row left by one column,
+      // so the pivot column is always register 0 and the loop body stays small; after
+      // step j the original column c sits at register (c - j - 1) mod NMAX.
+      bool used[ROWS];
+      float2 sc[ROWS];
+#pragma unroll
+      for (int s = 0; s < ROWS; ++s) {
+        used[s] = false;
+        sc[s] = make_float2(1.f, 0.f);
+      }
+#pragma unroll 1
+      for (int j = 0; j < N; ++j) {
+        unsigned key = 0u;
+#pragma unroll
+        for (int s = 0; s < ROWS; ++s) {
+          const int r = lane + 32 * s;
+          if (r < N && !used[s]) key = max(key, pack_key_w(a[s][0], r));
+        }
+        const unsigned best = __reduce_max_sync(0xffffffffu, key);
+        if (lane == 0 && ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u)) atomicOr(p.status, kFlagSingular);
+        const int prow = min(127 - (int)(best & 127u), N - 1);
+        const int pl = prow & 31, ps = prow >> 5;
+        if (lane == pl) {
+#pragma unroll
+          for (int s = 0; s < ROWS; ++s)
+            if (s == ps)
+#pragma unroll
+              for (int c = 0; c < NMAX; ++c) sBuf[c] = a[s][c];
+        }
+        __syncwarp();
+        const float2 r = frcp(sBuf[0]);
+        float2 lq[ROWS];
+        bool isp[ROWS];
+#pragma unroll
+        for (int s = 0; s < ROWS; ++s) {
+          isp[s] = (lane == pl) && (s == ps);
+          lq[s] = isp[s] ? zero2() : fmul(a[s][0], r);
+        }
+#pragma unroll
+        for (int c = 1; c < NMAX; ++c) {
+          const float2 uc = sBuf[c];
+#pragma unroll
+          for (int s = 0; s < ROWS; ++s) fsub_prod(a[s][c], lq[s], uc);
+        }
+#pragma unroll
+        for (int s = 0; s < ROWS; ++s) {
+          const float2 col = isp[s] ? make_float2(1.f, 0.f) : make_float2(-lq[s].x, -lq[s].y);
+#pragma unroll
+          for (int c = 0; c + 1 < NMAX; ++c) a[s][c] = a[s][c + 1];
+          a[s][NMAX - 1] = col;
+          if (isp[s]) {
+            used[s] = true;
+            sc[s] = r;
+          }
+        }
+        if (lane == 0) sPiv[j] = prow;
+        __syncwarp();  // the buffer is rewritten by the next pivot
+      }
+      // the inverse (true values s_r a_rc) for the traces: X[i][c] = B[p_i][q_c];
+      // register x holds the original column (x + N) mod NMAX
+#pragma unroll
+      for (int s = 0; s < ROWS; ++s) {
+        const int r = lane + 32 * s;
+        if (r < N)
+#pragma unroll
+          for (int x = 0; x < NMAX; ++x) {
+            int c = x + N;
+            if (c >= NMAX) c -= NMAX;
+            if (c < N) sX[r * ld + c] = fmul(sc[s], a[s][x]);
+          }
+      }
+      __syncwarp();
+      for (int j = lane; j < N; j += 32) sIdx[sPiv[j]] = j;
+      __syncwarp();
+      for (int x = lane; x < N; x += 32) sRow[x] = sPiv[x] * ld;
+      __syncwarp();
+      for (int x = lane; x < N; x += 32) acc_tr += (double)sX[sRow[x] + sIdx[x]].x;
+      float g2 = 0.f;
+      for (int e = lane; e < N * N; e += 32) {
+        const int i = e / N, c = e - i * N;
+        const float2 g1 = sX[sRow[i] + sIdx[c]], g3 = sX[sRow[c] + sIdx[i]];
+        g2 = __fmaf_rn(g1.x, g3.x, __fmaf_rn(-g1.y, g3.y, g2));
+      }
+      acc_g2 += (double)g2;
+      __syncwarp();  // sX and sS are rewritten by the next frequency
+    }
+    // deterministic: xor tree in each warp, then the warps in order
+    for (int off = 16; off; off >>= 1) {
+      acc_tr += __shfl_xor_sync(0xffffffffu, acc_tr, off);
+      acc_g2 += __shfl_xor_sync(0xffffffffu, acc_g2, off);
+    }
+    if (lane == 0) {
+      s_part[wp][0] = acc_tr;
+      s_part[wp][1] = acc_g2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0, u = 0.0;
+      for (int w = 0; w < W; ++w) {
+        t += s_part[w][0];
+        u += s_part[w][1];
+      }
+      double* o = p.occ_part + ((int64_t)kk * p.n_chunks + it.chunk) * 2;
+      o[0] = t;
+      o[1] = u;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int kW32Warps = 2;  // warps (matrices in flight) per CTA
+
+template <int NMAX, int ROWS>
+cudaError_t launch_w(const PointParams& p, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_point_w32<NMAX, ROWS, kW32Warps>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_point_w32<NMAX, ROWS, kW32Warps><<<grid, 32 * kW32Warps, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int NMAX, int ROWS>
+int bps_w(size_t smem) {
+  int nb = 0;
+  if (cudaFuncSetAttribute(k_point_w32<NMAX, ROWS, kW32Warps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_point_w32<NMAX, ROWS, kW32Warps>, 32 * kW32Warps,
+                                                    smem) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+}  // namespace
+
+// Largest window of the instantiation that serves nbmax, or 0.
+int w32_nmax(int nbmax) { return nbmax <= 16 ? 16 : (nbmax <= 40 ? 40 : 0); }
+
+int w32_threads() { return 32 * kW32Warps; }
+
+size_t point_w32_smem(int nbmax, int mmax) {
+  return make_layout_w(nbmax, mmax, w32_nmax(nbmax), kW32Warps).bytes;
+}
+
+int point_w32_blocks_per_sm(int nbmax, size_t smem) {
+  switch (w32_nmax(nbmax)) {
+    case 16: return bps_w<16, 1>(smem);
+    case 40: return bps_w<40, 2>(smem);
+    default: return 0;
+  }
+}
+
+cudaError_t launch_point_w32(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s) {
+  switch (w32_nmax(nbmax)) {
+    case 16: return launch_w<16, 1>(p, grid, smem, s);
+    case 40: return launch_w<40, 2>(p, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gf
