@@ -102,7 +102,8 @@ struct LaunchCfg {
   int kind = 0;        // 0 FP64, 1 FP32-pair shared-memory, 2 FP32-pair register-resident,
                        // 3 low-rank, 4 FP32 register-resident with refined projections,
                        // 5 tensor-core (tcgen05) blocked elimination, N(mu) passes,
-                       // 6 one warp per matrix (windows <= 40), N(mu) passes
+                       // 6 one warp per matrix (windows <= 40), 7 two or three warps per
+                       // matrix (windows 41-96): N(mu) passes
   int shape = -1;      // register tile shape (kinds 2 and 4); matrices per CTA (kind 5)
   int threads = gf::kThreads;
   size_t smem = 0;
@@ -129,7 +130,9 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
     GF_CU(gf::launch_point_lr(p, lr, grid, cfg.smem, c->stream));
     return GF_OK;
   }
-  if (cfg.kind == 6) {
+  if (cfg.kind == 7) {
+    GF_CU(gf::launch_point_wm(cfg.nbmax, p, grid, cfg.smem, c->stream));
+  } else if (cfg.kind == 6) {
     GF_CU(gf::launch_point_w32(cfg.nbmax, p, grid, cfg.smem, c->stream));
   } else if (cfg.kind == 5) {
     // GF_TC_TEST_SKIP_MMA=1 (failure-detection tests): the kernel's bounded waits run out
@@ -147,6 +150,8 @@ std::string cfg_name(const LaunchCfg& g) {
   char buf[96];
   if (g.kind == 6)
     std::snprintf(buf, sizeof(buf), "FP32 one warp per matrix, %d threads, %d CTAs", g.threads, g.grid);
+  else if (g.kind == 7)
+    std::snprintf(buf, sizeof(buf), "FP32 %d warps per matrix, %d CTAs", g.threads / 32, g.grid);
   else if (g.kind == 5)
     std::snprintf(buf, sizeof(buf), "tensor cores (TF32 split), %d matrices x 128 threads, %d CTAs", g.shape,
                   g.grid);
@@ -232,7 +237,7 @@ gf_status choose_cfg(gf_ctx* c, int mode, int bucket, int nbmax, const gf::Point
   std::vector<LaunchCfg> cands;
   if (c->precision == GF_PREC_MIXED) {
     // GF_KERNEL restricts the mixed candidates to one kernel family: tc (tensor cores),
-    // w32 (one warp per matrix) or f32r (register tiles)
+    // w32 (one to three warps per matrix) or f32r (register tiles)
     const char* only = std::getenv("GF_KERNEL");
     const bool use_tc = only && std::strcmp(only, "tc") == 0;
     const bool use_w32 = !only || std::strcmp(only, "w32") == 0;
@@ -260,6 +265,17 @@ gf_status choose_cfg(gf_ctx* c, int mode, int bucket, int nbmax, const gf::Point
       w.threads = gf::w32_threads();
       w.smem = gf::point_w32_smem(nbmax, c->mmax);
       const int bps = w.smem <= limit ? gf::point_w32_blocks_per_sm(nbmax, w.smem) : 0;
+      w.grid = c->sm_count * bps;
+      if (bps >= 1) cands.push_back(w);
+    }
+    // ... and of 41 to 96 bands: two or three warps per matrix, one row per lane
+    if (use_w32 && mode == gf::kOcc && gf::wm_nmax(nbmax) > 0) {
+      LaunchCfg w;
+      w.kind = 7;
+      w.nbmax = nbmax;
+      w.threads = gf::wm_threads(nbmax);
+      w.smem = gf::point_wm_smem(nbmax, c->mmax);
+      const int bps = w.smem <= limit ? gf::point_wm_blocks_per_sm(nbmax, w.smem) : 0;
       w.grid = c->sm_count * bps;
       if (bps >= 1) cands.push_back(w);
     }

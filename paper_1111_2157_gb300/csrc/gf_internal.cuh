@@ -329,6 +329,12 @@ int w32_threads();
 size_t point_w32_smem(int nbmax, int mmax);
 int point_w32_blocks_per_sm(int nbmax, size_t smem);
 cudaError_t launch_point_w32(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s);
+// ... and windows of 41 to 96 bands: 2 or 3 warps per matrix, one row per lane.
+int wm_nmax(int nbmax);
+int wm_threads(int nbmax);
+size_t point_wm_smem(int nbmax, int mmax);
+int point_wm_blocks_per_sm(int nbmax, size_t smem);
+cudaError_t launch_point_wm(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s);
 
 // Mixed-precision N(mu) kernel on the tcgen05 tensor cores (gf_tc.cu): ng matrix
 // groups of 128 threads per CTA, windows up to 128 bands.

@@ -66,6 +66,31 @@ __host__ __device__ inline LayoutW make_layout_w(int nbmax, int mmax, int nmax, 
   return L;
 }
 
+// Shared memory of k_point_wm (bytes): P and H_ii of the item's k-point, Sigma, T =
+// Sigma P (then the inverse for the traces), the diagonal, the double-buffered pivot
+// row stage of every warp and the pivot tables.
+struct LayoutM {
+  size_t oP, oHii, oS, oX, oD, oStage, oPiv, bytes;
+};
+
+__host__ __device__ inline LayoutM make_layout_m(int nbmax, int mmax, int nmax) {
+  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  LayoutM L;
+  const size_t ld = (size_t)(nbmax | 1);
+  size_t x = (size_t)mmax * nbmax;
+  if (x < (size_t)nbmax * ld) x = (size_t)nbmax * ld;
+  size_t o = 0;
+  L.oP = o; o = al(o + 8 * (size_t)mmax * nbmax);
+  L.oHii = o; o = al(o + 16 * (size_t)nbmax);
+  L.oS = o; o = al(o + 8 * (size_t)mmax * mmax);
+  L.oX = o; o = al(o + 8 * x);
+  L.oD = o; o = al(o + 8 * (size_t)nbmax);
+  L.oStage = o; o = al(o + 8 * 2 * (size_t)(nmax / 32) * nmax);
+  L.oPiv = o; o = al(o + 3 * sizeof(int) * (size_t)nmax);
+  L.bytes = o;
+  return L;
+}
+
 namespace {
 
 template <int NMAX, int ROWS, int W>
@@ -252,6 +277,192 @@ __global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
   }
 }
 
+// Windows of 41 to 96 bands: WPM warps per matrix, one row per lane (row 32 w + lane),
+// the same rotated exchange-form elimination with lazy row scales.  Per pivot every
+// warp's best unused row stages its values and key (double-buffered), one CTA barrier,
+// then every thread takes the group's winner from the stage.
+template <int NMAX, int WPM>
+__global__ void __launch_bounds__(32 * WPM) k_point_wm(const PointParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_item;
+  __shared__ unsigned s_key[2][4];
+  __shared__ double s_red[WPM];
+  const LayoutM L = make_layout_m(p.nbmax, p.mmax, NMAX);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int r = tid;  // this thread's row
+  float2* sP = reinterpret_cast<float2*>(smraw + L.oP);
+  double2* sHii = reinterpret_cast<double2*>(smraw + L.oHii);
+  float2* sS = reinterpret_cast<float2*>(smraw + L.oS);
+  float2* sX = reinterpret_cast<float2*>(smraw + L.oX);
+  float2* sD = reinterpret_cast<float2*>(smraw + L.oD);
+  float2* sStage = reinterpret_cast<float2*>(smraw + L.oStage);  // [2][WPM][NMAX]
+  int* sPiv = reinterpret_cast<int*>(smraw + L.oPiv);
+  int* sIdx = sPiv + NMAX;
+  int* sRow = sIdx + NMAX;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1);
+    __syncthreads();
+    const int itx = s_item;
+    if (itx >= p.n_items) break;
+    const Item it = p.items[itx];
+    const int kk = item_k(it, p.kperm, 0);  // N(mu) items hold one k-point
+    const KInfo ki = p.kinfo[kk];
+    const SInfo si = p.sinfo[ki.sys];
+    const int N = ki.nb, M = si.m, ld = N | 1;
+    const float2* Hk = p.Hs + ki.offH;
+    const double2* Hk64 = p.H + ki.offH;
+    const double mu = p.mu[ki.sys];
+    const double pib = M_PI / si.beta;
+    for (int e = tid; e < M * N; e += 32 * WPM) sP[e] = p.Ps[ki.offP + e];
+    for (int x = tid; x < N; x += 32 * WPM) sHii[x] = Hk64[x * N + x];
+    double acc_tr = 0.0, acc_g2 = 0.0;
+
+    for (int n = it.n0; n < it.n1; ++n) {
+      const double wn = (2.0 * n + 1.0) * pib;
+      __syncthreads();  // sP, sHii loaded; the previous frequency is done with sX, sS
+      for (int e = tid; e < M * M; e += 32 * WPM) sS[e] = p.Ss[si.offSig + (int64_t)n * M * M + e];
+      for (int x = tid; x < N; x += 32 * WPM)
+        sD[x] = make_float2(__double2float_rn(mu - sHii[x].x), __double2float_rn(wn - sHii[x].y));
+      __syncthreads();
+      for (int e = tid; e < M * N; e += 32 * WPM) {  // T = Sigma P (M x N)
+        const int a = e / N, j = e - a * N;
+        float2 acc = zero2();
+        for (int b = 0; b < M; ++b) fmac(acc, sS[a * M + b], sP[b * N + j]);
+        sX[e] = acc;
+      }
+      __syncthreads();
+      float2 a[NMAX];
+#pragma unroll
+      for (int c = 0; c < NMAX; ++c) {
+        float2 v = zero2();
+        if (r < N && c < N) {
+          const float2 h = Hk[r * N + c];
+          v = (r == c) ? sD[r] : make_float2(-h.x, -h.y);
+        }
+        a[c] = v;
+      }
+      if (r < N) {
+        for (int x = 0; x < M; ++x) {
+          const float2 pv = sP[x * N + r];
+          const float2 mp = make_float2(-pv.x, pv.y);  // -conj(P[x][r])
+#pragma unroll
+          for (int c = 0; c < NMAX; ++c)
+            if (c < N) fmac(a[c], mp, sX[x * N + c]);
+        }
+      }
+      bool used = false;
+      float2 sc = make_float2(1.f, 0.f);
+      int par = 0;
+#pragma unroll 1
+      for (int j = 0; j < N; ++j) {
+        const unsigned key = (r < N && !used) ? pack_key_w(a[0], r) : 0u;
+        const unsigned wk = __reduce_max_sync(0xffffffffu, key);
+        float2* stg = sStage + (par * WPM + wp) * NMAX;
+        if (wk != 0u && r == 127 - (int)(wk & 127u)) {
+#pragma unroll
+          for (int c = 0; c < NMAX; c += 2)
+            *reinterpret_cast<float4*>(stg + c) = make_float4(a[c].x, a[c].y, a[c + 1].x, a[c + 1].y);
+          s_key[par][wp] = wk;
+        } else if (wk == 0u && lane == 0) {
+          s_key[par][wp] = 0u;
+        }
+        __syncthreads();
+        unsigned best = s_key[par][0];
+        int qw = 0;
+#pragma unroll
+        for (int x = 1; x < WPM; ++x) {
+          const unsigned kx = s_key[par][x];
+          if (kx > best) {
+            best = kx;
+            qw = x;
+          }
+        }
+        const int prow = min(127 - (int)(best & 127u), N - 1);
+        if (tid == 0) {
+          if ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u) atomicOr(p.status, kFlagSingular);
+          sPiv[j] = prow;
+        }
+        const float2* u = sStage + (par * WPM + qw) * NMAX;
+        const float2 rc = frcp(u[0]);
+        const bool isp = (r == prow);
+        const float2 lq = isp ? zero2() : fmul(a[0], rc);
+#pragma unroll
+        for (int c = 1; c < NMAX; ++c) fsub_prod(a[c], lq, u[c]);
+        const float2 col = isp ? make_float2(1.f, 0.f) : make_float2(-lq.x, -lq.y);
+#pragma unroll
+        for (int c = 0; c + 1 < NMAX; ++c) a[c] = a[c + 1];
+        a[NMAX - 1] = col;
+        if (isp) {
+          used = true;
+          sc = rc;
+        }
+        par ^= 1;
+      }
+      __syncthreads();  // every thread is done with the stage and sX before the dump
+      if (r < N)
+#pragma unroll
+        for (int x = 0; x < NMAX; ++x) {
+          int c = x + N;
+          if (c >= NMAX) c -= NMAX;
+          if (c < N) sX[r * ld + c] = fmul(sc, a[x]);
+        }
+      for (int j = tid; j < N; j += 32 * WPM) sIdx[sPiv[j]] = j;
+      __syncthreads();
+      for (int x = tid; x < N; x += 32 * WPM) sRow[x] = sPiv[x] * ld;
+      __syncthreads();
+      for (int x = tid; x < N; x += 32 * WPM) acc_tr += (double)sX[sRow[x] + sIdx[x]].x;
+      float g2 = 0.f;
+      for (int e = tid; e < N * N; e += 32 * WPM) {
+        const int i = e / N, c = e - i * N;
+        const float2 g1 = sX[sRow[i] + sIdx[c]], g3 = sX[sRow[c] + sIdx[i]];
+        g2 = __fmaf_rn(g1.x, g3.x, __fmaf_rn(-g1.y, g3.y, g2));
+      }
+      acc_g2 += (double)g2;
+    }
+    // deterministic: xor tree in each warp, then the warps in order
+    for (int off = 16; off; off >>= 1) {
+      acc_tr += __shfl_xor_sync(0xffffffffu, acc_tr, off);
+      acc_g2 += __shfl_xor_sync(0xffffffffu, acc_g2, off);
+    }
+    __syncthreads();
+    if (lane == 0) s_red[wp] = acc_tr;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < WPM; ++w) t += s_red[w];
+    __syncthreads();
+    if (lane == 0) s_red[wp] = acc_g2;
+    __syncthreads();
+    if (tid == 0) {
+      double u2 = 0.0;
+      for (int w = 0; w < WPM; ++w) u2 += s_red[w];
+      double* o = p.occ_part + ((int64_t)kk * p.n_chunks + it.chunk) * 2;
+      o[0] = t;
+      o[1] = u2;
+    }
+    __syncthreads();
+  }
+}
+
+template <int NMAX, int WPM>
+cudaError_t launch_m(const PointParams& p, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_point_wm<NMAX, WPM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_point_wm<NMAX, WPM><<<grid, 32 * WPM, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int NMAX, int WPM>
+int bps_m(size_t smem) {
+  int nb = 0;
+  if (cudaFuncSetAttribute(k_point_wm<NMAX, WPM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_point_wm<NMAX, WPM>, 32 * WPM, smem) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
 constexpr int kW32Warps = 2;  // warps (matrices in flight) per CTA
 
 template <int NMAX, int ROWS>
@@ -279,6 +490,29 @@ int bps_w(size_t smem) {
 
 // Largest window of the instantiation that serves nbmax, or 0.
 int w32_nmax(int nbmax) { return nbmax <= 16 ? 16 : (nbmax <= 40 ? 40 : 0); }
+
+// Multi-warp form: windows of 41 to 96 bands, 2 or 3 warps per matrix.
+int wm_nmax(int nbmax) { return nbmax <= 40 ? 0 : (nbmax <= 64 ? 64 : (nbmax <= 96 ? 96 : 0)); }
+
+int wm_threads(int nbmax) { return wm_nmax(nbmax); }
+
+size_t point_wm_smem(int nbmax, int mmax) { return make_layout_m(nbmax, mmax, wm_nmax(nbmax)).bytes; }
+
+int point_wm_blocks_per_sm(int nbmax, size_t smem) {
+  switch (wm_nmax(nbmax)) {
+    case 64: return bps_m<64, 2>(smem);
+    case 96: return bps_m<96, 3>(smem);
+    default: return 0;
+  }
+}
+
+cudaError_t launch_point_wm(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s) {
+  switch (wm_nmax(nbmax)) {
+    case 64: return launch_m<64, 2>(p, grid, smem, s);
+    case 96: return launch_m<96, 3>(p, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 int w32_threads() { return 32 * kW32Warps; }
 

@@ -1,13 +1,14 @@
-"""N(mu) passes on the warp-per-matrix kernel (GF_KERNEL=w32, windows up to 40 bands)
-against the oracle.
+"""N(mu) passes on the warp-per-matrix kernels (GF_KERNEL=w32: one warp per matrix for
+windows up to 40 bands, two or three warps per matrix up to 96) against the oracle.
 
-One warp inverts one A = (i w_n + mu) I - H_k - P_k^+ Sigma P_k in FP32 with the matrix in
+One warp (or a few) inverts one A = (i w_n + mu) I - H_k - P_k^+ Sigma P_k in FP32 with the matrix in
 its registers (Gauss-Jordan in exchange form, rows rotated by one column per pivot, lazy
 row scales); the traces are summed in FP64.  It computes the same single-word FP32 inverse
 as the register-tile kernel, so the mixed path's contract tolerances hold: N within 1e-7 of
 the FP64 oracle (it reaches 1e-9 to 1e-8 here), dN/dmu within 1e-5.  Cases: windows of 1 to
 40 bands (one row per lane, two rows per lane, a window of exactly 40), ragged windows and
-several systems in one launch, the d-shell toy and a small Ce-like case.
+several systems in one launch, the d-shell toy and small Ce-like and NiO-like cases, and
+windows of 41 to 96 bands on two or three warps.
 """
 import numpy as np
 import pytest
@@ -36,12 +37,29 @@ def ragged_systems():
     return systems
 
 
+def ragged_wide_systems():
+    rng = synth.rng_for(77)
+    systems = []
+    for sidx, (m, nbs) in enumerate([(3, [41, 64, 50]), (5, [65, 96, 70, 90]), (2, [44, 88])]):
+        H = [synth.hamiltonian_dense(rng, 1, n, -4, 4, 0.3)[0] for n in nbs]
+        P = [(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))) / np.sqrt(n) for n in nbs]
+        pole = synth.sigma_two_pole(rng, m, 3.0)
+        systems.append(synth.System(H, P, pole, pole.sample(8.0 + 4 * sidx, 40), 8.0 + 4 * sidx, 1.0))
+    return systems
+
+
 CASES = {
     "d_toy": (lambda: [synth.d_toy().systems[0]], [0.3]),
     "ce_like_small": (lambda: [synth.ce_like(nk=5, n_iw=48).systems[0]], [0.1]),
     "window_13": (lambda: [synth.random_system(5, 4, 13, 3, 32, 10.0)], [0.05]),
     "window_40_two_orbitals": (lambda: [synth.random_system(9, 3, 40, 2, 20, 12.0)], [-0.3]),
     "ragged_three_systems": (ragged_systems, [0.2, -0.4, 1.1]),
+    # two or three warps per matrix (windows of 41 to 96 bands)
+    "nio_like_small": (lambda: [synth.nio_like(nk=3, n_iw=40).systems[0]], [0.2]),
+    "window_57": (lambda: [synth.random_system(4, 3, 57, 6, 24, 15.0)], [-0.2]),
+    "window_64": (lambda: [synth.random_system(3, 3, 64, 10, 24, 15.0)], [0.1]),
+    "window_96": (lambda: [synth.random_system(5, 2, 96, 12, 24, 20.0)], [0.3]),
+    "ragged_41_to_96": (ragged_wide_systems, [0.2, -0.4, 1.1]),
 }
 
 
