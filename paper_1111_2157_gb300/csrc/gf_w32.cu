@@ -6,9 +6,13 @@
 // FP64 and rounded once), X = A^{-1}, and Re Tr X, Re Tr X^2 summed over the item's
 // frequencies in FP64 (the N(mu) and dN/dmu partial sums).
 //
-// Lane l holds rows l and l + 32 (all N_b columns, NMAX complex registers per row).
+// Lane l holds row l (all N_b columns, NMAX complex registers).  Windows of 33 to 40
+// bands add rows 32 to 39, each split over a group of four lanes: lane l holds columns
+// 10 (l mod 4) to 10 (l mod 4) + 9 of row 32 + l / 4, so every lane updates 50 entries
+// per pivot instead of the 80 of two whole rows a lane.
 // Gauss-Jordan in exchange form with partial pivoting, every register index static
-// (each step rotates the rows by one column, so the pivot column is register 0), and
+// (each step rotates the rows by one column, so the pivot column is register 0; a split
+// row rotates across its four lanes with one shuffle), and
 // lazy row scaling: the stored matrix is the true one with each
 // former pivot row divided by its scale s_p.  Step j, pivot row p (unused, largest
 // |a_ij|), u = row p as stored (its scale is still 1), r = 1 / u_j:
@@ -93,13 +97,22 @@ __host__ __device__ inline LayoutM make_layout_m(int nbmax, int mmax, int nmax) 
 
 namespace {
 
-template <int NMAX, int ROWS, int W>
-__global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
+// 2-warp CTAs resident per SM that the register budget must allow (168 registers a
+// thread); shared memory allows six for a 40-band window with 14 orbitals.
+constexpr int kW32MinBlocks = 6;
+
+template <int NMAX, int ROWS, int W, bool SPLIT>
+__global__ void __launch_bounds__(32 * W, kW32MinBlocks) k_point_w32(const PointParams p) {
+  static_assert(!SPLIT || (ROWS == 1 && NMAX == 40), "split rows: one whole row a lane, 40 columns");
+  constexpr int SEG = NMAX / 4;  // columns of a split row on one lane
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_item;
   __shared__ double s_part[W][2];
   const LayoutW L = make_layout_w(p.nbmax, p.mmax, NMAX, W);
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  // split row of this lane: row 32 + lane / 4, columns c1 .. c1 + SEG - 1 (register order)
+  const int g = lane & 3, r1 = 32 + (lane >> 2), c1 = SEG * g;
+  const int lead = lane & ~3, nxt = lead | ((lane + 1) & 3);
   float2* sP = reinterpret_cast<float2*>(smraw + L.oP);
   double2* sHii = reinterpret_cast<double2*>(smraw + L.oHii);
   unsigned char* wb = smraw + L.warp0 + (size_t)wp * L.wstride;
@@ -143,8 +156,9 @@ __global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
         sX[e] = acc;
       }
       __syncwarp();
-      // A = diag - H - P^+ T, rows lane and lane + 32
+      // A = diag - H - P^+ T: rows lane (and lane + 32), the split row's segment
       float2 a[ROWS][NMAX];
+      float2 a1[SPLIT ? SEG : 1];
 #pragma unroll
       for (int s = 0; s < ROWS; ++s) {
         const int r = lane + 32 * s;
@@ -167,11 +181,32 @@ __global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
           }
         }
       }
+      if constexpr (SPLIT) {
+#pragma unroll
+        for (int y = 0; y < SEG; ++y) {
+          const int c = c1 + y;
+          float2 v = zero2();
+          if (r1 < N && c < N) {
+            const float2 h = Hk[r1 * N + c];
+            v = (r1 == c) ? sD[r1] : make_float2(-h.x, -h.y);
+          }
+          a1[y] = v;
+        }
+        if (r1 < N) {
+          for (int x = 0; x < M; ++x) {
+            const float2 pv = sP[x * N + r1];
+            const float2 mp = make_float2(-pv.x, pv.y);
+#pragma unroll
+            for (int y = 0; y < SEG; ++y)
+              if (c1 + y < N) fmac(a1[y], mp, sX[x * N + c1 + y]);
+          }
+        }
+      }
       // Gauss-Jordan, lazy row scales.  Each step rotates every row left by one column,
       // so the pivot column is always register 0 and the loop body stays small; after
       // step j the original column c sits at register (c - j - 1) mod NMAX.
-      bool used[ROWS];
-      float2 sc[ROWS];
+      bool used[ROWS], used1 = false;
+      float2 sc[ROWS], sc1 = make_float2(1.f, 0.f);
 #pragma unroll
       for (int s = 0; s < ROWS; ++s) {
         used[s] = false;
@@ -185,6 +220,9 @@ __global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
           const int r = lane + 32 * s;
           if (r < N && !used[s]) key = max(key, pack_key_w(a[s][0], r));
         }
+        // a split row's pivot-column entry sits on the first lane of its group
+        if constexpr (SPLIT)
+          if (g == 0 && r1 < N && !used1) key = max(key, pack_key_w(a1[0], r1));
         const unsigned best = __reduce_max_sync(0xffffffffu, key);
         if (lane == 0 && ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u)) atomicOr(p.status, kFlagSingular);
         const int prow = min(127 - (int)(best & 127u), N - 1);
@@ -196,6 +234,10 @@ __global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
 #pragma unroll
               for (int c = 0; c < NMAX; ++c) sBuf[c] = a[s][c];
         }
+        if constexpr (SPLIT)
+          if (r1 == prow)
+#pragma unroll
+            for (int y = 0; y < SEG; ++y) sBuf[c1 + y] = a1[y];
         __syncwarp();
         const float2 r = frcp(sBuf[0]);
         float2 lq[ROWS];
@@ -222,6 +264,26 @@ __global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
             sc[s] = r;
           }
         }
+        if constexpr (SPLIT) {
+          // the split row: l from its first lane; every entry updated (the pivot
+          // column's is replaced below), then the row rotates left across the group
+          const float2 h1 = make_float2(__shfl_sync(0xffffffffu, a1[0].x, lead),
+                                        __shfl_sync(0xffffffffu, a1[0].y, lead));
+          const bool isp1 = (r1 == prow);
+          const float2 lq1 = isp1 ? zero2() : fmul(h1, r);
+#pragma unroll
+          for (int y = 0; y < SEG; ++y) fsub_prod(a1[y], lq1, sBuf[c1 + y]);
+          if (g == 0) a1[0] = isp1 ? make_float2(1.f, 0.f) : make_float2(-lq1.x, -lq1.y);
+          const float2 t = make_float2(__shfl_sync(0xffffffffu, a1[0].x, nxt),
+                                       __shfl_sync(0xffffffffu, a1[0].y, nxt));
+#pragma unroll
+          for (int y = 0; y + 1 < SEG; ++y) a1[y] = a1[y + 1];
+          a1[SEG - 1] = t;
+          if (isp1) {
+            used1 = true;
+            sc1 = r;
+          }
+        }
         if (lane == 0) sPiv[j] = prow;
         __syncwarp();  // the buffer is rewritten by the next pivot
       }
@@ -238,6 +300,14 @@ __global__ void __launch_bounds__(32 * W) k_point_w32(const PointParams p) {
             if (c < N) sX[r * ld + c] = fmul(sc[s], a[s][x]);
           }
       }
+      if constexpr (SPLIT)
+        if (r1 < N)
+#pragma unroll
+          for (int y = 0; y < SEG; ++y) {
+            int c = c1 + y + N;
+            if (c >= NMAX) c -= NMAX;
+            if (c < N) sX[r1 * ld + c] = fmul(sc1, a1[y]);
+          }
       __syncwarp();
       for (int j = lane; j < N; j += 32) sIdx[sPiv[j]] = j;
       __syncwarp();
@@ -465,23 +535,31 @@ int bps_m(size_t smem) {
 
 constexpr int kW32Warps = 2;  // warps (matrices in flight) per CTA
 
-template <int NMAX, int ROWS>
-cudaError_t launch_w(const PointParams& p, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_point_w32<NMAX, ROWS, kW32Warps>,
+// Dynamic shared memory of the launch, and the largest carveout: six 2-warp CTAs of a
+// 40-band window (36 KB each) fill an SM only with the whole 228 KB as shared memory.
+template <int NMAX, int ROWS, bool SPLIT>
+cudaError_t set_attrs_w(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_point_w32<NMAX, ROWS, kW32Warps, SPLIT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_point_w32<NMAX, ROWS, kW32Warps><<<grid, 32 * kW32Warps, smem, s>>>(p);
+  return cudaFuncSetAttribute(k_point_w32<NMAX, ROWS, kW32Warps, SPLIT>,
+                              cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <int NMAX, int ROWS, bool SPLIT>
+cudaError_t launch_w(const PointParams& p, int grid, size_t smem, cudaStream_t s) {
+  const cudaError_t e = set_attrs_w<NMAX, ROWS, SPLIT>(smem);
+  if (e != cudaSuccess) return e;
+  k_point_w32<NMAX, ROWS, kW32Warps, SPLIT><<<grid, 32 * kW32Warps, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int NMAX, int ROWS>
+template <int NMAX, int ROWS, bool SPLIT>
 int bps_w(size_t smem) {
   int nb = 0;
-  if (cudaFuncSetAttribute(k_point_w32<NMAX, ROWS, kW32Warps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_point_w32<NMAX, ROWS, kW32Warps>, 32 * kW32Warps,
-                                                    smem) != cudaSuccess)
+  if (set_attrs_w<NMAX, ROWS, SPLIT>(smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_point_w32<NMAX, ROWS, kW32Warps, SPLIT>,
+                                                    32 * kW32Warps, smem) != cudaSuccess)
     return 0;
   return nb;
 }
@@ -489,7 +567,7 @@ int bps_w(size_t smem) {
 }  // namespace
 
 // Largest window of the instantiation that serves nbmax, or 0.
-int w32_nmax(int nbmax) { return nbmax <= 16 ? 16 : (nbmax <= 40 ? 40 : 0); }
+int w32_nmax(int nbmax) { return nbmax <= 16 ? 16 : (nbmax <= 32 ? 32 : (nbmax <= 40 ? 40 : 0)); }
 
 // Multi-warp form: windows of 41 to 96 bands, 2 or 3 warps per matrix.
 int wm_nmax(int nbmax) { return nbmax <= 40 ? 0 : (nbmax <= 64 ? 64 : (nbmax <= 96 ? 96 : 0)); }
@@ -522,16 +600,18 @@ size_t point_w32_smem(int nbmax, int mmax) {
 
 int point_w32_blocks_per_sm(int nbmax, size_t smem) {
   switch (w32_nmax(nbmax)) {
-    case 16: return bps_w<16, 1>(smem);
-    case 40: return bps_w<40, 2>(smem);
+    case 16: return bps_w<16, 1, false>(smem);
+    case 32: return bps_w<32, 1, false>(smem);
+    case 40: return bps_w<40, 1, true>(smem);
     default: return 0;
   }
 }
 
 cudaError_t launch_point_w32(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s) {
   switch (w32_nmax(nbmax)) {
-    case 16: return launch_w<16, 1>(p, grid, smem, s);
-    case 40: return launch_w<40, 2>(p, grid, smem, s);
+    case 16: return launch_w<16, 1, false>(p, grid, smem, s);
+    case 32: return launch_w<32, 1, false>(p, grid, smem, s);
+    case 40: return launch_w<40, 1, true>(p, grid, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -3,10 +3,12 @@ windows up to 40 bands, two or three warps per matrix up to 96) against the orac
 
 One warp (or a few) inverts one A = (i w_n + mu) I - H_k - P_k^+ Sigma P_k in FP32 with the matrix in
 its registers (Gauss-Jordan in exchange form, rows rotated by one column per pivot, lazy
-row scales); the traces are summed in FP64.  It computes the same single-word FP32 inverse
+row scales; rows 32 to 39 of a 33- to 40-band window split over four lanes each); the
+traces are summed in FP64.  It computes the same single-word FP32 inverse
 as the register-tile kernel, so the mixed path's contract tolerances hold: N within 1e-7 of
 the FP64 oracle (it reaches 1e-9 to 1e-8 here), dN/dmu within 1e-5.  Cases: windows of 1 to
-40 bands (one row per lane, two rows per lane, a window of exactly 40), ragged windows and
+40 bands (one row per lane for 16- and 32-column instances, split rows from 33 bands on, a
+window of exactly 40), ragged windows and
 several systems in one launch, the d-shell toy and small Ce-like and NiO-like cases, and
 windows of 41 to 96 bands on two or three warps.
 """
@@ -52,6 +54,8 @@ CASES = {
     "d_toy": (lambda: [synth.d_toy().systems[0]], [0.3]),
     "ce_like_small": (lambda: [synth.ce_like(nk=5, n_iw=48).systems[0]], [0.1]),
     "window_13": (lambda: [synth.random_system(5, 4, 13, 3, 32, 10.0)], [0.05]),
+    "window_29": (lambda: [synth.random_system(6, 3, 29, 5, 24, 10.0)], [0.15]),
+    "window_35_split_rows": (lambda: [synth.random_system(8, 3, 35, 4, 24, 10.0)], [-0.1]),
     "window_40_two_orbitals": (lambda: [synth.random_system(9, 3, 40, 2, 20, 12.0)], [-0.3]),
     "ragged_three_systems": (ragged_systems, [0.2, -0.4, 1.1]),
     # two or three warps per matrix (windows of 41 to 96 bands)
