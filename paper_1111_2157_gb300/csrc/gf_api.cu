@@ -103,7 +103,8 @@ struct LaunchCfg {
                        // 3 low-rank, 4 FP32 register-resident with refined projections,
                        // 5 tensor-core (tcgen05) blocked elimination, N(mu) passes,
                        // 6 one warp per matrix (windows <= 40), 7 two or three warps per
-                       // matrix (windows 41-96): N(mu) passes
+                       // matrix (windows 41-96): N(mu) passes; 8 one warp per matrix and
+                       // the CTA's refined projections: fused passes, windows <= 40
   int shape = -1;      // register tile shape (kinds 2 and 4); matrices per CTA (kind 5)
   int threads = gf::kThreads;
   size_t smem = 0;
@@ -130,7 +131,9 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
     GF_CU(gf::launch_point_lr(p, lr, grid, cfg.smem, c->stream));
     return GF_OK;
   }
-  if (cfg.kind == 7) {
+  if (cfg.kind == 8) {
+    GF_CU(gf::launch_point_f32w(cfg.nbmax, p, grid, cfg.smem, c->stream));
+  } else if (cfg.kind == 7) {
     GF_CU(gf::launch_point_wm(cfg.nbmax, p, grid, cfg.smem, c->stream));
   } else if (cfg.kind == 6) {
     GF_CU(gf::launch_point_w32(cfg.nbmax, p, grid, cfg.smem, c->stream));
@@ -148,7 +151,10 @@ gf_status launch_cfg(gf_ctx* c, const LaunchCfg& cfg, gf::PointParams p, int n_i
 
 std::string cfg_name(const LaunchCfg& g) {
   char buf[96];
-  if (g.kind == 6)
+  if (g.kind == 8)
+    std::snprintf(buf, sizeof(buf), "FP32 one warp per matrix + CTA projections, %d threads, %d CTAs", g.threads,
+                  g.grid);
+  else if (g.kind == 6)
     std::snprintf(buf, sizeof(buf), "FP32 one warp per matrix, %d threads, %d CTAs", g.threads, g.grid);
   else if (g.kind == 7)
     std::snprintf(buf, sizeof(buf), "FP32 %d warps per matrix, %d CTAs", g.threads / 32, g.grid);
@@ -183,6 +189,8 @@ gf_status autotune(gf_ctx* c, int key, const std::vector<LaunchCfg>& cands, gf::
   if (cands.size() == 1 || (env && std::atoi(env) == 0)) {
     c->tuned[key] = (int)cands.size() - 1;
     *out = cands.back();
+    c->tune_log += "mode " + std::to_string(key >> 3) + ", windows <= " + std::to_string(cands[0].nbmax) + ": " +
+                   cfg_name(cands.back()) + (cands.size() == 1 ? " (only candidate); " : " (not timed); ");
     return GF_OK;
   }
   // the sample: one item per CTA of the largest candidate grid; a second run of a
@@ -265,6 +273,17 @@ gf_status choose_cfg(gf_ctx* c, int mode, int bucket, int nbmax, const gf::Point
       w.threads = gf::w32_threads();
       w.smem = gf::point_w32_smem(nbmax, c->mmax);
       const int bps = w.smem <= limit ? gf::point_w32_blocks_per_sm(nbmax, w.smem) : 0;
+      w.grid = c->sm_count * bps;
+      if (bps >= 1) cands.push_back(w);
+    }
+    // fused passes of windows up to 40 bands: one warp per matrix, the CTA's epilogues
+    if (use_w32 && mode != gf::kOcc && gf::f32w_nmax(nbmax) > 0) {
+      LaunchCfg w;
+      w.kind = 8;
+      w.nbmax = nbmax;
+      w.threads = gf::f32w_threads();
+      w.smem = gf::point_f32w_smem(nbmax, c->mmax, mode);
+      const int bps = w.smem <= limit ? gf::point_f32w_blocks_per_sm(nbmax, w.smem) : 0;
       w.grid = c->sm_count * bps;
       if (bps >= 1) cands.push_back(w);
     }

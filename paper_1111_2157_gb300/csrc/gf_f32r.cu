@@ -36,6 +36,7 @@
 
 #include "gf_complex.cuh"
 #include "gf_internal.cuh"
+#include "gf_warp_gj.cuh"
 
 namespace gf {
 
@@ -255,6 +256,173 @@ __host__ __device__ inline LayoutF make_layout_f(int nbmax, int mmax, int mode) 
 
 namespace {
 
+// Buffers of the refined-projection epilogues in shared memory (LayoutF).
+struct EpiF {
+  const float2* sP;                                // P_k in FP32 (M x N)
+  float4 *sW, *sV, *sQa, *sQb, *sMt, *sPart;       // pairs
+  float2 *sY0, *sR, *sdY, *sZ0, *sdZ;              // FP32
+};
+
+// The kRho, kGloc and kAdj epilogues of frequency n of k-point ki (slot q of the item's
+// k-group), the inverse given as X[i][c] = sG[sRow[i] + sIdx[c]]; kRho adds X to the
+// item's S_k, kGloc and kAdj refine G P^+ (and P G) once with an FP32-pair residual and
+// store the k-group slot.  Every thread of the CTA runs it; consecutive products are
+// separated by CTA barriers; the caller puts a barrier before (the inverse visible to
+// all) and after (the buffers free).
+__device__ __forceinline__ void f32r_epilogues(const PointParams& p, const EpiF& eb, const Item& it,
+                                               const KInfo& ki, const SInfo& si, int q, int N, int M, int n,
+                                               double wn, double mu, double beta, double wk, double nbar,
+                                               const float4* Hkp, const float4* Pkp, const float2* sG,
+                                               const int* sRow, const int* sIdx, double& acc_mu) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const float2* sP = eb.sP;
+  float4 *sW = eb.sW, *sV = eb.sV, *sQa = eb.sQa, *sQb = eb.sQb, *sMt = eb.sMt, *sPart = eb.sPart;
+  float2 *sY0 = eb.sY0, *sR = eb.sR, *sdY = eb.sdY, *sZ0 = eb.sZ0, *sdZ = eb.sdZ;
+  if (p.mode & kRho) {
+    double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
+    const bool first = (n == it.n0);
+    for (int e = tid; e < N * N; e += nthr) {
+      const int i = e / N, c = e - i * N;
+      const float2 g = sG[sRow[i] + sIdx[c]];
+      if (first) {
+        S[e] = make_double2((double)g.x, (double)g.y);
+      } else {
+        double2 s = S[e];
+        s.x += (double)g.x;
+        s.y += (double)g.y;
+        S[e] = s;
+      }
+    }
+  }
+  if (p.mode & (kGloc | kAdj)) {
+    const bool adj = (p.mode & kAdj) != 0;
+    cf zw;  // -(i w_n + mu) as a pair
+    split(-mu, zw.rh, zw.rl);
+    split(-wn, zw.ih, zw.il);
+    const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
+    auto X = [&](int i, int c) { return sG[sRow[i] + sIdx[c]]; };
+    // Y0 = X P^+ (N x M)
+    mm_f32(N, M, N, X, [&](int c, int b) { return fconj(sP[b * N + c]); },
+           [&](int i, int b, float2 v) { sY0[i * M + b] = v; });
+    // Z0 = P X (M x N)
+    if (adj)
+      mm_f32(M, N, N, [&](int a, int i) { return sP[a * N + i]; }, X,
+             [&](int a, int c, float2 v) { sZ0[a * N + c] = v; });
+    __syncthreads();
+    // W = P Y0 (pairs; the sum over bands split in S parts, partials in the R region)
+    const int S = max(1, min(4, N / M));
+    mm_pair(M, M, N, S, sPart, [&](int a, int i) { return ld4(Pkp[a * N + i]); },
+            [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
+            [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
+    __syncthreads();
+    // V = Sigma W (pairs)
+    mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(Sgp[a * M + x]); },
+            [&](int x, int b) { return ld4(sW[x * M + b]); }, [&](int, int) { return czero(); },
+            [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
+    __syncthreads();
+    // R = P^+ - A Y0 = P^+ - (i w + mu) Y0 + H Y0 + P^+ V  (pairs, rounded to FP32)
+    mm_pair(N, M, N, 1, sPart, [&](int i, int c) { return ld4(Hkp[i * N + c]); },
+            [&](int c, int b) { return sY0[c * M + b]; },
+            [&](int i, int b) {
+              cf acc = conj_cf(ld4(Pkp[b * N + i]));
+              cacc1(acc, zw, sY0[i * M + b]);
+              for (int a = 0; a < M; ++a) cacc_ca(acc, ld4(Pkp[a * N + i]), ld4(sV[a * M + b]));
+              return acc;
+            },
+            [&](int i, int b, const cf& v) { sR[i * M + b] = round_cf(v); });
+    __syncthreads();
+    // dY = X R (FP32);  Y = Y0 + dY
+    mm_f32(N, M, N, X, [&](int c, int b) { return sR[c * M + b]; },
+           [&](int i, int b, float2 v) { sdY[i * M + b] = v; });
+    __syncthreads();
+    // P Y = W + P dY (the second term in FP32)
+    if (p.mode & kGloc) {
+      double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+      mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
+             [&](int i, int b) { return sdY[i * M + b]; },
+             [&](int a, int b, float2 d) {
+               const double2 w = to_d2(ld4(sW[a * M + b]));
+               gq_put(&out[a * M + b], q, make_double2(wk * (w.x + (double)d.x), wk * (w.y + (double)d.y)));
+             });
+    }
+    if (adj) {
+      // A_k = P Y in pairs
+      mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
+             [&](int i, int b) { return sdY[i * M + b]; },
+             [&](int a, int b, float2 d) {
+               cf q = ld4(sW[a * M + b]);
+               add_single(q, d);
+               sQa[a * M + b] = st4(q);
+             });
+      __syncthreads();
+      // W' = Z0 P^+ (pairs), then V' = W' Sigma
+      mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+              [&](int i, int b) { return conj_cf(ld4(Pkp[b * N + i])); }, [&](int, int) { return czero(); },
+              [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
+      __syncthreads();
+      mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(sW[a * M + x]); },
+              [&](int x, int b) { return ld4(Sgp[x * M + b]); }, [&](int, int) { return czero(); },
+              [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
+      __syncthreads();
+      // R' = P - Z0 A = P - (i w + mu) Z0 + Z0 H + V' P  (pairs, rounded), M x N
+      mm_pair(M, N, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+              [&](int i, int c) { return ld4(Hkp[i * N + c]); },
+              [&](int a, int c) {
+                cf acc = ld4(Pkp[a * N + c]);
+                cacc1(acc, zw, sZ0[a * N + c]);
+                for (int b = 0; b < M; ++b) cacc(acc, ld4(sV[a * M + b]), ld4(Pkp[b * N + c]));
+                return acc;
+              },
+              [&](int a, int c, const cf& v) { sR[a * N + c] = round_cf(v); });
+      __syncthreads();
+      // dZ = R' X (FP32)
+      mm_f32(M, N, N, [&](int a, int i) { return sR[a * N + i]; }, X,
+             [&](int a, int c, float2 v) { sdZ[a * N + c] = v; });
+      __syncthreads();
+      // B_k = Z Y = Z0 Y0 (pairs of exact FP32 products) + Z0 dY + dZ Y0 (FP32)
+      mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
+              [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
+              [&](int a, int b, const cf& v) { sQb[a * M + b] = st4(v); });
+      __syncthreads();
+      mm_f32(M, M, 2 * N,
+             [&](int a, int k) { return k < N ? sZ0[a * N + k] : sdZ[a * N + k - N]; },
+             [&](int k, int b) { return k < N ? sdY[k * M + b] : sY0[(k - N) * M + b]; },
+             [&](int a, int b, float2 d) {
+               cf q = ld4(sQb[a * M + b]);
+               add_single(q, d);
+               sQb[a * M + b] = st4(q);
+             });
+      __syncthreads();
+      const bool have_gbar = (p.Gbd != nullptr);
+      if (have_gbar) {
+        const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
+        // Mt = Gbar A_k^+ (pairs)
+        mm_pair(M, M, M, 1, sPart, [&](int a, int c) { return ld4(Gb[a * M + c]); },
+                [&](int c, int b) { return conj_cf(ld4(sQa[b * M + c])); }, [&](int, int) { return czero(); },
+                [&](int a, int b, const cf& v) { sMt[a * M + b] = st4(v); });
+        // mu_bar partial: - w_k Re<Gbar, B_k>
+        for (int e = tid; e < M * M; e += nthr) {
+          const double2 gv = to_d2(ld4(Gb[e])), bv = to_d2(ld4(sQb[e]));
+          acc_mu -= wk * fma(gv.x, bv.x, gv.y * bv.y);
+        }
+        __syncthreads();
+      }
+      double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
+      const double cb = nbar * 2.0 / beta;
+      for (int e = tid; e < M * M; e += nthr) {
+        const int a = e / M, b = e - a * M;
+        cf acc = czero();
+        if (have_gbar)
+          for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sMt[c * M + b]));
+        cnorm(acc);
+        const double2 v = to_d2(acc);
+        const double2 bt = to_d2(ld4(sQb[b * M + a]));
+        gq_put(&out[e], q, make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y)));
+      }
+    }
+  }
+}
+
 template <int RA, int RB, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_point_f32r(const PointParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -285,6 +453,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_f32r(const PointParams p) 
   int* sIdx = sPiv + p.nbmax;
   int* sRow = sIdx + p.nbmax;
   const int nbp = f32r_nbp(p.nbmax);
+  const EpiF eb{sP, sW, sV, sQa, sQb, sMt, sPart, sY0, sR, sdY, sZ0, sdZ};
   float2* bCol = sB;
   float2* bU = sB + 2 * nbp;
   float2* bCx = sB + 4 * nbp;
@@ -528,149 +697,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_point_f32r(const PointParams p) 
           }
           acc_g2 += (double)g2;
         }
-        if (p.mode & kRho) {
-          double2* S = p.rho_part + (int64_t)it.chunk * p.rho_chunk_stride + ki.offH;
-          const bool first = (n == it.n0);
-          for (int e = tid; e < N * N; e += nthr) {
-            const int i = e / N, c = e - i * N;
-            const float2 g = sG[sRow[i] + sIdx[c]];
-            if (first) {
-              S[e] = make_double2((double)g.x, (double)g.y);
-            } else {
-              double2 s = S[e];
-              s.x += (double)g.x;
-              s.y += (double)g.y;
-              S[e] = s;
-            }
-          }
-        }
-        if (p.mode & (kGloc | kAdj)) {
-          const bool adj = (p.mode & kAdj) != 0;
-          cf zw;  // -(i w_n + mu) as a pair
-          split(-mu, zw.rh, zw.rl);
-          split(-wn, zw.ih, zw.il);
-          const float4* Sgp = p.Sd + si.offSig + (int64_t)n * M * M;
-          auto X = [&](int i, int c) { return sG[sRow[i] + sIdx[c]]; };
-          // Y0 = X P^+ (N x M)
-          mm_f32(N, M, N, X, [&](int c, int b) { return fconj(sP[b * N + c]); },
-                 [&](int i, int b, float2 v) { sY0[i * M + b] = v; });
-          // Z0 = P X (M x N)
-          if (adj)
-            mm_f32(M, N, N, [&](int a, int i) { return sP[a * N + i]; }, X,
-                   [&](int a, int c, float2 v) { sZ0[a * N + c] = v; });
-          __syncthreads();
-          // W = P Y0 (pairs; the sum over bands split in S parts, partials in the R region)
-          const int S = max(1, min(4, N / M));
-          mm_pair(M, M, N, S, sPart, [&](int a, int i) { return ld4(Pkp[a * N + i]); },
-                  [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
-                  [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
-          __syncthreads();
-          // V = Sigma W (pairs)
-          mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(Sgp[a * M + x]); },
-                  [&](int x, int b) { return ld4(sW[x * M + b]); }, [&](int, int) { return czero(); },
-                  [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
-          __syncthreads();
-          // R = P^+ - A Y0 = P^+ - (i w + mu) Y0 + H Y0 + P^+ V  (pairs, rounded to FP32)
-          mm_pair(N, M, N, 1, sPart, [&](int i, int c) { return ld4(Hkp[i * N + c]); },
-                  [&](int c, int b) { return sY0[c * M + b]; },
-                  [&](int i, int b) {
-                    cf acc = conj_cf(ld4(Pkp[b * N + i]));
-                    cacc1(acc, zw, sY0[i * M + b]);
-                    for (int a = 0; a < M; ++a) cacc_ca(acc, ld4(Pkp[a * N + i]), ld4(sV[a * M + b]));
-                    return acc;
-                  },
-                  [&](int i, int b, const cf& v) { sR[i * M + b] = round_cf(v); });
-          __syncthreads();
-          // dY = X R (FP32);  Y = Y0 + dY
-          mm_f32(N, M, N, X, [&](int c, int b) { return sR[c * M + b]; },
-                 [&](int i, int b, float2 v) { sdY[i * M + b] = v; });
-          __syncthreads();
-          // P Y = W + P dY (the second term in FP32)
-          if (p.mode & kGloc) {
-            double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
-            mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
-                   [&](int i, int b) { return sdY[i * M + b]; },
-                   [&](int a, int b, float2 d) {
-                     const double2 w = to_d2(ld4(sW[a * M + b]));
-                     gq_put(&out[a * M + b], q, make_double2(wk * (w.x + (double)d.x), wk * (w.y + (double)d.y)));
-                   });
-          }
-          if (adj) {
-            // A_k = P Y in pairs
-            mm_f32(M, M, N, [&](int a, int i) { return sP[a * N + i]; },
-                   [&](int i, int b) { return sdY[i * M + b]; },
-                   [&](int a, int b, float2 d) {
-                     cf q = ld4(sW[a * M + b]);
-                     add_single(q, d);
-                     sQa[a * M + b] = st4(q);
-                   });
-            __syncthreads();
-            // W' = Z0 P^+ (pairs), then V' = W' Sigma
-            mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
-                    [&](int i, int b) { return conj_cf(ld4(Pkp[b * N + i])); }, [&](int, int) { return czero(); },
-                    [&](int a, int b, const cf& v) { sW[a * M + b] = st4(v); });
-            __syncthreads();
-            mm_pair(M, M, M, 1, sPart, [&](int a, int x) { return ld4(sW[a * M + x]); },
-                    [&](int x, int b) { return ld4(Sgp[x * M + b]); }, [&](int, int) { return czero(); },
-                    [&](int a, int b, const cf& v) { sV[a * M + b] = st4(v); });
-            __syncthreads();
-            // R' = P - Z0 A = P - (i w + mu) Z0 + Z0 H + V' P  (pairs, rounded), M x N
-            mm_pair(M, N, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
-                    [&](int i, int c) { return ld4(Hkp[i * N + c]); },
-                    [&](int a, int c) {
-                      cf acc = ld4(Pkp[a * N + c]);
-                      cacc1(acc, zw, sZ0[a * N + c]);
-                      for (int b = 0; b < M; ++b) cacc(acc, ld4(sV[a * M + b]), ld4(Pkp[b * N + c]));
-                      return acc;
-                    },
-                    [&](int a, int c, const cf& v) { sR[a * N + c] = round_cf(v); });
-            __syncthreads();
-            // dZ = R' X (FP32)
-            mm_f32(M, N, N, [&](int a, int i) { return sR[a * N + i]; }, X,
-                   [&](int a, int c, float2 v) { sdZ[a * N + c] = v; });
-            __syncthreads();
-            // B_k = Z Y = Z0 Y0 (pairs of exact FP32 products) + Z0 dY + dZ Y0 (FP32)
-            mm_pair(M, M, N, 1, sPart, [&](int a, int i) { return sZ0[a * N + i]; },
-                    [&](int i, int b) { return sY0[i * M + b]; }, [&](int, int) { return czero(); },
-                    [&](int a, int b, const cf& v) { sQb[a * M + b] = st4(v); });
-            __syncthreads();
-            mm_f32(M, M, 2 * N,
-                   [&](int a, int k) { return k < N ? sZ0[a * N + k] : sdZ[a * N + k - N]; },
-                   [&](int k, int b) { return k < N ? sdY[k * M + b] : sY0[(k - N) * M + b]; },
-                   [&](int a, int b, float2 d) {
-                     cf q = ld4(sQb[a * M + b]);
-                     add_single(q, d);
-                     sQb[a * M + b] = st4(q);
-                   });
-            __syncthreads();
-            const bool have_gbar = (p.Gbd != nullptr);
-            if (have_gbar) {
-              const float4* Gb = p.Gbd + si.offSig + (int64_t)n * M * M;
-              // Mt = Gbar A_k^+ (pairs)
-              mm_pair(M, M, M, 1, sPart, [&](int a, int c) { return ld4(Gb[a * M + c]); },
-                      [&](int c, int b) { return conj_cf(ld4(sQa[b * M + c])); }, [&](int, int) { return czero(); },
-                      [&](int a, int b, const cf& v) { sMt[a * M + b] = st4(v); });
-              // mu_bar partial: - w_k Re<Gbar, B_k>
-              for (int e = tid; e < M * M; e += nthr) {
-                const double2 gv = to_d2(ld4(Gb[e])), bv = to_d2(ld4(sQb[e]));
-                acc_mu -= wk * fma(gv.x, bv.x, gv.y * bv.y);
-              }
-              __syncthreads();
-            }
-            double2* out = p.gq + ((int64_t)(it.g - p.gb0) * p.n_iw + n) * p.mmax * p.mmax;
-            const double cb = nbar * 2.0 / beta;
-            for (int e = tid; e < M * M; e += nthr) {
-              const int a = e / M, b = e - a * M;
-              cf acc = czero();
-              if (have_gbar)
-                for (int c = 0; c < M; ++c) cacc_ca(acc, ld4(sQa[c * M + a]), ld4(sMt[c * M + b]));
-              cnorm(acc);
-              const double2 v = to_d2(acc);
-              const double2 bt = to_d2(ld4(sQb[b * M + a]));
-              gq_put(&out[e], q, make_double2(wk * fma(cb, bt.x, v.x), wk * fma(-cb, bt.y, v.y)));
-            }
-          }
-        }
+        f32r_epilogues(p, eb, it, ki, si, q, N, M, n, wn, mu, beta, wk, nbar, Hkp, Pkp, sG, sRow, sIdx,
+                       acc_mu);
       }
       if (p.mode & kOcc) {
         const double tr_ = block_sum_f(acc_tr, s_red);
@@ -787,6 +815,240 @@ cudaError_t launch_point_f32r(int shape, const PointParams& p, int grid, int thr
 #undef X
   }
   return cudaErrorInvalidValue;
+}
+
+
+// Shared memory of k_point_f32w (bytes): the CTA's P and H_ii of the k-point and the
+// epilogue buffers (as in LayoutF; R and dY contiguous for the pair partial sums), then
+// per warp Sigma, T = Sigma P (then the warp's inverse), the diagonal, the pivot-row
+// buffer and the pivot tables.
+struct LayoutFW {
+  size_t oP, oHii, oW, oV, oY0, oR, odY, oZ0, odZ, oQa, oQb, oMt, warp0, wstride, wS, wX, wD, wBuf, wPiv, bytes;
+};
+
+__host__ __device__ inline LayoutFW make_layout_fw(int nbmax, int mmax, int mode, int nmax, int nwarps) {
+  LayoutFW L;
+  const size_t ld = (size_t)(nbmax | 1);
+  const size_t mn = (size_t)mmax * nbmax, mm = (size_t)mmax * mmax;
+  const bool refine = (mode & (kGloc | kAdj)) != 0;
+  const bool adj = (mode & kAdj) != 0;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {  // 16-byte aligned region
+    o = (o + 15) & ~(size_t)15;
+    const size_t at = o;
+    o += bytes;
+    return at;
+  };
+  L.oP = take(8 * mn);
+  L.oHii = take(16 * (size_t)nbmax);
+  L.oW = take(refine ? 16 * mm : 0);
+  L.oV = take(refine ? 16 * mm : 0);
+  L.oY0 = take(refine ? 8 * mn : 0);
+  L.oR = take(refine ? 8 * mn : 0);
+  L.odY = o; o += refine ? 8 * mn : 0;
+  L.oZ0 = take(adj ? 8 * mn : 0);
+  L.odZ = take(adj ? 8 * mn : 0);
+  L.oQa = take(adj ? 16 * mm : 0);
+  L.oQb = take(adj ? 16 * mm : 0);
+  L.oMt = take(adj ? 16 * mm : 0);
+  L.warp0 = take(0);
+  size_t g = 0;
+  auto wtake = [&g](size_t bytes) {
+    g = (g + 15) & ~(size_t)15;
+    const size_t at = g;
+    g += bytes;
+    return at;
+  };
+  size_t x = mn;
+  if (x < (size_t)nbmax * ld) x = (size_t)nbmax * ld;
+  L.wS = wtake(8 * mm);
+  L.wX = wtake(8 * x);
+  L.wD = wtake(8 * (size_t)nbmax);
+  L.wBuf = wtake(8 * (size_t)nmax);
+  L.wPiv = wtake(3 * sizeof(int) * (size_t)nmax);
+  L.wstride = (g + 15) & ~(size_t)15;
+  L.bytes = L.warp0 + (size_t)nwarps * L.wstride;
+  return L;
+}
+
+namespace {
+
+constexpr int kF32wWarps = 4;  // warps per CTA: frequencies inverted together
+
+// Fused passes (kRho, kGloc, kAdj, with or without kOcc) for windows up to 40 bands.
+// Each warp inverts one frequency of the item with warp_invert (one warp per matrix,
+// the matrix in registers; kOcc traces taken by the warp from its inverse), then the
+// whole CTA runs the refined-projection epilogues of the W inverses in frequency order.
+template <int NMAX, bool SPLIT, int W>
+__global__ void __launch_bounds__(32 * W, 2) k_point_f32w(const PointParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_item;
+  __shared__ double s_red[W];
+  const LayoutFW L = make_layout_fw(p.nbmax, p.mmax, p.mode, NMAX, W);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  float2* sP = reinterpret_cast<float2*>(smraw + L.oP);
+  double2* sHii = reinterpret_cast<double2*>(smraw + L.oHii);
+  const EpiF eb{sP,
+                reinterpret_cast<float4*>(smraw + L.oW),
+                reinterpret_cast<float4*>(smraw + L.oV),
+                reinterpret_cast<float4*>(smraw + L.oQa),
+                reinterpret_cast<float4*>(smraw + L.oQb),
+                reinterpret_cast<float4*>(smraw + L.oMt),
+                reinterpret_cast<float4*>(smraw + L.oR),
+                reinterpret_cast<float2*>(smraw + L.oY0),
+                reinterpret_cast<float2*>(smraw + L.oR),
+                reinterpret_cast<float2*>(smraw + L.odY),
+                reinterpret_cast<float2*>(smraw + L.oZ0),
+                reinterpret_cast<float2*>(smraw + L.odZ)};
+  auto warp_region = [&](int w) { return smraw + L.warp0 + (size_t)w * L.wstride; };
+  auto bufs_of = [&](int w) {
+    unsigned char* wb = warp_region(w);
+    int* piv = reinterpret_cast<int*>(wb + L.wPiv);
+    return wgj::WarpBufs{reinterpret_cast<float2*>(wb + L.wX), reinterpret_cast<float2*>(wb + L.wBuf), piv,
+                         piv + NMAX, piv + 2 * NMAX};
+  };
+  float2* sS = reinterpret_cast<float2*>(warp_region(wp) + L.wS);
+  float2* sD = reinterpret_cast<float2*>(warp_region(wp) + L.wD);
+  const wgj::WarpBufs mine = bufs_of(wp);
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1);
+    __syncthreads();
+    const int itx = s_item;
+    if (itx >= p.n_items) break;
+    const Item it = p.items[itx];
+    for (int q = 0; q < it.nk; ++q) {
+      const int kk = item_k(it, p.kperm, q);
+      const KInfo ki = p.kinfo[kk];
+      const SInfo si = p.sinfo[ki.sys];
+      const int N = ki.nb, M = si.m;
+      const float2* Hk = p.Hs + ki.offH;
+      const double2* Hk64 = p.H + ki.offH;
+      const float4* Hkp = p.Hd + ki.offH;
+      const float4* Pkp = p.Pd + ki.offP;
+      const double mu = p.mu[ki.sys];
+      const double beta = si.beta;
+      const double wk = ki.w;
+      double nbar = 0.0;
+      if ((p.mode & kAdj) && p.nbar) nbar = p.nbar[ki.sys];
+      for (int e = tid; e < M * N; e += 32 * W) sP[e] = p.Ps[ki.offP + e];
+      for (int i = tid; i < N; i += 32 * W) sHii[i] = Hk64[i * N + i];
+      __syncthreads();
+      const double pib = M_PI / beta;
+      double acc_tr = 0.0, acc_g2 = 0.0, acc_mu = 0.0;
+      for (int nb = it.n0; nb < it.n1; nb += W) {
+        // every warp inverts one frequency
+        const int n = nb + wp;
+        if (n < it.n1) {
+          const double wn = (2.0 * n + 1.0) * pib;
+          for (int e = lane; e < M * M; e += 32) sS[e] = p.Ss[si.offSig + (int64_t)n * M * M + e];
+          for (int x = lane; x < N; x += 32)
+            sD[x] = make_float2(__double2float_rn(mu - sHii[x].x), __double2float_rn(wn - sHii[x].y));
+          __syncwarp();
+          for (int e = lane; e < M * N; e += 32) {  // T = Sigma P (M x N)
+            const int a = e / N, j = e - a * N;
+            float2 acc = f2zero();
+            for (int b = 0; b < M; ++b) fmac(acc, sS[a * M + b], sP[b * N + j]);
+            mine.sX[e] = acc;
+          }
+          __syncwarp();
+          wgj::warp_invert<NMAX, SPLIT>(Hk, sD, sP, mine, N, M, lane, p.status);
+          if (p.mode & kOcc) {
+            const float2* sX = mine.sX;
+            for (int x = lane; x < N; x += 32) acc_tr += (double)sX[mine.sRow[x] + mine.sIdx[x]].x;
+            float g2 = 0.f;
+            for (int e = lane; e < N * N; e += 32) {
+              const int i = e / N, c = e - i * N;
+              const float2 g1 = sX[mine.sRow[i] + mine.sIdx[c]], g3 = sX[mine.sRow[c] + mine.sIdx[i]];
+              g2 = __fmaf_rn(g1.x, g3.x, __fmaf_rn(-g1.y, g3.y, g2));
+            }
+            acc_g2 += (double)g2;
+          }
+        }
+        __syncthreads();  // the inverses of the batch are visible to the CTA
+        // the CTA's epilogues, one frequency after the other
+        const int nw = min(W, it.n1 - nb);
+        for (int w = 0; w < nw; ++w) {
+          const int nn = nb + w;
+          const wgj::WarpBufs bw = bufs_of(w);
+          f32r_epilogues(p, eb, it, ki, si, q, N, M, nn, (2.0 * nn + 1.0) * pib, mu, beta, wk, nbar, Hkp, Pkp,
+                         bw.sX, bw.sRow, bw.sIdx, acc_mu);
+          __syncthreads();  // epilogue buffers and the warp regions free again
+        }
+      }
+      if (p.mode & kOcc) {
+        const double tr_ = block_sum_f(acc_tr, s_red);
+        const double g2 = block_sum_f(acc_g2, s_red);
+        if (tid == 0) {
+          double* o = p.occ_part + ((int64_t)kk * p.n_chunks + it.chunk) * 2;
+          o[0] = tr_;
+          o[1] = g2;
+        }
+      }
+      if (p.mode & kAdj) {
+        const double mb = block_sum_f(acc_mu, s_red);
+        if (tid == 0) p.mubar_part[(int64_t)kk * p.n_chunks + it.chunk] = mb;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int NMAX, bool SPLIT>
+cudaError_t set_attrs_fw(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_point_f32w<NMAX, SPLIT, kF32wWarps>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_point_f32w<NMAX, SPLIT, kF32wWarps>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <int NMAX, bool SPLIT>
+cudaError_t launch_fw(const PointParams& p, int grid, size_t smem, cudaStream_t s) {
+  const cudaError_t e = set_attrs_fw<NMAX, SPLIT>(smem);
+  if (e != cudaSuccess) return e;
+  k_point_f32w<NMAX, SPLIT, kF32wWarps><<<grid, 32 * kF32wWarps, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int NMAX, bool SPLIT>
+int bps_fw(size_t smem) {
+  int nb = 0;
+  if (set_attrs_fw<NMAX, SPLIT>(smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_point_f32w<NMAX, SPLIT, kF32wWarps>, 32 * kF32wWarps,
+                                                    smem) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+}  // namespace
+
+// Largest window of the instantiation that serves nbmax, or 0 (the one-warp inverse
+// holds windows up to 40 bands).
+int f32w_nmax(int nbmax) { return nbmax <= 16 ? 16 : (nbmax <= 32 ? 32 : (nbmax <= 40 ? 40 : 0)); }
+
+int f32w_threads() { return 32 * kF32wWarps; }
+
+size_t point_f32w_smem(int nbmax, int mmax, int mode) {
+  return make_layout_fw(nbmax, mmax, mode, f32w_nmax(nbmax), kF32wWarps).bytes;
+}
+
+int point_f32w_blocks_per_sm(int nbmax, size_t smem) {
+  switch (f32w_nmax(nbmax)) {
+    case 16: return bps_fw<16, false>(smem);
+    case 32: return bps_fw<32, false>(smem);
+    case 40: return bps_fw<40, true>(smem);
+    default: return 0;
+  }
+}
+
+cudaError_t launch_point_f32w(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s) {
+  switch (f32w_nmax(nbmax)) {
+    case 16: return launch_fw<16, false>(p, grid, smem, s);
+    case 32: return launch_fw<32, false>(p, grid, smem, s);
+    case 40: return launch_fw<40, true>(p, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace gf

@@ -321,6 +321,13 @@ bool f32r_shape_fits(int shape, int nbmax);
 int f32r_threads(int shape, int nbmax);
 size_t point_f32r_smem(int nbmax, int mmax, int mode);
 int point_f32r_blocks_per_sm(int shape, int threads, size_t smem);
+// ... and its fused passes for windows up to 40 bands with one warp per matrix: each warp
+// inverts one frequency, the CTA runs the refined projections (gf_f32r.cu).
+int f32w_nmax(int nbmax);
+int f32w_threads();
+size_t point_f32w_smem(int nbmax, int mmax, int mode);
+int point_f32w_blocks_per_sm(int nbmax, size_t smem);
+cudaError_t launch_point_f32w(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s);
 
 // Mixed-precision N(mu) kernel for windows up to 40 bands (gf_w32.cu): one warp per
 // matrix, the matrix in registers.

@@ -6,39 +6,24 @@
 // FP64 and rounded once), X = A^{-1}, and Re Tr X, Re Tr X^2 summed over the item's
 // frequencies in FP64 (the N(mu) and dN/dmu partial sums).
 //
-// Lane l holds row l (all N_b columns, NMAX complex registers).  Windows of 33 to 40
-// bands add rows 32 to 39, each split over a group of four lanes: lane l holds columns
-// 10 (l mod 4) to 10 (l mod 4) + 9 of row 32 + l / 4, so every lane updates 50 entries
-// per pivot instead of the 80 of two whole rows a lane.
-// Gauss-Jordan in exchange form with partial pivoting, every register index static
-// (each step rotates the rows by one column, so the pivot column is register 0; a split
-// row rotates across its four lanes with one shuffle), and
-// lazy row scaling: the stored matrix is the true one with each
-// former pivot row divided by its scale s_p.  Step j, pivot row p (unused, largest
-// |a_ij|), u = row p as stored (its scale is still 1), r = 1 / u_j:
-//   every other row i:  l_i = a_ij r;  a_ic -= l_i u_c (c != j);  a_ij = -l_i
-//   row p:              unchanged except a_pj = 1, and its scale becomes r
-// which is the sweep of the true matrix written in stored terms (a former pivot row
-// updates with its stored values, because its true l and its true entries carry the
-// same scale).  The row reaches the warp through a shared-memory buffer, the pivot
-// through a warp max-reduction; the true inverse is s_r a_rc at the end.
+// The elimination (one warp per matrix, rows rotated one column per pivot, rows 32 to 39
+// of 33- to 40-band windows split over four lanes, lazy row scales) is warp_invert of
+// gf_warp_gj.cuh.  Windows of 41 to 96 bands run k_point_wm below: two or three warps
+// per matrix, one row per lane.
 #include <math.h>
 #include <stdint.h>
 
 #include "gf_complex.cuh"
 #include "gf_internal.cuh"
+#include "gf_warp_gj.cuh"
 
 namespace gf {
 
 namespace {
 
 using namespace cx;
-
-__device__ __forceinline__ float2 zero2() { return make_float2(0.f, 0.f); }
-
-__device__ __forceinline__ unsigned pack_key_w(float2 v, int i) {
-  return (pivot_key_s(v) & ~127u) | (unsigned)(127 - i);
-}
+using wgj::pack_key_w;
+using wgj::zero2;
 
 }  // namespace
 
@@ -101,28 +86,23 @@ namespace {
 // thread); shared memory allows six for a 40-band window with 14 orbitals.
 constexpr int kW32MinBlocks = 6;
 
-template <int NMAX, int ROWS, int W, bool SPLIT>
+template <int NMAX, int W, bool SPLIT>
 __global__ void __launch_bounds__(32 * W, kW32MinBlocks) k_point_w32(const PointParams p) {
-  static_assert(!SPLIT || (ROWS == 1 && NMAX == 40), "split rows: one whole row a lane, 40 columns");
-  constexpr int SEG = NMAX / 4;  // columns of a split row on one lane
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_item;
   __shared__ double s_part[W][2];
   const LayoutW L = make_layout_w(p.nbmax, p.mmax, NMAX, W);
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-  // split row of this lane: row 32 + lane / 4, columns c1 .. c1 + SEG - 1 (register order)
-  const int g = lane & 3, r1 = 32 + (lane >> 2), c1 = SEG * g;
-  const int lead = lane & ~3, nxt = lead | ((lane + 1) & 3);
   float2* sP = reinterpret_cast<float2*>(smraw + L.oP);
   double2* sHii = reinterpret_cast<double2*>(smraw + L.oHii);
   unsigned char* wb = smraw + L.warp0 + (size_t)wp * L.wstride;
   float2* sS = reinterpret_cast<float2*>(wb + L.wS);
   float2* sX = reinterpret_cast<float2*>(wb + L.wX);
   float2* sD = reinterpret_cast<float2*>(wb + L.wD);
-  float2* sBuf = reinterpret_cast<float2*>(wb + L.wBuf);
   int* sPiv = reinterpret_cast<int*>(wb + L.wPiv);
-  int* sIdx = sPiv + NMAX;
-  int* sRow = sIdx + NMAX;
+  const wgj::WarpBufs bufs{sX, reinterpret_cast<float2*>(wb + L.wBuf), sPiv, sPiv + NMAX, sPiv + 2 * NMAX};
+  const int* sIdx = bufs.sIdx;
+  const int* sRow = bufs.sRow;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(p.queue, 1);
@@ -133,7 +113,7 @@ __global__ void __launch_bounds__(32 * W, kW32MinBlocks) k_point_w32(const Point
     const int kk = item_k(it, p.kperm, 0);  // N(mu) items hold one k-point
     const KInfo ki = p.kinfo[kk];
     const SInfo si = p.sinfo[ki.sys];
-    const int N = ki.nb, M = si.m, ld = N | 1;
+    const int N = ki.nb, M = si.m;
     const float2* Hk = p.Hs + ki.offH;
     const double2* Hk64 = p.H + ki.offH;
     const double mu = p.mu[ki.sys];
@@ -156,163 +136,7 @@ __global__ void __launch_bounds__(32 * W, kW32MinBlocks) k_point_w32(const Point
         sX[e] = acc;
       }
       __syncwarp();
-      // A = diag - H - P^+ T: rows lane (and lane + 32), the split row's segment
-      float2 a[ROWS][NMAX];
-      float2 a1[SPLIT ? SEG : 1];
-#pragma unroll
-      for (int s = 0; s < ROWS; ++s) {
-        const int r = lane + 32 * s;
-#pragma unroll
-        for (int c = 0; c < NMAX; ++c) {
-          float2 v = zero2();
-          if (r < N && c < N) {
-            const float2 h = Hk[r * N + c];
-            v = (r == c) ? sD[r] : make_float2(-h.x, -h.y);
-          }
-          a[s][c] = v;
-        }
-        if (r < N) {
-          for (int x = 0; x < M; ++x) {
-            const float2 pv = sP[x * N + r];
-            const float2 mp = make_float2(-pv.x, pv.y);  // -conj(P[x][r])
-#pragma unroll
-            for (int c = 0; c < NMAX; ++c)
-              if (c < N) fmac(a[s][c], mp, sX[x * N + c]);
-          }
-        }
-      }
-      if constexpr (SPLIT) {
-#pragma unroll
-        for (int y = 0; y < SEG; ++y) {
-          const int c = c1 + y;
-          float2 v = zero2();
-          if (r1 < N && c < N) {
-            const float2 h = Hk[r1 * N + c];
-            v = (r1 == c) ? sD[r1] : make_float2(-h.x, -h.y);
-          }
-          a1[y] = v;
-        }
-        if (r1 < N) {
-          for (int x = 0; x < M; ++x) {
-            const float2 pv = sP[x * N + r1];
-            const float2 mp = make_float2(-pv.x, pv.y);
-#pragma unroll
-            for (int y = 0; y < SEG; ++y)
-              if (c1 + y < N) fmac(a1[y], mp, sX[x * N + c1 + y]);
-          }
-        }
-      }
-      // Gauss-Jordan, lazy row scales.  Each step rotates every row left by one column,
-      // so the pivot column is always register 0 and the loop body stays small; after
-      // step j the original column c sits at register (c - j - 1) mod NMAX.
-      bool used[ROWS], used1 = false;
-      float2 sc[ROWS], sc1 = make_float2(1.f, 0.f);
-#pragma unroll
-      for (int s = 0; s < ROWS; ++s) {
-        used[s] = false;
-        sc[s] = make_float2(1.f, 0.f);
-      }
-#pragma unroll 1
-      for (int j = 0; j < N; ++j) {
-        unsigned key = 0u;
-#pragma unroll
-        for (int s = 0; s < ROWS; ++s) {
-          const int r = lane + 32 * s;
-          if (r < N && !used[s]) key = max(key, pack_key_w(a[s][0], r));
-        }
-        // a split row's pivot-column entry sits on the first lane of its group
-        if constexpr (SPLIT)
-          if (g == 0 && r1 < N && !used1) key = max(key, pack_key_w(a1[0], r1));
-        const unsigned best = __reduce_max_sync(0xffffffffu, key);
-        if (lane == 0 && ((best >> 7) == 0u || (best & ~127u) >= 0x7f800000u)) atomicOr(p.status, kFlagSingular);
-        const int prow = min(127 - (int)(best & 127u), N - 1);
-        const int pl = prow & 31, ps = prow >> 5;
-        if (lane == pl) {
-#pragma unroll
-          for (int s = 0; s < ROWS; ++s)
-            if (s == ps)
-#pragma unroll
-              for (int c = 0; c < NMAX; ++c) sBuf[c] = a[s][c];
-        }
-        if constexpr (SPLIT)
-          if (r1 == prow)
-#pragma unroll
-            for (int y = 0; y < SEG; ++y) sBuf[c1 + y] = a1[y];
-        __syncwarp();
-        const float2 r = frcp(sBuf[0]);
-        float2 lq[ROWS];
-        bool isp[ROWS];
-#pragma unroll
-        for (int s = 0; s < ROWS; ++s) {
-          isp[s] = (lane == pl) && (s == ps);
-          lq[s] = isp[s] ? zero2() : fmul(a[s][0], r);
-        }
-#pragma unroll
-        for (int c = 1; c < NMAX; ++c) {
-          const float2 uc = sBuf[c];
-#pragma unroll
-          for (int s = 0; s < ROWS; ++s) fsub_prod(a[s][c], lq[s], uc);
-        }
-#pragma unroll
-        for (int s = 0; s < ROWS; ++s) {
-          const float2 col = isp[s] ? make_float2(1.f, 0.f) : make_float2(-lq[s].x, -lq[s].y);
-#pragma unroll
-          for (int c = 0; c + 1 < NMAX; ++c) a[s][c] = a[s][c + 1];
-          a[s][NMAX - 1] = col;
-          if (isp[s]) {
-            used[s] = true;
-            sc[s] = r;
-          }
-        }
-        if constexpr (SPLIT) {
-          // the split row: l from its first lane; every entry updated (the pivot
-          // column's is replaced below), then the row rotates left across the group
-          const float2 h1 = make_float2(__shfl_sync(0xffffffffu, a1[0].x, lead),
-                                        __shfl_sync(0xffffffffu, a1[0].y, lead));
-          const bool isp1 = (r1 == prow);
-          const float2 lq1 = isp1 ? zero2() : fmul(h1, r);
-#pragma unroll
-          for (int y = 0; y < SEG; ++y) fsub_prod(a1[y], lq1, sBuf[c1 + y]);
-          if (g == 0) a1[0] = isp1 ? make_float2(1.f, 0.f) : make_float2(-lq1.x, -lq1.y);
-          const float2 t = make_float2(__shfl_sync(0xffffffffu, a1[0].x, nxt),
-                                       __shfl_sync(0xffffffffu, a1[0].y, nxt));
-#pragma unroll
-          for (int y = 0; y + 1 < SEG; ++y) a1[y] = a1[y + 1];
-          a1[SEG - 1] = t;
-          if (isp1) {
-            used1 = true;
-            sc1 = r;
-          }
-        }
-        if (lane == 0) sPiv[j] = prow;
-        __syncwarp();  // the buffer is rewritten by the next pivot
-      }
-      // the inverse (true values s_r a_rc) for the traces: X[i][c] = B[p_i][q_c];
-      // register x holds the original column (x + N) mod NMAX
-#pragma unroll
-      for (int s = 0; s < ROWS; ++s) {
-        const int r = lane + 32 * s;
-        if (r < N)
-#pragma unroll
-          for (int x = 0; x < NMAX; ++x) {
-            int c = x + N;
-            if (c >= NMAX) c -= NMAX;
-            if (c < N) sX[r * ld + c] = fmul(sc[s], a[s][x]);
-          }
-      }
-      if constexpr (SPLIT)
-        if (r1 < N)
-#pragma unroll
-          for (int y = 0; y < SEG; ++y) {
-            int c = c1 + y + N;
-            if (c >= NMAX) c -= NMAX;
-            if (c < N) sX[r1 * ld + c] = fmul(sc1, a1[y]);
-          }
-      __syncwarp();
-      for (int j = lane; j < N; j += 32) sIdx[sPiv[j]] = j;
-      __syncwarp();
-      for (int x = lane; x < N; x += 32) sRow[x] = sPiv[x] * ld;
-      __syncwarp();
+      wgj::warp_invert<NMAX, SPLIT>(Hk, sD, sP, bufs, N, M, lane, p.status);
       for (int x = lane; x < N; x += 32) acc_tr += (double)sX[sRow[x] + sIdx[x]].x;
       float g2 = 0.f;
       for (int e = lane; e < N * N; e += 32) {
@@ -537,28 +361,28 @@ constexpr int kW32Warps = 2;  // warps (matrices in flight) per CTA
 
 // Dynamic shared memory of the launch, and the largest carveout: six 2-warp CTAs of a
 // 40-band window (36 KB each) fill an SM only with the whole 228 KB as shared memory.
-template <int NMAX, int ROWS, bool SPLIT>
+template <int NMAX, bool SPLIT>
 cudaError_t set_attrs_w(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_point_w32<NMAX, ROWS, kW32Warps, SPLIT>,
+  cudaError_t e = cudaFuncSetAttribute(k_point_w32<NMAX, kW32Warps, SPLIT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_point_w32<NMAX, ROWS, kW32Warps, SPLIT>,
+  return cudaFuncSetAttribute(k_point_w32<NMAX, kW32Warps, SPLIT>,
                               cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
-template <int NMAX, int ROWS, bool SPLIT>
+template <int NMAX, bool SPLIT>
 cudaError_t launch_w(const PointParams& p, int grid, size_t smem, cudaStream_t s) {
-  const cudaError_t e = set_attrs_w<NMAX, ROWS, SPLIT>(smem);
+  const cudaError_t e = set_attrs_w<NMAX, SPLIT>(smem);
   if (e != cudaSuccess) return e;
-  k_point_w32<NMAX, ROWS, kW32Warps, SPLIT><<<grid, 32 * kW32Warps, smem, s>>>(p);
+  k_point_w32<NMAX, kW32Warps, SPLIT><<<grid, 32 * kW32Warps, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int NMAX, int ROWS, bool SPLIT>
+template <int NMAX, bool SPLIT>
 int bps_w(size_t smem) {
   int nb = 0;
-  if (set_attrs_w<NMAX, ROWS, SPLIT>(smem) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_point_w32<NMAX, ROWS, kW32Warps, SPLIT>,
+  if (set_attrs_w<NMAX, SPLIT>(smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_point_w32<NMAX, kW32Warps, SPLIT>,
                                                     32 * kW32Warps, smem) != cudaSuccess)
     return 0;
   return nb;
@@ -600,18 +424,18 @@ size_t point_w32_smem(int nbmax, int mmax) {
 
 int point_w32_blocks_per_sm(int nbmax, size_t smem) {
   switch (w32_nmax(nbmax)) {
-    case 16: return bps_w<16, 1, false>(smem);
-    case 32: return bps_w<32, 1, false>(smem);
-    case 40: return bps_w<40, 1, true>(smem);
+    case 16: return bps_w<16, false>(smem);
+    case 32: return bps_w<32, false>(smem);
+    case 40: return bps_w<40, true>(smem);
     default: return 0;
   }
 }
 
 cudaError_t launch_point_w32(int nbmax, const PointParams& p, int grid, size_t smem, cudaStream_t s) {
   switch (w32_nmax(nbmax)) {
-    case 16: return launch_w<16, 1, false>(p, grid, smem, s);
-    case 32: return launch_w<32, 1, false>(p, grid, smem, s);
-    case 40: return launch_w<40, 1, true>(p, grid, smem, s);
+    case 16: return launch_w<16, false>(p, grid, smem, s);
+    case 32: return launch_w<32, false>(p, grid, smem, s);
+    case 40: return launch_w<40, true>(p, grid, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }
