@@ -193,21 +193,25 @@ gf_status autotune(gf_ctx* c, int key, const std::vector<LaunchCfg>& cands, gf::
                    cfg_name(cands.back()) + (cands.size() == 1 ? " (only candidate); " : " (not timed); ");
     return GF_OK;
   }
-  // the sample: one item per CTA of the largest candidate grid; a second run of a
-  // candidate only when its first took under 50 ms (the first run of a kernel also loads
-  // its module, which is noise against a long sample)
+  // the sample: whole waves of every candidate's grid, at least one item per CTA of the
+  // largest grid (so a candidate with fewer CTAs is not charged a partial last wave), and
+  // the time per item compared; a second run of a candidate only when its first took under
+  // 50 ms (the first run of a kernel also loads its module, which is noise against a long
+  // sample)
   int maxgrid = 1;
   for (const LaunchCfg& g : cands) maxgrid = std::max(maxgrid, g.grid);
-  const int n_sample = std::min(n_items, maxgrid);
   p.items = items;
   std::vector<float> ms(cands.size(), 0.f);
+  std::vector<int> n_sample(cands.size(), 1);
   ScopedEvents ev;
   GF_CU(ev.create());
   for (size_t cand = 0; cand < cands.size(); ++cand) {
+    const int g = std::max(1, std::min(cands[cand].grid, n_items));
+    n_sample[cand] = std::min(n_items, g * ((maxgrid + g - 1) / g));
     for (int rep = 0; rep < 2; ++rep) {
       GF_CU(cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream));
       GF_CU(cudaEventRecord(ev.start, c->stream));
-      gf_status st = launch_cfg(c, cands[cand], p, n_sample);
+      gf_status st = launch_cfg(c, cands[cand], p, n_sample[cand]);
       if (st) return st;
       GF_CU(cudaEventRecord(ev.stop, c->stream));
       GF_CU(cudaEventSynchronize(ev.stop));
@@ -218,15 +222,14 @@ gf_status autotune(gf_ctx* c, int key, const std::vector<LaunchCfg>& cands, gf::
   }
   int best = 0;
   for (size_t cand = 1; cand < cands.size(); ++cand)
-    if (ms[cand] < ms[best]) best = (int)cand;
+    if (ms[cand] / n_sample[cand] < ms[best] / n_sample[best]) best = (int)cand;
   c->tuned[key] = best;
   *out = cands[best];
   std::string line = "mode " + std::to_string(key >> 3) + ", windows <= " +
-                     std::to_string(cands[0].nbmax) + ": " + cfg_name(cands[best]) + " (sample of " +
-                     std::to_string(n_sample) + " items:";
+                     std::to_string(cands[0].nbmax) + ": " + cfg_name(cands[best]) + " (samples:";
   for (size_t cand = 0; cand < cands.size(); ++cand) {
-    char buf[48];
-    std::snprintf(buf, sizeof(buf), " %.3f ms", ms[cand]);
+    char buf[64];
+    std::snprintf(buf, sizeof(buf), " %d items %.3f ms", n_sample[cand], ms[cand]);
     line += (cand ? "; " : " ") + cfg_name(cands[cand]) + buf;
   }
   c->tune_log += line + "); ";
