@@ -941,17 +941,8 @@ __global__ void __launch_bounds__(32 * W, 2) k_point_f32w(const PointParams p) {
         const int n = nb + wp;
         if (n < it.n1) {
           const double wn = (2.0 * n + 1.0) * pib;
-          for (int e = lane; e < M * M; e += 32) sS[e] = p.Ss[si.offSig + (int64_t)n * M * M + e];
-          for (int x = lane; x < N; x += 32)
-            sD[x] = make_float2(__double2float_rn(mu - sHii[x].x), __double2float_rn(wn - sHii[x].y));
-          __syncwarp();
-          for (int e = lane; e < M * N; e += 32) {  // T = Sigma P (M x N)
-            const int a = e / N, j = e - a * N;
-            float2 acc = f2zero();
-            for (int b = 0; b < M; ++b) fmac(acc, sS[a * M + b], sP[b * N + j]);
-            mine.sX[e] = acc;
-          }
-          __syncwarp();
+          wgj::warp_point_inputs(p.Ss + si.offSig + (int64_t)n * M * M, sHii, sP, mu, wn, N, M, lane, sS, sD,
+                                 mine.sX);
           wgj::warp_invert<NMAX, SPLIT>(Hk, sD, sP, mine, N, M, lane, p.status);
           if (p.mode & kOcc) {
             const float2* sX = mine.sX;

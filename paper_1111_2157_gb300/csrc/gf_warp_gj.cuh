@@ -4,7 +4,7 @@
 // the refined projections.
 //
 // A = (i w_n + mu) I - H_k - P_k^+ T with T = Sigma(i w_n) P_k (Eq. dmftloop1), FP32,
-// the diagonal (i w_n + mu - H_ii) formed in FP64 by the caller and rounded once.
+// the diagonal (i w_n + mu - H_ii) formed in FP64 and rounded once (warp_point_inputs).
 //
 // Layout: lane l holds row l (NMAX complex registers).  Windows of 33 to 40 bands add
 // rows 32 to 39, each split over a group of four lanes: lane l holds columns
@@ -51,6 +51,25 @@ struct WarpBufs {
   int* sIdx;
   int* sRow;
 };
+
+// Per-frequency inputs of one warp's matrix: Sigma(i w_n) (Sn, M x M, FP32) to sS, the
+// diagonal (i w_n + mu - H_ii) formed in FP64 and rounded once to sD, and T = Sigma P
+// (M x N) to sX; visible to the whole warp on return.
+__device__ __forceinline__ void warp_point_inputs(const float2* __restrict__ Sn, const double2* sHii,
+                                                  const float2* sP, double mu, double wn, int N, int M, int lane,
+                                                  float2* sS, float2* sD, float2* sX) {
+  for (int e = lane; e < M * M; e += 32) sS[e] = Sn[e];
+  for (int x = lane; x < N; x += 32)
+    sD[x] = make_float2(__double2float_rn(mu - sHii[x].x), __double2float_rn(wn - sHii[x].y));
+  __syncwarp();
+  for (int e = lane; e < M * N; e += 32) {
+    const int a = e / N, j = e - a * N;
+    float2 acc = zero2();
+    for (int b = 0; b < M; ++b) fmac(acc, sS[a * M + b], sP[b * N + j]);
+    sX[e] = acc;
+  }
+  __syncwarp();
+}
 
 // Embedding, elimination and the inverse in shared memory, for N <= NMAX (SPLIT: NMAX =
 // 40 and rows 32 to 39 split).  On exit X[i][c] = sX[sRow[i] + sIdx[c]], visible to the
