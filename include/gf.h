@@ -73,11 +73,14 @@ typedef enum {
  *                residual in FP32 pairs.  Errors against FP64: about
  *                kappa(A) 2^-24 per G entry before refinement, which averages
  *                to ~1e-9 relative on N(mu); ~1e-11 on G_loc after it.
- *                N(mu) passes of windows up to 40 bands may run one warp per
- *                matrix (the autotuner's choice).  With the environment variable
- *                GF_KERNEL=tc the N(mu) passes run on the tcgen05 tensor cores
- *                instead (blocked elimination, TF32 split operands): N within
- *                ~1e-7 of FP64.
+ *                N(mu) passes of windows up to 96 bands may run one to three
+ *                warps per matrix, and the other passes of windows up to 40
+ *                bands one warp per matrix with the CTA's refined projections
+ *                (the autotuner's choice, the same arithmetic).  The environment
+ *                variable GF_KERNEL restricts the candidates: f32r (register
+ *                tiles), w32 (the warp kernels), or tc, which runs the N(mu)
+ *                passes on the tcgen05 tensor cores (blocked elimination, TF32
+ *                split operands): N within ~1e-7 of FP64.
  *  GF_PREC_PAIR  every matrix entry an FP32 pair (hi + lo) with error-free
  *                transformations on the FP32 pipes: ~1e-14 of FP64 results. */
 typedef enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1, GF_PREC_PAIR = 2 } gf_precision;
